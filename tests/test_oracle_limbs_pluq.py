@@ -1,0 +1,96 @@
+"""Pins for the oracle's limb split and rank-revealing PLUQ (CPU only)."""
+import numpy as np
+import pytest
+
+import fm_inputs
+
+
+def test_limb_counts_and_bounds():
+    from oracle import limbs
+    assert [limbs.n_limbs(p) for p in (2, 251, 257, 65521, 65537, 2147483647)] == [1, 1, 2, 2, 3, 4]
+    assert limbs.bounds(2) == (-32896, 32639)
+    assert limbs.bounds(4) == (-128 * 16843009, 127 * 16843009)
+
+
+def test_split_exhaustive_65521():
+    from oracle import limbs
+    p = 65521
+    x = np.arange(p, dtype=np.int64)
+    d = limbs.split(x, p)
+    assert d.shape == (2, p) and d.dtype == np.int8
+    r = limbs.recombine(d)
+    lo, hi = limbs.bounds(2)
+    assert r.min() >= lo and r.max() <= hi
+    assert np.array_equal(r % p, x)
+    # representative rule: x itself up to Hi, x - p above it
+    assert np.array_equal(r[:hi + 1], x[:hi + 1])
+    assert np.array_equal(r[hi + 1:], x[hi + 1:] - p)
+
+
+def test_split_31bit_random_and_extremes():
+    from oracle import limbs
+    p = 2147483647
+    _, hi = limbs.bounds(4)
+    x = np.concatenate([fm_inputs.uniform_residues(1, 200000, p).astype(np.int64),
+                        np.array([0, 1, 127, 128, hi, hi + 1, p - 2, p - 1], dtype=np.int64)])
+    d = limbs.split(x, p)
+    r = limbs.recombine(d)
+    assert np.array_equal(r % p, x)
+    assert d.min() >= -128 and d.max() <= 127
+
+
+@pytest.mark.parametrize("p", [65521, 2147483647, 257])
+def test_limb_products_reproduce_modular_product(orc, p):
+    # sum_s 256^s sum_{i+j=s} A_i B_j == A_r B_r exactly; mod p it is A*B mod p
+    from oracle import limbs
+    A = fm_inputs.uniform_residues(2, (9, 31), p, 1)
+    B = fm_inputs.uniform_residues(2, (31, 7), p, 2)
+    dA, dB = limbs.split(A, p), limbs.split(B, p)
+    w = dA.shape[0]
+    total = np.zeros((9, 7), dtype=object)
+    for i in range(w):
+        for j in range(w):
+            P = dA[i].astype(np.int64) @ dB[j].astype(np.int64)
+            total = total + P.astype(object) * (256 ** (i + j))
+    got = np.array([[int(v) % p for v in row] for row in total], dtype=np.uint32)
+    assert np.array_equal(got, orc.gemm_modp(None, A, B, p, 0))
+
+
+def _check_pluq(orc, A, p):
+    rp, cp, L, U, r = orc.pluq(A, p)
+    assert sorted(rp.tolist()) == list(range(A.shape[0]))
+    assert sorted(cp.tolist()) == list(range(A.shape[1]))
+    LU = orc.gemm_modp(None, L, U, p, 0)
+    assert np.array_equal(orc.permute(A, rp, cp), LU)
+    for t in range(r):
+        assert L[t, t] == 1 and not L[:t, t].any()
+        assert U[t, t] != 0 and not U[t, :t].any()
+    return r
+
+
+def test_pluq_special_cases(orc):
+    p = 65521
+    assert _check_pluq(orc, np.zeros((5, 7), np.uint32), p) == 0
+    assert _check_pluq(orc, np.eye(6, dtype=np.uint32), p) == 6
+    u = fm_inputs.uniform_residues(1, 8, p, 1).astype(np.int64)
+    v = fm_inputs.uniform_residues(1, 5, p, 2).astype(np.int64)
+    u[0] = 1
+    v[0] = 1
+    assert _check_pluq(orc, (np.outer(u, v) % p).astype(np.uint32), p) == 1
+
+
+@pytest.mark.parametrize("p", [2, 3, 65521])
+def test_pluq_rank_deficient_against_library_rank(orc, p):
+    sympy = pytest.importorskip("sympy")
+    from sympy.polys.matrices import DomainMatrix
+    from sympy import GF
+    for seed in range(8):
+        m, n, r = (int(x) for x in fm_inputs.integers(seed, 3, 1, 9, stream=p % 97))
+        r = min(r, m, n)
+        X = fm_inputs.uniform_residues(seed, (m, r), p, 1)
+        Y = fm_inputs.uniform_residues(seed, (r, n), p, 2)
+        A = orc.gemm_modp(None, X, Y, p, 0)
+        rank = _check_pluq(orc, A, p)
+        dm = DomainMatrix([[GF(p)(int(v)) for v in row] for row in A.tolist()], (m, n), GF(p))
+        assert rank == dm.rank()
+        assert rank <= r
