@@ -1,0 +1,462 @@
+"""Throughput of the exact modular GEMM hot path on GB300.
+
+Default workload: C <- C - (P A Q) * B mod 65521 with n = 8192 (M = N = K),
+uint32 residues, i.i.d. uniform. One step is one pass of the whole path:
+row-major A, B, C (resident in HBM) -> Morton-hybrid (T' = 128) with TURBO's
+row/column permutations applied to A -> balanced int8 limb split -> tcgen05
+limb GEMM with the exact mod-p recombine/subtract epilogue -> C back to
+row-major. The plain CUDA-core form (aligned/contained decomposition of
+Sec. 2.2, T' = 64) and the FP64 DFMA form run the same step for comparison.
+
+value     = 2 M N K / (device time of one step), Gop/s (algorithmic ops only)
+e2e       = same, through host buffers: pinned H2D of A, B, C and D2H of C
+            inside the timed region
+roofline  = the limb GEMM kernel: tensor work 2 M N K w^2 (w = 2 limbs) per
+            launch / its CUDA-event duration, against the measured bf16 peak
+            (f16 runs at the bf16 rate)
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fm|reference]
+For N > 1 launch with torchrun; every rank runs an independent replica.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact modular GEMM Gop/s (2MNK/s) at p=65521, n=8192: INT8-limb vs plain, 1 GB300"
+P = 65521
+N_DEFAULT = 8192
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fm", choices=["fm", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip plain / DFMA comparison")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        load = [s for s in sm if mx and s > 0.5 * mx] or sm
+        med = load[len(load) // 2] if load else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_src: str, name: str):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if the
+    kernel's source has not changed since (summary line 'source_sha256:')."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip().lstrip("-* ").lower()] = v.strip().strip("`")
+    if vals.get("source_sha256") != sha:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(n, p, target_s, threads=0):
+    """Times the oracle's C - A*B mod p on a bounded sample of rows of the
+    n x n x n product (host cores). Returns (Gop/s, cores, sample text, seconds)."""
+    import numpy as np
+
+    import fm_inputs
+    import oracle
+    cores = oracle.set_threads(threads)
+    B = fm_inputs.uniform_residues(7, (n, n), p, 2)
+    A = fm_inputs.uniform_residues(7, (4 * cores, n), p, 1)
+    C = fm_inputs.uniform_residues(7, (4 * cores, n), p, 3)
+    rows = cores
+    t0 = time.perf_counter()
+    oracle.gemm_modp(C[:rows], A[:rows], B, p, oracle.OP_SUB)
+    dt = time.perf_counter() - t0
+    scale = max(1, int(target_s / max(dt, 1e-3)))
+    rows2 = min(4 * cores, rows * scale)
+    if rows2 > rows:
+        t0 = time.perf_counter()
+        oracle.gemm_modp(C[:rows2], A[:rows2], B, p, oracle.OP_SUB)
+        dt = time.perf_counter() - t0
+        rows = rows2
+    ops = 2.0 * rows * n * n
+    return ops / dt / 1e9, cores, f"{rows} rows of C - A*B mod {p}, n={n} (K=N=n)", dt
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain CPU triple loop) as the reference arm."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import fm_inputs
+    import oracle
+    n = args.n
+    cores = oracle.set_threads(0)
+    B = fm_inputs.uniform_residues(7, (n, n), P, 2)
+    # size one step to ~1/ (steps + warmup) of a ~3 minute budget
+    probe_rows = cores
+    A = fm_inputs.uniform_residues(7, (probe_rows, n), P, 1)
+    C = fm_inputs.uniform_residues(7, (probe_rows, n), P, 3)
+    t0 = time.perf_counter()
+    oracle.gemm_modp(C, A, B, P, oracle.OP_SUB)
+    dt = time.perf_counter() - t0
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    rows = max(1, min(n, int(probe_rows * per_step_budget / max(dt, 1e-3))))
+    A = fm_inputs.uniform_residues(7, (rows, n), P, 1)
+    C = fm_inputs.uniform_residues(7, (rows, n), P, 3)
+    for _ in range(args.warmup):
+        oracle.gemm_modp(C, A, B, P, oracle.OP_SUB)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gemm_modp(C, A, B, P, oracle.OP_SUB)
+    total = time.perf_counter() - t0
+    ops = 2.0 * rows * n * n
+    value = ops * args.steps / total / 1e9
+    sample = f"{rows} rows of C - A*B mod {P} per step, n={n} (K=N=n)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gop/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 accumulate (u128), mod p", "data": "synthetic",
+        "config": {"workload": f"C -= A*B mod {P}, n={n}, row-major, CPU oracle", "n": n, "p": P},
+        "cpu_baseline": {"value": value, "unit": "Gop/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_fm(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import fm_inputs
+    import paper_1705_04807_gb300 as fm
+    from paper_1705_04807_gb300 import build as fmbuild
+
+    if rank == 0 or world == 1:
+        fmbuild.build()
+    barrier(world)
+    fm.lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    p = P
+    w = 2
+    lt_limb, lt_plain = 7, 6
+
+    def lg_for(lt):
+        lg = 0
+        while (1 << lg) << lt < n:
+            lg += 1
+        return lg
+
+    # seeded host inputs (same on every rank: replicas)
+    A = fm_inputs.uniform_residues(1, (n, n), p, 1)
+    B = fm_inputs.uniform_residues(1, (n, n), p, 2)
+    C = fm_inputs.uniform_residues(1, (n, n), p, 3)
+    rp = fm_inputs.permutation(1, n, 4)
+    cp = fm_inputs.permutation(1, n, 5)
+
+    def dev_i32(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int32)).to(dev)
+
+    dA, dB, dC = dev_i32(A), dev_i32(B), dev_i32(C)
+    drp, dcp = dev_i32(rp), dev_i32(cp)
+    dOut = torch.empty((n, n), dtype=torch.int32, device=dev)
+
+    def morton(lt):
+        lg = lg_for(lt)
+        side = (1 << lg) << lt
+        t = torch.empty(side * side, dtype=torch.int32, device=dev)
+        return t, fm.matrix(t, lg, lt)
+
+    tA, mA = morton(lt_limb)
+    tB, mB = morton(lt_limb)
+    tC, mC = morton(lt_limb)
+    sA, sB, sC = fm.sub(mA, 0, 0, n, n), fm.sub(mB, 0, 0, n, n), fm.sub(mC, 0, 0, n, n)
+    pa = torch.empty(fm.fm_limb_planes_size(n, n, fm.FM_LIMB_A, p) // 4 + 4, dtype=torch.int32,
+                     device=dev)
+    pb = torch.empty(fm.fm_limb_planes_size(n, n, fm.FM_LIMB_B, p) // 4 + 4, dtype=torch.int32,
+                     device=dev)
+    s = stream.cuda_stream
+
+    def layout_in(srcA, srcB, srcC, mA_, mB_, mC_):
+        fm.fm_layout_to_morton_permuted(srcA, n, n, n, drp, dcp, mA_, s)
+        fm.fm_layout_to_morton(srcB, n, n, n, mB_, s)
+        fm.fm_layout_to_morton(srcC, n, n, n, mC_, s)
+
+    kern = {"layout_in": [], "limb_split": [], "limb_gemm": [], "layout_out": []}
+
+    def limb_step(srcA=dA, srcB=dB, srcC=dC, out=dOut, ev=None):
+        if ev:
+            ev[0].record(stream)
+        layout_in(srcA, srcB, srcC, mA, mB, mC)
+        if ev:
+            ev[1].record(stream)
+        fm.fm_limb_split(sA, fm.FM_LIMB_A, p, pa, None, s)
+        fm.fm_limb_split(sB, fm.FM_LIMB_B, p, pb, None, s)
+        if ev:
+            ev[2].record(stream)
+        fm.fm_limb_gemm(sC, pa, pb, n, p, fm.FM_OP_SUB, None, s)
+        if ev:
+            ev[3].record(stream)
+        fm.fm_layout_from_morton(mC, n, n, out, n, s)
+        if ev:
+            ev[4].record(stream)
+
+    launches_per_step = 3 + 2 + 1 + 1
+
+    # ---- device-timed region (inputs resident in HBM, 3 x 256 MiB > L2) ----
+    for _ in range(args.warmup):
+        limb_step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        limb_step(ev=evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    for ev in evs:
+        kern["layout_in"].append(ev[0].elapsed_time(ev[1]))
+        kern["limb_split"].append(ev[1].elapsed_time(ev[2]))
+        kern["limb_gemm"].append(ev[2].elapsed_time(ev[3]))
+        kern["layout_out"].append(ev[3].elapsed_time(ev[4]))
+    local_ms = t_start.elapsed_time(t_end)
+    total_ms = allreduce_max(local_ms, world)
+    ops = 2.0 * n * n * n
+    value = world * ops * args.steps / (total_ms / 1e3) / 1e9
+    st = fm.fm_get_last_device_status(s)
+    assert st == 0, f"device status {st}"
+
+    # ---- end to end through host buffers ----
+    hA = torch.from_numpy(A.view(np.int32)).pin_memory()
+    hB = torch.from_numpy(B.view(np.int32)).pin_memory()
+    hC = torch.from_numpy(C.view(np.int32)).pin_memory()
+    hOut = torch.empty((n, n), dtype=torch.int32).pin_memory()
+    xA, xB, xC = torch.empty_like(dA), torch.empty_like(dB), torch.empty_like(dC)
+
+    def e2e_step():
+        xA.copy_(hA, non_blocking=True)
+        xB.copy_(hB, non_blocking=True)
+        xC.copy_(hC, non_blocking=True)
+        limb_step(xA, xB, xC, dOut)
+        hOut.copy_(dOut, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
+    e2e_value = world * ops * args.steps / (e2e_ms / 1e3) / 1e9
+    # the result read back equals the device result
+    assert torch.equal(hOut, dOut.cpu())
+
+    out = {}
+    # ---- comparison forms on the same inputs (same step, other GEMM) ----
+    if not args.no_compare:
+        tA6, mA6 = morton(lt_plain)
+        tB6, mB6 = morton(lt_plain)
+        tC6, mC6 = morton(lt_plain)
+        s6 = [fm.sub(m_, 0, 0, n, n) for m_ in (mC6, mA6, mB6)]
+
+        def plain_step(algo):
+            layout_in(dA, dB, dC, mA6, mB6, mC6)
+            fm.fm_gemm_modp(s6[0], s6[1], s6[2], p, fm.FM_OP_SUB, algo, None, s)
+            fm.fm_layout_from_morton(mC6, n, n, dOut, n, s)
+
+        ref = None
+        limb_step()
+        torch.cuda.synchronize()
+        ref = dOut.clone()
+        for name, algo, steps in (("plain", fm.FM_ALGO_PLAIN, 3), ("dfma", fm.FM_ALGO_DFMA, 1)):
+            plain_step(algo)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                plain_step(algo)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            same = bool(torch.equal(dOut, ref))
+            out[name] = {"value": ops * steps / (ms / 1e3) / 1e9, "unit": "Gop/s",
+                         "ms_per_step": ms / steps, "bit_identical_to_limb": same}
+        del tA6, tB6, tC6
+
+    # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
+    burst, sustained, hbm, src = measured_peaks()
+    gemm_ms = sorted(kern["limb_gemm"])[len(kern["limb_gemm"]) // 2]
+    gemm_avg = sum(kern["limb_gemm"]) / len(kern["limb_gemm"])
+    mma_flops = 2.0 * n * n * n * w * w
+    achieved = mma_flops / (gemm_avg / 1e3) / 1e12
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_1705_04807_gb300", "csrc", "limb.cu"),
+                               "limb_gemm_n8192.md")
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
+                "frac": achieved / sustained, "traffic": traffic,
+                "kernel": "limb_gemm_kernel<256,fold>",
+                "work": f"2*M*N*K*w^2 f16 MMA flops per launch (w={w} limbs), n={n}",
+                "peak_source": f"bf16 sustained, {src} (f16 = bf16 rate)",
+                "modular_gops": ops / (gemm_avg / 1e3) / 1e9}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32 residues mod p; int8 limbs on f16 tensor cores, f32 exact accumulate",
+        "data": "synthetic",
+        "config": {"workload": f"C -= (P A Q) * B mod {p}, n={n}, Morton-hybrid T'=128, "
+                               "row-major in/out", "n": n, "p": p, "T": 1 << lt_limb,
+                   "l2": "inputs larger than L2 (3 x 256 MiB)"},
+        "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 3 * 4 * n * n,
+                "d2h_bytes_per_step": 4 * n * n},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "roofline": roofline,
+        "kernels_ms": {k: sum(v) / len(v) for k, v in kern.items()},
+    }
+    if "plain" in out:
+        line["plain"] = out["plain"]
+        line["dfma"] = out["dfma"]
+        line["limb_over_plain"] = value / out["plain"]["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, secs = cpu_oracle_rate(n, p, target_s=12.0)
+        line["cpu_baseline"] = {"value": v, "unit": "Gop/s", "cores": cores, "kind": "oracle",
+                                "sample": sample, "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_fm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * fm.h -- C ABI of libfm: exact modular matrix multiply on Morton-hybrid
+ * matrices for NVIDIA GB300 (sm_103a).
+ *
+ * Abu Salem and Al Arab, "Cache-oblivious Matrix Multiplication for Exact
+ * Factorisation" (arXiv 1705.04807):
+ *   Sec. 1   the Morton-hybrid layout: Z-order over T' x T' tiles, each tile
+ *            row-major; TU decomposition with row and column permutations.
+ *   Sec. 2   the problem: multiply sub-matrices S_A = S_B * S_C (accumulated
+ *            as S_A += S_B * S_C) of Morton-hybrid matrices over a finite field.
+ *   Sec. 2.1 aligned and contained sub-matrices; base cases on contained parts.
+ *   Sec. 2.2 Steps 1-4: recursion on the aligned parents, so every base case
+ *            multiplies parts that each lie inside one row-major tile.
+ *
+ * Naming. The library writes the update as C <- C op A*B (mod p); the paper's
+ * S_A, S_B, S_C are this C, A, B.
+ *
+ * Conventions for every entry point:
+ *   - All matrix and index pointers are DEVICE pointers owned by the caller,
+ *     unless a parameter says "host". The library never frees caller memory.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default
+ *     stream); the return code reports argument and launch errors only.
+ *     Errors raised inside a kernel (a bounded wait that expired) are read
+ *     with fm_get_last_device_status.
+ *   - Return value: FM_OK (0) or a negative fm_status.
+ *   - Residues are uint32 in [0, p); 2 <= p < 2^31. Outputs are canonical
+ *     residues in [0, p). Results are bit-exact: every algorithm returns the
+ *     same integers as the definition.
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (identical to cudaStream_t / CUstream). */
+typedef struct CUstream_st* fm_stream;
+
+typedef enum fm_status {
+    FM_OK = 0,
+    FM_EINVAL = -1,       /* bad shape, descriptor, pointer or overlap           */
+    FM_EMODULUS = -2,     /* p < 2 or p >= 2^31                                  */
+    FM_ERANGE = -3,       /* a residue >= p (only reported by validating calls)   */
+    FM_ECUDA = -4,        /* a CUDA runtime call failed                           */
+    FM_ETIMEOUT = -5,     /* a bounded device-side wait expired                   */
+    FM_ENOMEM = -6,       /* workspace allocation failed                          */
+    FM_EUNSUPPORTED = -7  /* valid request this build does not implement          */
+} fm_status;
+
+/* A Morton-hybrid matrix (Sec. 1): n x n with n = 2^log2_grid * T',
+ * T' = 2^log2_T, stored as n*n uint32 entries. Tile (I, J) (T' x T',
+ * row-major inside) starts at element Z(I, J) * T'^2, where Z interleaves the
+ * bits of I and J with the row bit more significant (quadrants NW=0, NE=1,
+ * SW=2, SE=3, Sec. 2.2 Step 1). Entry (i, j) of a tile starting at sigma is at
+ * sigma + i*T' + j (Sec. 2.1, problem P2). base must be 16-byte aligned.
+ * Limits: 0 <= log2_T <= 10, 0 <= log2_grid, n <= 2^20. */
+typedef struct fm_matrix {
+    uint32_t* base;
+    int32_t log2_grid;
+    int32_t log2_T;
+} fm_matrix;
+
+/* A sub-matrix (M, sigma, r, c) of Sec. 2.2: rows x cols starting at Cartesian
+ * (row0, col0) of m, so sigma = encode(row0, col0). Any offset is allowed
+ * (aligned or not); the part must lie inside the matrix. */
+typedef struct fm_sub {
+    fm_matrix m;
+    int64_t row0, col0, rows, cols;
+} fm_sub;
+
+typedef enum fm_op { FM_OP_SET = 0, FM_OP_ADD = 1, FM_OP_SUB = 2 } fm_op;
+
+typedef enum fm_algo {
+    FM_ALGO_AUTO = 0,      /* library choice (limb tensor-core form when it pays) */
+    FM_ALGO_PLAIN = 1,     /* CUDA-core integer GEMM with delayed reduction       */
+    FM_ALGO_LIMB_TC = 2,   /* balanced 8-bit limbs on tcgen05 tensor cores         */
+    FM_ALGO_LIMB_MMA_S8 = 3, /* reserved: legacy int8 mma.sync form (unsupported)  */
+    FM_ALGO_DFMA = 4       /* FP64 FMA with delayed reduction (exact while the
+                              accumulated sum stays below 2^53)                    */
+} fm_algo;
+
+/* Optional tuning; pass NULL for defaults. Zero fields mean "default". */
+typedef struct fm_opts {
+    int32_t k_chunk;        /* limb form: K elements per exact accumulation chunk  */
+    int32_t block_n;        /* limb form: output tile width, 128 or 256            */
+    int32_t reserved[6];
+} fm_opts;
+
+/* ---- layout and permutation (Sec. 1; HBM-bound gathers) ---------------- */
+
+/* Row-major src (rows x cols, leading dimension ld >= cols, device) into the
+ * Morton-hybrid matrix dst: dst(i, j) = src[i*ld + j] for i < rows, j < cols
+ * and 0 elsewhere (the zero padding fills the whole n x n grid).
+ * Errors: FM_EINVAL if rows or cols exceed n, ld < cols, or a pointer is
+ * null or misaligned. */
+int fm_layout_to_morton(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                        fm_matrix dst, fm_stream stream);
+
+/* Same, with TURBO's permutations applied first (Sec. 1):
+ * dst(i, j) = src[row_perm[i]*ld + col_perm[j]]; a NULL permutation is the
+ * identity. Permutation entries must lie in [0, rows) / [0, cols) (not
+ * checked on the device; out-of-range entries are undefined behaviour). */
+int fm_layout_to_morton_permuted(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                                 const int32_t* row_perm, const int32_t* col_perm,
+                                 fm_matrix dst, fm_stream stream);
+
+/* The leading rows x cols of the Morton-hybrid src into row-major dst
+ * (leading dimension ld >= cols). */
+int fm_layout_from_morton(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst, int64_t ld,
+                          fm_stream stream);
+
+/* Morton-hybrid to Morton-hybrid permutation (Sec. 1, TURBO's virtual row and
+ * column permutations made explicit): dst(i, j) = src(row_perm[i], col_perm[j])
+ * for i < rows, j < cols; the rest of dst is set to 0. src and dst must not
+ * overlap and may have different T'. NULL permutation = identity. */
+int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
+                         const int32_t* row_perm, const int32_t* col_perm, fm_stream stream);
+
+/* ---- the modular product (Sec. 2, 2.2) ---------------------------------- */
+
+/* C <- C op A*B mod p on sub-matrices: C is rows x cols, A is C.rows x K,
+ * B is K x C.cols with K = A.cols = B.rows. A and B may share a matrix; C must
+ * not overlap A or B (FM_EINVAL). All three matrices must have the same T'
+ * for FM_ALGO_PLAIN and FM_ALGO_DFMA (which run the aligned/contained tile
+ * decomposition of Sec. 2.2); the limb form accepts any T'.
+ * FM_ALGO_DFMA requires (p-1)^2 * K < 2^53 (FM_EUNSUPPORTED otherwise).
+ * Workspace (decomposition lists, limb planes) is owned by the library, cached
+ * per device and reused; the first call at a new size allocates. */
+int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, int32_t algo,
+                 const fm_opts* opts, fm_stream stream);
+
+/* Bytes of device workspace fm_gemm_modp needs for these operands and algo. */
+int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t algo,
+                                    const fm_opts* opts);
+
+/* ---- tensor-core limb form, step by step ------------------------------
+ * fm_gemm_modp with FM_ALGO_LIMB_TC runs these two steps on cached workspace.
+ * They are exposed so that a caller can split an operand once and reuse its
+ * limb planes for several products (as a TU decomposition does with a panel).
+ * The paper has no limbs (its base case is a plain triple loop over GF(2)).
+ *
+ * Limb planes. Every residue x in [0, p) is written as w balanced digits in
+ * [-128, 127] (w = least w with 256^w >= p), low digit first, of the
+ * representative r = x if x <= Hi else x - p, Hi = 127 * sum_{t<w} 256^t,
+ * so that r == x (mod p) and r = sum_t d_t 256^t. Digit t of every entry forms
+ * plane t, stored as IEEE half (exact for these integers).
+ *   role FM_LIMB_A (an M x K operand): plane t holds ceil(M/128) x ceil(K/64)
+ *     tiles in row-block-major order, each 128 rows x 64 k (16 KB).
+ *   role FM_LIMB_B (a K x N operand, stored transposed): plane t holds
+ *     ceil(N/BN) x ceil(K/64) tiles, each BN rows (n) x 64 k (BN * 128 bytes),
+ *     BN = the product's output tile width (fm_opts.block_n; default 256 when
+ *     p < 2^16 and p is odd or p < 256, else 128).
+ *   Inside a tile, row r is 128 bytes; its 16-byte chunk c (8 consecutive k)
+ *   is stored at r*128 + ((c ^ (r % 8)) * 16) (the 128-byte swizzle of the
+ *   tensor core's shared-memory operand layout). Entries past the operand's
+ *   extent are zero. Planes follow each other without gaps. */
+enum { FM_LIMB_A = 0, FM_LIMB_B = 1 };
+
+/* Bytes of the limb planes of an operand (rows x cols as the operand is
+ * used: M x K for FM_LIMB_A, K x N for FM_LIMB_B), or a negative fm_status. */
+int64_t fm_limb_planes_size(int64_t rows, int64_t cols, int32_t role, uint32_t p,
+                            const fm_opts* opts);
+
+/* Splits the sub-matrix X (Morton-hybrid, any T' and offset) into limb planes
+ * at the device pointer planes (fm_limb_planes_size bytes, 16-byte aligned). */
+int fm_limb_split(fm_sub X, int32_t role, uint32_t p, const fm_opts* opts, void* planes,
+                  fm_stream stream);
+
+/* C <- C op A*B mod p from limb planes of A (C.rows x K) and B (K x C.cols),
+ * both produced by fm_limb_split with the same p and opts. Exact: the limb
+ * products run on tcgen05 tensor cores (FP16 carrier, FP32 accumulation) in K
+ * chunks of at most 1024 (960 when the running residue is folded into the
+ * accumulator), each drained to exact integers and reduced mod p. */
+int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K, uint32_t p,
+                 int32_t op, const fm_opts* opts, fm_stream stream);
+
+/* ---- batching form (Sec. 2.2, Prop. on work and span: the base-case
+ * products are independent and may run in parallel) ---------------------- */
+
+/* One call of a batch: C <- C op A*B mod p on sub-matrices (all fields as in
+ * fm_gemm_modp). */
+typedef struct fm_gemm_call {
+    fm_sub C, A, B;
+    int32_t op;
+    int32_t reserved;
+} fm_gemm_call;
+
+typedef struct fm_plan fm_plan;
+
+/* Plans a batch of n calls (host array calls[0..n-1]) for one modulus p:
+ * decomposes every call into contained tile products (Sec. 2.2), packs them
+ * into one work list and uploads it. Calls of one batch must write disjoint
+ * C regions. The plan owns its device workspace until fm_plan_destroy. */
+int fm_plan_create(fm_plan** plan, const fm_gemm_call* calls, int64_t n, uint32_t p,
+                   int32_t algo, const fm_opts* opts);
+
+/* Runs every call of the plan in ONE persistent kernel launch on stream (its
+ * CTAs pull work items from a device queue). May be captured in a CUDA graph;
+ * the plan must outlive the graph. */
+int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream);
+
+/* Number of work items / base-case tile products in the plan (host). */
+int64_t fm_plan_work_items(const fm_plan* plan);
+
+int fm_plan_destroy(fm_plan* plan);
+
+/* ---- decomposition (host only; Sec. 2.2 Steps 1-4) ---------------------- */
+
+/* Writes the base-case products of C <- C op A*B as local index ranges
+ * (i_lo, i_hi, j_lo, j_hi, l_lo, l_hi), 6 int64 per product, into the host
+ * array out (capacity cap products). Each product multiplies parts of A, B and
+ * C that each lie inside one T' x T' tile (contained, Sec. 2.1). Returns the
+ * number of products (which may exceed cap; only cap are written) or a
+ * negative fm_status. Needs no GPU. */
+int64_t fm_decompose(fm_sub C, fm_sub A, fm_sub B, int64_t* out, int64_t cap);
+
+/* ---- status ------------------------------------------------------------- */
+
+/* Synchronises stream, returns and clears the device status word that
+ * kernels raise on an expired bounded wait (FM_OK or FM_ETIMEOUT). */
+int fm_get_last_device_status(fm_stream stream);
+
+/* Static string for a status code. */
+const char* fm_strerror(int status);
+
+/* Frees the library's cached per-device workspace (current device). */
+int fm_release_workspace(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FM_H */

@@ -1,0 +1,40 @@
+// fm_kernels.h -- launchers shared between the translation units of libfm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fm_sched.h"
+
+enum { kArithNarrow = 0, kArithWide = 1, kArithDfma = 2 };
+
+// Plain / DFMA base-case kernel over a work list (gemm_plain.cu). With a
+// non-null queue (zeroed beforehand) the grid is persistent and CTAs pull
+// items from it; otherwise CTA b processes item b.
+int fm_plain_launch(int lt, int arith, const FmCallDesc* calls, const FmWorkItem* items,
+                    const FmLPiece* lps, int64_t n_items, uint32_t p, int* queue, int grid,
+                    int* status, cudaStream_t s);
+int fm_plain_occupancy(int lt, int arith);
+
+// Limb tensor-core form (limb.cu): split A and B into balanced 8-bit limb
+// planes in the tensor-core tile layout, then the tcgen05 GEMM with the
+// recombine / reduce / combine epilogue. workspace must hold
+// fm_limb_workspace_bytes(...).
+struct FmLimbPlan {
+    int64_t M, N, K;
+    int w;            // limbs per residue
+    int block_n;      // 128 or 256
+    int fold;         // 1: residue folded into the fp32 accumulator (p < 2^16)
+    int chunk_stages; // 64-wide K stages per exact accumulation chunk
+    int MB, NB, KB;
+    size_t a_plane_bytes, b_plane_bytes;
+};
+int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
+                 FmLimbPlan* plan);
+size_t fm_limb_workspace_bytes(const FmLimbPlan& plan);
+int fm_limb_run(const FmLimbPlan& plan, fm_sub C, fm_sub A, fm_sub B, uint32_t p, int op,
+                void* workspace, int* status, cudaStream_t s);
+int fm_limb_split_run(const FmLimbPlan& plan, fm_sub X, int role, uint32_t p, void* planes,
+                      cudaStream_t s);
+int fm_limb_gemm_run(const FmLimbPlan& plan, fm_sub C, const void* a_planes,
+                     const void* b_planes, uint32_t p, int op, int* status, cudaStream_t s);

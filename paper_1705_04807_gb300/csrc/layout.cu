@@ -1,0 +1,216 @@
+// layout.cu -- row-major <-> Morton-hybrid conversion and permutations.
+//
+// Sec. 1: matrices live in the Morton-hybrid layout (Z-order over T' x T'
+// row-major tiles); TURBO needs row and column permutations, which require
+// index conversion between the curve and Cartesian order. These kernels are
+// HBM-bound gathers: each CTA walks whole tiles of the Morton matrix, so the
+// Morton side is read or written as contiguous 16-byte vectors and the
+// row-major side in row segments of T' elements.
+#include "fm_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// dst(i, j) = src[rp(i) * ld + cp(j)] (0 outside rows x cols), dst Morton.
+template <bool kPerm>
+__global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __restrict__ src,
+                                                             int64_t rows, int64_t cols, int64_t ld,
+                                                             const int32_t* __restrict__ rp,
+                                                             const int32_t* __restrict__ cp,
+                                                             uint32_t* __restrict__ dst, int lg,
+                                                             int lt)
+{
+    const int64_t tiles = (int64_t)1 << (2 * lg);
+    const int64_t tile_elems = (int64_t)1 << (2 * lt);
+    const bool vec_ok = !kPerm && lt >= 2 && ((ld & 3) == 0) && (((uintptr_t)src & 15) == 0);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t I = fm_compact_bits((uint64_t)t >> 1);
+        const uint64_t J = fm_compact_bits((uint64_t)t);
+        uint32_t* tile = dst + (t << (2 * lt));
+        const int64_t i_base = (int64_t)I << lt, j_base = (int64_t)J << lt;
+        if (lt >= 2) {
+            for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
+                const int64_t i = i_base + (e >> lt);
+                const int64_t j = j_base + (e & ((1 << lt) - 1));
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (i < rows) {
+                    if (vec_ok && j + 3 < cols) {
+                        v = __ldg(reinterpret_cast<const uint4*>(src + i * ld + j));
+                    } else {
+                        const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t jj = j + q;
+                            const int64_t sj = kPerm && cp && jj < cols ? (int64_t)__ldg(cp + jj) : jj;
+                            w[q] = jj < cols ? __ldg(src + si * ld + sj) : 0u;
+                        }
+                        v = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                *reinterpret_cast<uint4*>(tile + e) = v;
+            }
+        } else {
+            for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
+                const int64_t i = i_base + (e >> lt);
+                const int64_t j = j_base + (e & ((1 << lt) - 1));
+                uint32_t v = 0;
+                if (i < rows && j < cols) {
+                    const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
+                    const int64_t sj = kPerm && cp ? (int64_t)__ldg(cp + j) : j;
+                    v = __ldg(src + si * ld + sj);
+                }
+                tile[e] = v;
+            }
+        }
+    }
+}
+
+// dst[i * ld + j] = src(i, j) for i < rows, j < cols, src Morton.
+__global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* __restrict__ src,
+                                                               int lg, int lt, int64_t rows,
+                                                               int64_t cols,
+                                                               uint32_t* __restrict__ dst,
+                                                               int64_t ld)
+{
+    const int64_t tiles_side = (int64_t)1 << lg;
+    const int64_t T = (int64_t)1 << lt;
+    // only tiles that intersect the rows x cols corner
+    const int64_t tr = (rows + T - 1) >> lt, tc = (cols + T - 1) >> lt;
+    const int64_t ntiles = tr * tc;
+    const int64_t tile_elems = T * T;
+    const bool vec_ok = lt >= 2 && ((ld & 3) == 0) && (((uintptr_t)dst & 15) == 0);
+    (void)tiles_side;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t I = t / tc, J = t % tc;
+        const uint32_t* tile = src + fm_tile_base((uint64_t)I, (uint64_t)J, lt);
+        const int64_t i_base = I << lt, j_base = J << lt;
+        if (lt >= 2) {
+            for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
+                const int64_t i = i_base + (e >> lt);
+                const int64_t j = j_base + (e & (T - 1));
+                if (i >= rows || j >= cols) continue;
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(tile + e));
+                if (vec_ok && j + 3 < cols) {
+                    *reinterpret_cast<uint4*>(dst + i * ld + j) = v;
+                } else {
+                    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (j + q < cols) dst[i * ld + j + q] = w[q];
+                }
+            }
+        } else {
+            for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
+                const int64_t i = i_base + (e >> lt);
+                const int64_t j = j_base + (e & (T - 1));
+                if (i < rows && j < cols) dst[i * ld + j] = __ldg(tile + e);
+            }
+        }
+    }
+}
+
+// dst(i, j) = src(rp[i], cp[j]) for i < rows, j < cols, else 0; both Morton.
+__global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __restrict__ src,
+                                                           int lts, uint32_t* __restrict__ dst,
+                                                           int lgd, int ltd, int64_t rows,
+                                                           int64_t cols,
+                                                           const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ cp)
+{
+    const int64_t tiles = (int64_t)1 << (2 * lgd);
+    const int64_t tile_elems = (int64_t)1 << (2 * ltd);
+    const int64_t Td = (int64_t)1 << ltd;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t I = fm_compact_bits((uint64_t)t >> 1);
+        const uint64_t J = fm_compact_bits((uint64_t)t);
+        uint32_t* tile = dst + (t << (2 * ltd));
+        const int64_t i_base = (int64_t)I << ltd, j_base = (int64_t)J << ltd;
+        for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
+            const int64_t i = i_base + (e >> ltd);
+            const int64_t j = j_base + (e & (Td - 1));
+            uint32_t v = 0;
+            if (i < rows && j < cols) {
+                const uint64_t si = rp ? (uint64_t)__ldg(rp + i) : (uint64_t)i;
+                const uint64_t sj = cp ? (uint64_t)__ldg(cp + j) : (uint64_t)j;
+                v = __ldg(src + fm_encode(si, sj, lts));
+            }
+            tile[e] = v;
+        }
+    }
+}
+
+int grid_for(int64_t tiles)
+{
+    const int64_t cap = (int64_t)fm_sm_count() * 8;
+    return (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
+}
+
+int to_morton_impl(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                   const int32_t* rp, const int32_t* cp, fm_matrix dst, fm_stream stream)
+{
+    FM_TRY(fm_check_matrix(dst));
+    const int64_t n = fm_side(dst);
+    if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
+    if ((rows > 0 && cols > 0) && src == nullptr) return FM_EINVAL;
+    const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
+    if (rp || cp)
+        to_morton_kernel<true><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
+    else
+        to_morton_kernel<false><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+            src, rows, cols, ld, nullptr, nullptr, dst.base, dst.log2_grid, dst.log2_T);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+}  // namespace
+
+extern "C" int fm_layout_to_morton(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                                   fm_matrix dst, fm_stream stream)
+{
+    return to_morton_impl(src, rows, cols, ld, nullptr, nullptr, dst, stream);
+}
+
+extern "C" int fm_layout_to_morton_permuted(const uint32_t* src, int64_t rows, int64_t cols,
+                                            int64_t ld, const int32_t* row_perm,
+                                            const int32_t* col_perm, fm_matrix dst,
+                                            fm_stream stream)
+{
+    return to_morton_impl(src, rows, cols, ld, row_perm, col_perm, dst, stream);
+}
+
+extern "C" int fm_layout_from_morton(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst,
+                                     int64_t ld, fm_stream stream)
+{
+    FM_TRY(fm_check_matrix(src));
+    const int64_t n = fm_side(src);
+    if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
+    if (rows == 0 || cols == 0) return FM_OK;
+    if (dst == nullptr) return FM_EINVAL;
+    const int64_t T = (int64_t)1 << src.log2_T;
+    const int64_t tiles = ((rows + T - 1) / T) * ((cols + T - 1) / T);
+    from_morton_kernel<<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        src.base, src.log2_grid, src.log2_T, rows, cols, dst, ld);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
+                                    const int32_t* row_perm, const int32_t* col_perm,
+                                    fm_stream stream)
+{
+    FM_TRY(fm_check_matrix(src));
+    FM_TRY(fm_check_matrix(dst));
+    const int64_t ns = fm_side(src), nd = fm_side(dst);
+    if (rows < 0 || cols < 0 || rows > ns || cols > ns || rows > nd || cols > nd) return FM_EINVAL;
+    const uint64_t sbytes = (uint64_t)ns * ns * 4, dbytes = (uint64_t)nd * nd * 4;
+    const uintptr_t s0 = (uintptr_t)src.base, d0 = (uintptr_t)dst.base;
+    if (s0 < d0 + dbytes && d0 < s0 + sbytes) return FM_EINVAL;  // src and dst overlap
+    const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
+    permute_kernel<<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        src.base, src.log2_T, dst.base, dst.log2_grid, dst.log2_T, rows, cols, row_perm, col_perm);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}

@@ -1,0 +1,680 @@
+// limb.cu -- the tensor-core form of C <- C op A*B mod p.
+//
+// Residues are split into w balanced signed 8-bit limbs (digits in [-128, 127],
+// base 256, representative r = x if x <= Hi else x - p with
+// Hi = 127 * sum_{t<w} 256^t). Then
+//     A*B == sum_{i,j} 256^(i+j) * (A_i * B_j)      (mod p)
+// and every limb product A_i * B_j is an integer GEMM with |entry| <= 2^14.
+// GB300's tcgen05 has no integer MMA kind on sm_103a, so the 8-bit limbs are
+// carried exactly as FP16 values through tcgen05.mma kind::f16 with FP32
+// accumulation in tensor memory. FP32 holds every integer of magnitude
+// <= 2^24 exactly, so K is cut into chunks of at most 1024 (64-wide stages)
+// and each chunk's accumulator is drained into exact integers before it could
+// leave that range.
+//
+// Kernels:
+//   split_a / split_b  read the (sub-)matrices from the Morton-hybrid layout
+//                      (Sec. 1), re-base them to an aligned grid and write the
+//                      limb planes as tiles in the 128-byte-swizzled K-major
+//                      layout the MMA descriptors expect, so that each
+//                      pipeline stage is ONE contiguous 1-D bulk copy per
+//                      operand (the paper's contiguous base case, Sec. 2.1).
+//   limb_gemm          one 128 x BN output tile per CTA: a TMA producer warp,
+//                      an MMA warp (tcgen05.mma into TMEM) and four epilogue
+//                      warps that drain each accumulator chunk with
+//                      tcgen05.ld, reduce mod p and either fold the running
+//                      residue back into the accumulator (p < 2^16) or add it
+//                      to a residue region of TMEM (any p < 2^31); the final
+//                      residue is combined with C (set / add / subtract) and
+//                      written back in the Morton-hybrid layout.
+#include <cuda_fp16.h>
+
+#include "fm_internal.cuh"
+#include "fm_kernels.h"
+
+namespace {
+
+constexpr int kBM = 128;                     // output rows per CTA (TMEM lanes)
+constexpr int kBK = 64;                      // K per stage: one 128-byte swizzle row of f16
+constexpr uint32_t kATileBytes = kBM * 128;  // 16 KB
+constexpr int kSplitThreads = 256;
+constexpr int kGemmThreads = 192;            // producer, MMA, 4 epilogue warps
+
+// ---- limb digits ----------------------------------------------------------
+__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, int w, int (&d)[4])
+{
+    int32_t r = (x <= (uint32_t)hi) ? (int32_t)x : (int32_t)((int64_t)x - (int64_t)p);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (t < w) {
+            const int32_t dt = ((r + 128) & 255) - 128;
+            d[t] = dt;
+            r = (r - dt) >> 8;
+        } else {
+            d[t] = 0;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_half2(int lo, int hi)
+{
+    const __half a = __int2half_rn(lo), b = __int2half_rn(hi);
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// Byte offset of the 16-byte chunk kc (8 f16 values) of row r inside a tile
+// whose rows are 128 bytes, in the 128-byte swizzle pattern (chunk index XOR
+// row index mod 8), identical to what a TMA SWIZZLE_128B load produces.
+__device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t kc)
+{
+    return r * 128u + ((kc ^ (r & 7u)) << 4);
+}
+
+// Loads 8 consecutive entries (row gi, columns gj..gj+7) of a Morton-hybrid
+// matrix, zero outside [0, rows) x [0, cols) of the sub-matrix.
+__device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, int lt, int64_t row0,
+                                             int64_t col0, int64_t i, int64_t j, int64_t rows,
+                                             int64_t cols, uint32_t (&x)[8])
+{
+    if (i >= rows) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = 0;
+        return;
+    }
+    const uint64_t gi = (uint64_t)(row0 + i);
+    const uint64_t mask = (1ull << lt) - 1;
+    uint64_t addr = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int64_t jj = j + e;
+        const uint64_t gj = (uint64_t)(col0 + jj);
+        if (e == 0 || (gj & mask) == 0)
+            addr = fm_encode(gi, gj, lt);
+        else
+            addr += 1;
+        x[e] = jj < cols ? __ldg(base + addr) : 0u;
+    }
+}
+
+// A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
+__global__ void __launch_bounds__(kSplitThreads)
+    split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
+                   int64_t K, int KB, int w, uint32_t p, int32_t hi, uint8_t* __restrict__ planes,
+                   size_t plane_bytes)
+{
+    const int tile = blockIdx.x;
+    const int mb = tile / KB, kb = tile % KB;
+    uint8_t* out = planes + (size_t)tile * kATileBytes;
+    for (int c = threadIdx.x; c < kBM * 8; c += kSplitThreads) {
+        const int r = c >> 3, kc = c & 7;
+        uint32_t x[8];
+        load8_morton(A, lt, row0, col0, (int64_t)mb * kBM + r, (int64_t)kb * kBK + kc * 8, M, K, x);
+        int d[8][4];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) limb_digits(x[e], p, hi, w, d[e]);
+        const uint32_t off = sw128_offset(r, kc);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (t >= w) break;
+            uint4 v;
+            v.x = pack_half2(d[0][t], d[1][t]);
+            v.y = pack_half2(d[2][t], d[3][t]);
+            v.z = pack_half2(d[4][t], d[5][t]);
+            v.w = pack_half2(d[6][t], d[7][t]);
+            *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+        }
+    }
+}
+
+// B (K x N) -> w planes of [NB][KB] tiles, each BN rows (n) x 64 k f16 (B
+// transposed to K-major), swizzled. Staged through shared memory so that both
+// the Morton reads (along n) and the tile writes (along k) are coalesced.
+__global__ void __launch_bounds__(kSplitThreads)
+    split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
+                   int64_t N, int KB, int BN, int w, uint32_t p, int32_t hi,
+                   uint8_t* __restrict__ planes, size_t plane_bytes)
+{
+    extern __shared__ uint32_t sb[];  // [kBK][BN + 1]
+    const int tile = blockIdx.x;
+    const int nb = tile / KB, kb = tile % KB;
+    const int ld = BN + 1;
+    const uint64_t mask = (1ull << lt) - 1;
+    for (int idx = threadIdx.x; idx < kBK * BN; idx += kSplitThreads) {
+        const int kk = idx / BN, nn = idx % BN;
+        const int64_t gk = (int64_t)kb * kBK + kk, gn = (int64_t)nb * BN + nn;
+        uint32_t v = 0;
+        if (gk < K && gn < N) v = __ldg(B + fm_encode((uint64_t)(row0 + gk), (uint64_t)(col0 + gn), lt));
+        sb[kk * ld + nn] = v;
+    }
+    (void)mask;
+    __syncthreads();
+    uint8_t* out = planes + (size_t)tile * BN * 128;
+    for (int c = threadIdx.x; c < BN * 8; c += kSplitThreads) {
+        const int n = c % BN, kc = c / BN;
+        int d[8][4];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) limb_digits(sb[(kc * 8 + e) * ld + n], p, hi, w, d[e]);
+        const uint32_t off = sw128_offset(n, kc);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (t >= w) break;
+            uint4 v;
+            v.x = pack_half2(d[0][t], d[1][t]);
+            v.y = pack_half2(d[2][t], d[3][t]);
+            v.z = pack_half2(d[4][t], d[5][t]);
+            v.w = pack_half2(d[6][t], d[7][t]);
+            *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+        }
+    }
+}
+
+// ---- modular helpers --------------------------------------------------------
+__device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t p, uint32_t mu)
+{
+    const uint32_t q = __umulhi(x, mu);
+    uint32_t r = x - q * p;
+    return r >= p ? r - p : r;
+}
+
+__device__ __forceinline__ uint32_t barrett64(uint64_t t, uint32_t p, uint64_t mu)
+{
+    const uint64_t q = __umul64hi(t, mu);
+    uint64_t r = t - q * (uint64_t)p;
+    while (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+__device__ __forceinline__ uint32_t op_combine(uint32_t c, uint32_t s, uint32_t p, int op)
+{
+    if (op == FM_OP_SET) return s;
+    const uint32_t cc = c % p;
+    if (op == FM_OP_ADD) {
+        const uint32_t r = cc + s;
+        return r >= p ? r - p : r;
+    }
+    return cc >= s ? cc - s : cc + (p - s);
+}
+
+struct LimbGemmArgs {
+    const uint8_t* Ap;
+    const uint8_t* Bp;
+    uint64_t a_plane_bytes, b_plane_bytes;
+    int MB, NB, KB, w, chunk_stages;
+    uint32_t p, mu32, offp;
+    uint64_t mu64;
+    uint32_t wt[16];  // weight 256^(i+j) mod p of job index i*w + j
+    uint32_t cn[16];  // fold form: wt[idx] * wt[(idx + 2) % w^2]^-1 mod p
+    uint32_t* C;
+    int c_lt, op;
+    int64_t c_row0, c_col0, M, N;
+    int* status;
+};
+
+template <int BN>
+struct GemmCfg {
+    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr uint32_t kBTileBytes = BN * 128;
+    static constexpr uint32_t kStageBytes = kATileBytes + kBTileBytes;
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
+};
+
+template <int BN, bool FOLD>
+__global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGemmArgs args)
+{
+    using Cfg = GemmCfg<BN>;
+    constexpr int S = Cfg::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    __shared__ __align__(8) uint64_t full_bar[S];
+    __shared__ __align__(8) uint64_t empty_bar[S];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    __shared__ uint32_t s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // output tile, grouped raster (groups of 8 row blocks) for L2 reuse
+    const int GROUP = 8;
+    const int per_group = GROUP * args.NB;
+    const int gidx = blockIdx.x / per_group;
+    const int first_mb = gidx * GROUP;
+    const int gsz = min(args.MB - first_mb, GROUP);
+    const int inner = blockIdx.x % per_group;
+    const int mb = first_mb + inner % gsz, nb = inner / gsz;
+
+    const int w = args.w, w2 = w * w;
+    const int CS = args.chunk_stages;
+    const int n_chunks = (args.KB + CS - 1) / CS;
+    const int njobs = n_chunks * w2;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            fm_mbar_init(&full_bar[s], 1);
+            fm_mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            fm_mbar_init(&accf_bar[b], 1);
+            fm_mbar_init(&acce_bar[b], 4);
+        }
+        fm_mbar_init(&done_bar, 1);
+        fm_fence_mbar_init();
+        s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    if (warp == 1) {
+        fm_tmem_alloc(&tmem_slot, 512);
+        fm_tmem_relinquish();
+    }
+    fm_tc_fence_before();
+    __syncthreads();
+    fm_tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: one bulk copy per operand per stage ----
+            uint32_t g = 0;
+            for (int t = 0; t < njobs && !*(volatile int*)&s_abort; ++t) {
+                const int c = t / w2, idx = t % w2, i = idx / w, j = idx % w;
+                const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
+                const uint8_t* a_src = args.Ap + (size_t)i * args.a_plane_bytes +
+                                       ((size_t)mb * args.KB) * kATileBytes;
+                const uint8_t* b_src = args.Bp + (size_t)j * args.b_plane_bytes +
+                                       ((size_t)nb * args.KB) * Cfg::kBTileBytes;
+                bool ok = true;
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                    const int s = g % S;
+                    const uint32_t ph = (g / S) & 1;
+                    if (!fm_mbar_wait(&empty_bar[s], ph ^ 1, args.status, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + (size_t)s * Cfg::kStageBytes;
+                    fm_mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
+                    fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
+                    fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * Cfg::kBTileBytes,
+                                Cfg::kBTileBytes, &full_bar[s]);
+                }
+                if (!ok) break;
+            }
+            s_issued = g;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            const uint32_t idesc = fm_idesc_f16_f32(kBM, BN);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = 0; t < njobs && ok; ++t) {
+                const int b = t & 1;
+                const int c = t / w2;
+                const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
+                if (t >= 2 && !fm_mbar_wait(&acce_bar[b], ((t >> 1) - 1) & 1, args.status, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                fm_tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
+                bool first = true;
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                    const int s = g % S;
+                    const uint32_t ph = (g / S) & 1;
+                    if (!fm_mbar_wait(&full_bar[s], ph, args.status, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fm_tc_fence_after();
+                    const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * Cfg::kStageBytes);
+                    const uint32_t b_addr = a_addr + kATileBytes;
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k) {
+                        const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
+                        const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
+                        const uint32_t acc = ((FOLD && t >= 2) || !first || k > 0) ? 1u : 0u;
+                        fm_mma_f16(d_tmem, ad, bd, idesc, acc);
+                    }
+                    fm_mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+                    first = false;
+                }
+                if (!ok) break;
+                fm_mma_commit(&accf_bar[b]);  // accumulator b complete for job t
+            }
+            s_consumed = g;
+            // every MMA issued by this thread has completed before TMEM is freed
+            fm_mma_commit(&done_bar);
+            fm_mbar_wait(&done_bar, 0, args.status, nullptr);
+        }
+    } else {
+        // ---- epilogue: 4 warps, warp w reads TMEM lanes 32*(w%4) .. +31 ----
+        const int quarter = warp & 3;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const uint32_t p = args.p;
+        bool ok = true;
+        for (int t = 0; t < njobs; ++t) {
+            const int b = t & 1;
+            if (!fm_mbar_wait(&accf_bar[b], (t >> 1) & 1, args.status, &s_abort)) {
+                ok = false;
+                break;
+            }
+            fm_tc_fence_after();
+            const int idx = t % w2;
+            const bool last_on_buffer = (t + 2 >= njobs);
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                const uint32_t dcol = tmem + lane_base + (uint32_t)(b * BN + cc * 32);
+                uint32_t v[32];
+                fm_tmem_ld32(dcol, v);
+                if (FOLD) {
+                    fm_tmem_wait_ld();
+                    const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+                        const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
+                        const uint32_t y = barrett32(mul * xm, p, args.mu32);  // p < 2^16
+                        v[e] = last_on_buffer ? y : __float_as_uint((float)y);
+                    }
+                    fm_tmem_st32(dcol, v);
+                } else {
+                    const uint32_t rcol = tmem + lane_base + (uint32_t)(2 * BN + cc * 32);
+                    uint32_t r[32];
+                    fm_tmem_ld32(rcol, r);
+                    fm_tmem_wait_ld();
+                    const uint32_t wt = args.wt[idx];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+                        const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
+                        const uint32_t prev = t == 0 ? 0u : r[e];
+                        r[e] = barrett64((uint64_t)wt * xm + prev, p, args.mu64);
+                    }
+                    fm_tmem_st32(rcol, r);
+                }
+            }
+            fm_tmem_wait_st();
+            fm_tc_fence_before();
+            __syncwarp();
+            if (lane == 0) fm_mbar_arrive(&acce_bar[b]);
+        }
+
+        // final residue -> combine with C -> Morton-hybrid write
+        if (ok) {
+            const int64_t gi = (int64_t)mb * kBM + quarter * 32 + lane;
+            const uint64_t cmask = (1ull << args.c_lt) - 1;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                uint32_t s[32];
+                if (FOLD) {
+                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(cc * 32), s);
+                    if (njobs >= 2) {
+                        uint32_t s1[32];
+                        fm_tmem_ld32(tmem + lane_base + (uint32_t)(BN + cc * 32), s1);
+                        fm_tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const uint32_t x = s[e] + s1[e];
+                            s[e] = x >= p ? x - p : x;
+                        }
+                    } else {
+                        fm_tmem_wait_ld();
+                    }
+                } else {
+                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN + cc * 32), s);
+                    fm_tmem_wait_ld();
+                }
+                if (gi < args.M) {
+                    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
+                    const int64_t j0 = (int64_t)nb * BN + cc * 32;
+                    uint64_t addr = 0;
+                    for (int e = 0; e < 32; ++e) {
+                        const int64_t j = j0 + e;
+                        if (j >= args.N) break;
+                        const uint64_t cj = (uint64_t)(args.c_col0 + j);
+                        if (e == 0 || (cj & cmask) == 0)
+                            addr = fm_encode(ci, cj, args.c_lt);
+                        else
+                            addr += 1;
+                        const uint32_t old = args.op == FM_OP_SET ? 0u : args.C[addr];
+                        args.C[addr] = op_combine(old, s[e], p, args.op);
+                    }
+                }
+            }
+        }
+    }
+
+    fm_tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        // let bulk copies still in flight land before the CTA exits
+        for (uint32_t g = s_consumed; g < s_issued; ++g)
+            fm_mbar_wait(&full_bar[g % S], (g / S) & 1, args.status, nullptr);
+    }
+    if (warp == 1) {
+        fm_tc_fence_after();
+        fm_tmem_dealloc(tmem, 512);
+    }
+}
+
+uint32_t powmod(uint64_t b, uint64_t e, uint32_t p)
+{
+    uint64_t r = 1 % p;
+    b %= p;
+    while (e) {
+        if (e & 1) r = r * b % p;
+        b = b * b % p;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+// Inverse of a mod m (gcd(a, m) = 1) by the extended Euclidean algorithm.
+uint32_t invmod(uint32_t a, uint32_t m)
+{
+    int64_t t = 0, nt = 1, r = m, nr = a % m;
+    while (nr != 0) {
+        const int64_t q = r / nr;
+        int64_t tmp = t - q * nt;
+        t = nt;
+        nt = tmp;
+        tmp = r - q * nr;
+        r = nr;
+        nr = tmp;
+    }
+    if (t < 0) t += m;
+    return (uint32_t)(t % m);
+}
+
+template <int BN, bool FOLD>
+int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
+{
+    auto k = limb_gemm_kernel<BN, FOLD>;
+    const size_t smem = GemmCfg<BN>::kSmem;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, kGemmThreads, smem, s>>>(a);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+}  // namespace
+
+int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
+                 FmLimbPlan* plan)
+{
+    if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
+    FmLimbPlan q;
+    q.M = M;
+    q.N = N;
+    q.K = K;
+    int w = 1;
+    while (w < 4 && (uint64_t)1 << (8 * w) < p) ++w;
+    q.w = w;
+    q.fold = (p < (1u << 16) && (w == 1 || (p & 1))) ? 1 : 0;
+    int bn = q.fold ? 256 : 128;
+    if (opts && opts->block_n) {
+        if (opts->block_n != 128 && opts->block_n != 256) return FM_EINVAL;
+        bn = opts->block_n;
+    }
+    if (!q.fold && bn != 128) return FM_EINVAL;  // residue region needs the third TMEM slice
+    q.block_n = bn;
+    // exactness: |chunk sum| + (p - 1 if folded) must stay <= 2^24 with |limb product| <= 2^14
+    const int64_t max_k = q.fold ? ((int64_t)(1 << 24) - (int64_t)(p - 1)) / (1 << 14) : 1024;
+    int cs = (int)(max_k / kBK);
+    if (opts && opts->k_chunk) {
+        if (opts->k_chunk % kBK != 0 || opts->k_chunk / kBK > cs || opts->k_chunk <= 0)
+            return FM_EINVAL;
+        cs = opts->k_chunk / kBK;
+    }
+    if (cs < 1) return FM_EUNSUPPORTED;
+    q.chunk_stages = cs;
+    q.MB = (int)((M + kBM - 1) / kBM);
+    q.NB = (int)((N + bn - 1) / bn);
+    q.KB = (int)((K + kBK - 1) / kBK);
+    q.a_plane_bytes = (size_t)q.MB * q.KB * kATileBytes;
+    q.b_plane_bytes = (size_t)q.NB * q.KB * bn * 128;
+    *plan = q;
+    return FM_OK;
+}
+
+size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
+{
+    return (size_t)q.w * (q.a_plane_bytes + q.b_plane_bytes);
+}
+
+namespace {
+int32_t limb_hi(int w)
+{
+    int32_t hi = 0;
+    for (int t = 0; t < w; ++t) hi += 127 * (1 << (8 * t));  // 127 * sum 256^t
+    return hi;
+}
+}  // namespace
+
+int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void* planes,
+                      cudaStream_t s)
+{
+    uint8_t* out = static_cast<uint8_t*>(planes);
+    const int32_t hi = limb_hi(q.w);
+    if (role == FM_LIMB_A) {
+        if (q.MB * q.KB == 0) return FM_OK;
+        split_a_kernel<<<q.MB * q.KB, kSplitThreads, 0, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0,
+                                                             q.M, q.K, q.KB, q.w, p, hi, out,
+                                                             q.a_plane_bytes);
+    } else {
+        if (q.NB * q.KB == 0) return FM_OK;
+        const size_t sb_smem = (size_t)kBK * (q.block_n + 1) * 4;
+        FM_CUDA_TRY(cudaFuncSetAttribute(split_b_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
+        split_b_kernel<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0,
+                                                                   X.col0, q.K, q.N, q.KB, q.block_n,
+                                                                   q.w, p, hi, out, q.b_plane_bytes);
+    }
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const void* b_planes,
+                     uint32_t p, int op, int* status, cudaStream_t s)
+{
+    if (q.M == 0 || q.N == 0 || q.K == 0) return FM_OK;
+    LimbGemmArgs a;
+    a.Ap = static_cast<const uint8_t*>(a_planes);
+    a.Bp = static_cast<const uint8_t*>(b_planes);
+    a.a_plane_bytes = q.a_plane_bytes;
+    a.b_plane_bytes = q.b_plane_bytes;
+    a.MB = q.MB;
+    a.NB = q.NB;
+    a.KB = q.KB;
+    a.w = q.w;
+    a.chunk_stages = q.chunk_stages;
+    a.p = p;
+    a.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
+    a.mu64 = ~0ull / p;
+    a.offp = (uint32_t)((((uint64_t)1 << 24) + p - 1) / p * p);
+    const int w2 = q.w * q.w;
+    for (int idx = 0; idx < 16; ++idx) {
+        a.wt[idx] = 0;
+        a.cn[idx] = 0;
+    }
+    for (int idx = 0; idx < w2; ++idx) {
+        const int i = idx / q.w, j = idx % q.w;
+        a.wt[idx] = powmod(256, (uint64_t)(i + j), p);
+    }
+    if (q.fold) {
+        for (int idx = 0; idx < w2; ++idx) {
+            const uint32_t inv = invmod(a.wt[(idx + 2) % w2], p);
+            a.cn[idx] = (uint32_t)((uint64_t)a.wt[idx] * inv % p);
+        }
+    }
+    a.C = C.m.base;
+    a.c_lt = C.m.log2_T;
+    a.op = op;
+    a.c_row0 = C.row0;
+    a.c_col0 = C.col0;
+    a.M = q.M;
+    a.N = q.N;
+    a.status = status;
+    const int grid = q.MB * q.NB;
+    if (q.fold) {
+        if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);
+        return launch_gemm<128, true>(a, grid, s);
+    }
+    return launch_gemm<128, false>(a, grid, s);
+}
+
+int fm_limb_run(const FmLimbPlan& q, fm_sub C, fm_sub A, fm_sub B, uint32_t p, int op,
+                void* workspace, int* status, cudaStream_t s)
+{
+    if (q.M == 0 || q.N == 0) return FM_OK;
+    uint8_t* Ap = static_cast<uint8_t*>(workspace);
+    uint8_t* Bp = Ap + (size_t)q.w * q.a_plane_bytes;
+    FM_TRY(fm_limb_split_run(q, A, FM_LIMB_A, p, Ap, s));
+    FM_TRY(fm_limb_split_run(q, B, FM_LIMB_B, p, Bp, s));
+    return fm_limb_gemm_run(q, C, Ap, Bp, p, op, status, s);
+}
+
+// ---- C entry points of the step-by-step limb form --------------------------
+extern "C" int64_t fm_limb_planes_size(int64_t rows, int64_t cols, int32_t role, uint32_t p,
+                                       const fm_opts* opts)
+{
+    if (rows < 0 || cols < 0) return FM_EINVAL;
+    if (role != FM_LIMB_A && role != FM_LIMB_B) return FM_EINVAL;
+    FmLimbPlan q;
+    // A is M x K; B is K x N
+    const int rc = role == FM_LIMB_A ? fm_limb_plan(rows, 1, cols, p, opts, &q)
+                                     : fm_limb_plan(1, cols, rows, p, opts, &q);
+    if (rc != FM_OK) return rc;
+    return (int64_t)q.w * (int64_t)(role == FM_LIMB_A ? q.a_plane_bytes : q.b_plane_bytes);
+}
+
+extern "C" int fm_limb_split(fm_sub X, int32_t role, uint32_t p, const fm_opts* opts, void* planes,
+                             fm_stream stream)
+{
+    if (role != FM_LIMB_A && role != FM_LIMB_B) return FM_EINVAL;
+    FM_TRY(fm_check_sub(X));
+    if (!planes || ((uintptr_t)planes & 15)) return FM_EINVAL;
+    FmLimbPlan q;
+    FM_TRY(role == FM_LIMB_A ? fm_limb_plan(X.rows, 1, X.cols, p, opts, &q)
+                             : fm_limb_plan(1, X.cols, X.rows, p, opts, &q));
+    return fm_limb_split_run(q, X, role, p, planes, (cudaStream_t)stream);
+}
+
+extern "C" int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K,
+                            uint32_t p, int32_t op, const fm_opts* opts, fm_stream stream)
+{
+    if (op < FM_OP_SET || op > FM_OP_SUB || K < 0) return FM_EINVAL;
+    FM_TRY(fm_check_sub(C));
+    if (((uintptr_t)a_planes & 15) || ((uintptr_t)b_planes & 15)) return FM_EINVAL;
+    FmLimbPlan q;
+    FM_TRY(fm_limb_plan(C.rows, C.cols, K, p, opts, &q));
+    if (C.rows == 0 || C.cols == 0) return FM_OK;
+    if (K == 0) return FM_EUNSUPPORTED;  // nothing to multiply: use fm_gemm_modp
+    if (!a_planes || !b_planes) return FM_EINVAL;
+    int* status = fm_device_status();
+    if (!status) return FM_ECUDA;
+    return fm_limb_gemm_run(q, C, a_planes, b_planes, p, op, status, (cudaStream_t)stream);
+}

@@ -1,0 +1,283 @@
+"""ctypes binding of libfm (include/fm.h): the same entry points, argument
+marshalling only. Every computation runs in the library's CUDA kernels; if the
+library is missing this module raises instead of falling back to anything.
+
+Pointers may be given as ints or as objects with ``data_ptr()`` (torch
+tensors); streams as ints, ``torch.cuda.Stream`` objects, or None for the
+current torch stream (legacy default stream when torch is not loaded).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfm.so")
+
+FM_OK, FM_EINVAL, FM_EMODULUS, FM_ERANGE, FM_ECUDA, FM_ETIMEOUT, FM_ENOMEM, FM_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+FM_OP_SET, FM_OP_ADD, FM_OP_SUB = 0, 1, 2
+FM_ALGO_AUTO, FM_ALGO_PLAIN, FM_ALGO_LIMB_TC, FM_ALGO_LIMB_MMA_S8, FM_ALGO_DFMA = 0, 1, 2, 3, 4
+FM_LIMB_A, FM_LIMB_B = 0, 1
+
+# Every symbol include/fm.h declares.
+EXPORTS = (
+    "fm_layout_to_morton", "fm_layout_to_morton_permuted", "fm_layout_from_morton",
+    "fm_permute_rows_cols", "fm_gemm_modp", "fm_gemm_modp_workspace_size", "fm_plan_create",
+    "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_destroy", "fm_decompose",
+    "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
+    "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm",
+)
+
+
+class FmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class fm_matrix(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_void_p), ("log2_grid", ctypes.c_int32),
+                ("log2_T", ctypes.c_int32)]
+
+
+class fm_sub(ctypes.Structure):
+    _fields_ = [("m", fm_matrix), ("row0", ctypes.c_int64), ("col0", ctypes.c_int64),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64)]
+
+
+class fm_opts(ctypes.Structure):
+    _fields_ = [("k_chunk", ctypes.c_int32), ("block_n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class fm_gemm_call(ctypes.Structure):
+    _fields_ = [("C", fm_sub), ("A", fm_sub), ("B", fm_sub), ("op", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libfm (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfm.so not found at {LIB_PATH}; build it with "
+                          "python -c 'import __graft_entry__ as g; g.build()'")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "fm_layout_to_morton": ([P, I64, I64, I64, fm_matrix, P], ctypes.c_int),
+        "fm_layout_to_morton_permuted": ([P, I64, I64, I64, P, P, fm_matrix, P], ctypes.c_int),
+        "fm_layout_from_morton": ([fm_matrix, I64, I64, P, I64, P], ctypes.c_int),
+        "fm_permute_rows_cols": ([fm_matrix, fm_matrix, I64, I64, P, P, P], ctypes.c_int),
+        "fm_gemm_modp": ([fm_sub, fm_sub, fm_sub, U32, I32, I32, ctypes.POINTER(fm_opts), P],
+                         ctypes.c_int),
+        "fm_gemm_modp_workspace_size": ([fm_sub, fm_sub, fm_sub, U32, I32,
+                                         ctypes.POINTER(fm_opts)], I64),
+        "fm_plan_create": ([ctypes.POINTER(P), ctypes.POINTER(fm_gemm_call), I64, U32, I32,
+                            ctypes.POINTER(fm_opts)], ctypes.c_int),
+        "fm_gemm_modp_batched": ([P, P], ctypes.c_int),
+        "fm_plan_work_items": ([P], I64),
+        "fm_plan_destroy": ([P], ctypes.c_int),
+        "fm_decompose": ([fm_sub, fm_sub, fm_sub, ctypes.POINTER(ctypes.c_int64), I64], I64),
+        "fm_get_last_device_status": ([P], ctypes.c_int),
+        "fm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "fm_release_workspace": ([], ctypes.c_int),
+        "fm_version": ([], ctypes.c_int),
+        "fm_limb_planes_size": ([I64, I64, I32, U32, ctypes.POINTER(fm_opts)], I64),
+        "fm_limb_split": ([fm_sub, I32, U32, ctypes.POINTER(fm_opts), P, P], ctypes.c_int),
+        "fm_limb_gemm": ([fm_sub, P, P, I64, U32, I32, ctypes.POINTER(fm_opts), P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().fm_strerror(int(code)).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != FM_OK:
+        raise FmError(rc, where)
+    return rc
+
+
+def matrix(base, log2_grid: int, log2_T: int) -> fm_matrix:
+    return fm_matrix(_ptr(base), int(log2_grid), int(log2_T))
+
+
+def sub(m: fm_matrix, row0: int, col0: int, rows: int, cols: int) -> fm_sub:
+    return fm_sub(m, int(row0), int(col0), int(rows), int(cols))
+
+
+def opts(k_chunk: int = 0, block_n: int = 0) -> fm_opts:
+    o = fm_opts()
+    o.k_chunk = int(k_chunk)
+    o.block_n = int(block_n)
+    return o
+
+
+# ---- entry points (same names as include/fm.h) ----------------------------
+def fm_layout_to_morton(src, rows, cols, ld, dst: fm_matrix, stream=None):
+    return _check(lib().fm_layout_to_morton(_ptr(src), rows, cols, ld, dst, _stream(stream)),
+                  "fm_layout_to_morton")
+
+
+def fm_layout_to_morton_permuted(src, rows, cols, ld, row_perm, col_perm, dst: fm_matrix,
+                                 stream=None):
+    return _check(lib().fm_layout_to_morton_permuted(_ptr(src), rows, cols, ld, _ptr(row_perm),
+                                                     _ptr(col_perm), dst, _stream(stream)),
+                  "fm_layout_to_morton_permuted")
+
+
+def fm_layout_from_morton(src: fm_matrix, rows, cols, dst, ld, stream=None):
+    return _check(lib().fm_layout_from_morton(src, rows, cols, _ptr(dst), ld, _stream(stream)),
+                  "fm_layout_from_morton")
+
+
+def fm_permute_rows_cols(src: fm_matrix, dst: fm_matrix, rows, cols, row_perm, col_perm,
+                         stream=None):
+    return _check(lib().fm_permute_rows_cols(src, dst, rows, cols, _ptr(row_perm),
+                                             _ptr(col_perm), _stream(stream)),
+                  "fm_permute_rows_cols")
+
+
+def fm_gemm_modp(C: fm_sub, A: fm_sub, B: fm_sub, p: int, op: int = FM_OP_SUB,
+                 algo: int = FM_ALGO_AUTO, options: fm_opts | None = None, stream=None):
+    o = ctypes.byref(options) if options is not None else None
+    return _check(lib().fm_gemm_modp(C, A, B, int(p), int(op), int(algo), o, _stream(stream)),
+                  "fm_gemm_modp")
+
+
+def fm_gemm_modp_workspace_size(C: fm_sub, A: fm_sub, B: fm_sub, p: int,
+                                algo: int = FM_ALGO_AUTO, options: fm_opts | None = None) -> int:
+    o = ctypes.byref(options) if options is not None else None
+    r = int(lib().fm_gemm_modp_workspace_size(C, A, B, int(p), int(algo), o))
+    if r < 0:
+        raise FmError(r, "fm_gemm_modp_workspace_size")
+    return r
+
+
+class Plan:
+    """Owns an fm_plan (fm_plan_create / fm_plan_destroy)."""
+
+    def __init__(self, calls, p: int, algo: int = FM_ALGO_AUTO, options: fm_opts | None = None):
+        arr = (fm_gemm_call * len(calls))(*calls)
+        h = ctypes.c_void_p()
+        o = ctypes.byref(options) if options is not None else None
+        _check(lib().fm_plan_create(ctypes.byref(h), arr, len(calls), int(p), int(algo), o),
+               "fm_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        return fm_gemm_modp_batched(self, stream)
+
+    @property
+    def work_items(self) -> int:
+        return int(lib().fm_plan_work_items(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().fm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fm_plan_create(calls, p: int, algo: int = FM_ALGO_AUTO, options=None) -> Plan:
+    return Plan(calls, p, algo, options)
+
+
+def fm_gemm_modp_batched(plan: Plan, stream=None):
+    return _check(lib().fm_gemm_modp_batched(plan.handle, _stream(stream)), "fm_gemm_modp_batched")
+
+
+def fm_plan_destroy(plan: Plan):
+    plan.close()
+    return FM_OK
+
+
+def fm_decompose(C: fm_sub, A: fm_sub, B: fm_sub):
+    """Base-case products as a list of (i_lo, i_hi, j_lo, j_hi, l_lo, l_hi)."""
+    n = int(lib().fm_decompose(C, A, B, None, 0))
+    if n < 0:
+        raise FmError(n, "fm_decompose")
+    buf = (ctypes.c_int64 * (6 * max(n, 1)))()
+    n2 = int(lib().fm_decompose(C, A, B, buf, n))
+    return [tuple(buf[6 * t:6 * t + 6]) for t in range(n2)]
+
+
+def fm_limb_planes_size(rows, cols, role, p, options: fm_opts | None = None) -> int:
+    o = ctypes.byref(options) if options is not None else None
+    r = int(lib().fm_limb_planes_size(rows, cols, role, int(p), o))
+    if r < 0:
+        raise FmError(r, "fm_limb_planes_size")
+    return r
+
+
+def fm_limb_split(X: fm_sub, role: int, p: int, planes, options: fm_opts | None = None,
+                  stream=None):
+    o = ctypes.byref(options) if options is not None else None
+    return _check(lib().fm_limb_split(X, int(role), int(p), o, _ptr(planes), _stream(stream)),
+                  "fm_limb_split")
+
+
+def fm_limb_gemm(C: fm_sub, a_planes, b_planes, K: int, p: int, op: int = FM_OP_SUB,
+                 options: fm_opts | None = None, stream=None):
+    o = ctypes.byref(options) if options is not None else None
+    return _check(lib().fm_limb_gemm(C, _ptr(a_planes), _ptr(b_planes), int(K), int(p), int(op),
+                                     o, _stream(stream)), "fm_limb_gemm")
+
+
+def fm_get_last_device_status(stream=None) -> int:
+    return int(lib().fm_get_last_device_status(_stream(stream)))
+
+
+def fm_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def fm_release_workspace():
+    return _check(lib().fm_release_workspace(), "fm_release_workspace")
+
+
+def fm_version() -> int:
+    return int(lib().fm_version())

@@ -1,0 +1,89 @@
+"""The C ABI: the library loads, exports every symbol include/fm.h declares, and
+its host-only decomposition (Sec. 2.2) matches the oracle's recursion. No GPU."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+import fm_inputs
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import __graft_entry__
+    from paper_1705_04807_gb300 import build
+    build.build()
+    import paper_1705_04807_gb300 as fm
+    fm.lib()
+    return fm
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fm_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol(fm):
+    declared = declared_functions()
+    assert {"fm_gemm_modp", "fm_layout_to_morton", "fm_layout_from_morton",
+            "fm_permute_rows_cols", "fm_gemm_modp_batched"} <= declared
+    lib = fm.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(fm.EXPORTS)
+
+
+def test_version_and_strerror(fm):
+    assert fm.fm_version() == 100
+    assert "modulus" in fm.fm_strerror(fm.FM_EMODULUS)
+    assert fm.fm_strerror(0) == "ok"
+
+
+def _subs(fm, n_lg, lt, rect):
+    M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rect)
+    fake = 1 << 20  # host-only call: any aligned non-null base, distinct per matrix
+    mC, mA, mB = fm.matrix(fake, n_lg, lt), fm.matrix(2 * fake, n_lg, lt), fm.matrix(3 * fake, n_lg, lt)
+    return fm.sub(mC, rC, cC, M, N), fm.sub(mA, rA, cA, M, K), fm.sub(mB, rB, cB, K, N)
+
+
+@pytest.mark.parametrize("lg,lt", [(2, 1), (3, 1), (2, 2), (1, 3)])
+def test_decomposition_matches_oracle_recursion(fm, lg, lt):
+    from oracle import recursion
+    T = 1 << lt
+    n = (1 << lg) * T
+    for rect in fm_inputs.sub_rectangles(lg * 7 + lt, 20, n):
+        C, A, B = _subs(fm, lg, lt, rect)
+        got = sorted(fm.fm_decompose(C, A, B))
+        M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rect)
+        # paper naming: S_A (output) = C, S_B = A, S_C = B
+        leaves = recursion.leaves(lg, T, (rC, cC, M, N), (rA, cA, M, K), (rB, cB, K, N))
+        want = sorted((l.i_lo, l.i_hi, l.j_lo, l.j_hi, l.l_lo, l.l_hi) for l in leaves)
+        assert got == want
+
+
+def test_decompose_rejects_bad_operands(fm):
+    mC, mA = fm.matrix(1 << 20, 2, 5), fm.matrix(2 << 20, 2, 5)
+    with pytest.raises(fm.FmError):
+        fm.fm_decompose(fm.sub(mC, 0, 0, 10, 10), fm.sub(mA, 0, 0, 11, 4), fm.sub(mA, 0, 0, 4, 10))
+    with pytest.raises(fm.FmError):   # outside the matrix
+        fm.fm_decompose(fm.sub(mC, 120, 0, 10, 10), fm.sub(mA, 0, 0, 10, 4), fm.sub(mA, 0, 0, 4, 10))
+    with pytest.raises(fm.FmError):   # C overlaps A
+        fm.fm_decompose(fm.sub(mC, 0, 0, 10, 10), fm.sub(mC, 5, 5, 10, 4), fm.sub(mA, 0, 0, 4, 10))
+    with pytest.raises(fm.FmError):   # different T'
+        fm.fm_decompose(fm.sub(mC, 0, 0, 10, 10), fm.sub(fm.matrix(2 << 20, 3, 4), 0, 0, 10, 4),
+                        fm.sub(mA, 0, 0, 4, 10))
+
+
+def test_aligned_decomposition_is_one_product_per_tile_triple(fm):
+    C, A, B = _subs(fm, 3, 5, (128, 64, 96, 32, 64, 0, 32, 64, 0))
+    assert len(fm.fm_decompose(C, A, B)) == (128 // 32) * (64 // 32) * (96 // 32)

@@ -1,0 +1,111 @@
+"""GPU parity of the batching form: many uneven calls in one persistent launch
+(Sec. 2.2, Prop. on work and span: the base-case products are independent)."""
+import numpy as np
+import pytest
+
+import fm_inputs
+from gpu_util import MortonMatrix, lib_and_device
+
+pytestmark = pytest.mark.gpu
+
+P16 = 65521
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_and_device()
+
+
+def make_batch(fm, dev, count, seed, lt=6, lo=32, hi=512, block=512, big=4096):
+    """count calls with M, N, K uniform in [lo, hi]; call c writes its own
+    block x block cell of C (disjoint), A and B parts are random rectangles of
+    shared matrices (reads may overlap)."""
+    cells = big // block
+    assert count <= cells * cells
+    lg = 0
+    while (1 << lg) << lt < big:
+        lg += 1
+    Cf = fm_inputs.uniform_residues(seed, (big, big), P16, 1)
+    Af = fm_inputs.uniform_residues(seed, (big, big), P16, 2)
+    Bf = fm_inputs.uniform_residues(seed, (big, big), P16, 3)
+    MC = MortonMatrix(fm, dev, lg, lt, fill=Cf)
+    MA = MortonMatrix(fm, dev, lg, lt, fill=Af)
+    MB = MortonMatrix(fm, dev, lg, lt, fill=Bf)
+    shapes = fm_inputs.batch_shapes(seed, count, lo, hi)
+    offs = fm_inputs.raw_u64(seed, 6 * count, 9).reshape(count, 6)
+    calls, meta = [], []
+    for c in range(count):
+        M, N, K = (int(x) for x in shapes[c])
+        cr, cc = (c // cells) * block, (c % cells) * block
+        cr += int(offs[c, 0]) % (block - M + 1)
+        cc += int(offs[c, 1]) % (block - N + 1)
+        ar, ac = int(offs[c, 2]) % (big - M + 1), int(offs[c, 3]) % (big - K + 1)
+        br, bc = int(offs[c, 4]) % (big - K + 1), int(offs[c, 5]) % (big - N + 1)
+        op = c % 3
+        call = fm.fm_gemm_call()
+        call.C, call.A, call.B = MC.sub(cr, cc, M, N), MA.sub(ar, ac, M, K), MB.sub(br, bc, K, N)
+        call.op = op
+        calls.append(call)
+        meta.append((M, N, K, cr, cc, ar, ac, br, bc, op))
+    return MC, MA, MB, Cf, Af, Bf, calls, meta
+
+
+def expected(orc, Cf, Af, Bf, meta, times=1):
+    want = Cf.copy()
+    for (M, N, K, cr, cc, ar, ac, br, bc, op) in meta:
+        blk = want[cr:cr + M, cc:cc + N]
+        for _ in range(times):
+            blk = orc.gemm_modp(blk, Af[ar:ar + M, ac:ac + K], Bf[br:br + K, bc:bc + N], P16, op)
+        want[cr:cr + M, cc:cc + N] = blk
+    return want
+
+
+@pytest.mark.parametrize("lt", [5, 6])
+def test_batched_matches_oracle_and_per_call(env, orc, lt):
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 48, seed=lt, lt=lt)
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_PLAIN)
+    assert plan.work_items > 0
+    saved = MC.t.clone()
+    plan.run()
+    got = MC.read()
+    assert fm.fm_get_last_device_status() == 0
+    assert np.array_equal(got, expected(orc, Cf, Af, Bf, meta))
+    # one launch per call gives the same integers
+    MC.t.copy_(saved)
+    for call in calls:
+        fm.fm_gemm_modp(call.C, call.A, call.B, P16, call.op, fm.FM_ALGO_PLAIN)
+    assert np.array_equal(MC.read(), got)
+    plan.close()
+
+
+def test_batched_graph_capture_and_replay(env, orc):
+    import torch
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 16, seed=9)
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_AUTO)
+    fm.fm_get_last_device_status()  # device status word exists before capture
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    torch.cuda.synchronize()
+    assert np.array_equal(MC.read(), Cf)  # capture does not execute
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(MC.read(), expected(orc, Cf, Af, Bf, meta, times=2))
+    plan.close()
+
+
+def test_empty_plan_and_errors(env):
+    fm, dev = env
+    plan = fm.fm_plan_create([], P16)
+    assert plan.work_items == 0
+    plan.run()
+    plan.close()
+    M = MortonMatrix(fm, dev, 1, 6)
+    call = fm.fm_gemm_call()
+    call.C, call.A, call.B = M.sub(0, 0, 8, 8), M.sub(8, 8, 8, 8), M.sub(4, 4, 8, 8)  # overlap
+    with pytest.raises(fm.FmError):
+        fm.fm_plan_create([call], P16)

@@ -1,0 +1,95 @@
+"""GPU parity of the layout and permutation kernels against the oracle (bit-exact)."""
+import numpy as np
+import pytest
+
+import fm_inputs
+from gpu_util import MortonMatrix, lib_and_device, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_and_device()
+
+
+@pytest.mark.parametrize("rows,cols,ld,lg,lt", [
+    (37, 53, 53, 2, 4), (64, 64, 64, 0, 6), (1, 1, 1, 0, 0), (5, 3, 7, 3, 0), (9, 15, 17, 3, 1),
+    (130, 250, 251, 1, 7), (300, 301, 304, 3, 6), (1000, 17, 20, 5, 5), (0, 0, 1, 1, 2)])
+def test_to_and_from_morton(env, orc, rows, cols, ld, lg, lt):
+    fm, dev = env
+    import torch
+    x = fm_inputs.uniform_residues(rows * 7 + cols, (rows, ld), 65521)
+    M = MortonMatrix(fm, dev, lg, lt)
+    M.t.fill_(-1)  # padding must be overwritten with zeros
+    fm.fm_layout_to_morton(to_dev(x, dev) if x.size else 0, rows, cols, ld, M.m)
+    got = to_host(M.t)
+    want = orc.to_morton(x[:, :cols], lg, 1 << lt)
+    assert np.array_equal(got, want)
+    if rows and cols:
+        out = torch.full((rows, ld), -1, dtype=torch.int32, device=dev)
+        fm.fm_layout_from_morton(M.m, rows, cols, out, ld)
+        back = to_host(out)
+        assert np.array_equal(back[:, :cols], x[:, :cols])
+        assert np.all(back[:, cols:] == 0xFFFFFFFF)  # columns beyond cols untouched
+
+
+@pytest.mark.parametrize("rows,cols,lg,lt", [(37, 53, 2, 4), (300, 170, 3, 6), (64, 64, 0, 6)])
+def test_to_morton_permuted(env, orc, rows, cols, lg, lt):
+    fm, dev = env
+    x = fm_inputs.uniform_residues(3, (rows, cols), 65521)
+    rp = fm_inputs.permutation(3, rows, 1)
+    cp = fm_inputs.permutation(3, cols, 2)
+    for r, c in ((rp, cp), (rp, None), (None, cp)):
+        M = MortonMatrix(fm, dev, lg, lt)
+        fm.fm_layout_to_morton_permuted(to_dev(x, dev), rows, cols, cols,
+                                        None if r is None else to_dev(r, dev),
+                                        None if c is None else to_dev(c, dev), M.m)
+        want = orc.to_morton(orc.permute(x, r, c), lg, 1 << lt)
+        assert np.array_equal(to_host(M.t), want)
+
+
+@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", [(100, 90, 2, 5, 1, 6), (33, 47, 3, 3, 1, 5),
+                                                        (128, 128, 1, 6, 1, 6)])
+def test_permute_rows_cols(env, orc, rows, cols, lgs, lts, lgd, ltd):
+    fm, dev = env
+    ns = (1 << lgs) << lts
+    x = fm_inputs.uniform_residues(5, (ns, ns), 2147483647)
+    S = MortonMatrix(fm, dev, lgs, lts, fill=x)
+    D = MortonMatrix(fm, dev, lgd, ltd)
+    D.t.fill_(-1)
+    rp = fm_inputs.permutation(5, rows, 1)
+    cp = fm_inputs.permutation(5, cols, 2)
+    fm.fm_permute_rows_cols(S.m, D.m, rows, cols, to_dev(rp, dev), to_dev(cp, dev))
+    nd = (1 << lgd) << ltd
+    canvas = np.zeros((nd, nd), dtype=np.uint32)
+    canvas[:rows, :cols] = orc.permute(x[:rows, :cols], rp, cp)
+    assert np.array_equal(to_host(D.t), orc.to_morton(canvas, lgd, 1 << ltd))
+
+
+def test_layout_errors(env):
+    fm, dev = env
+    M = MortonMatrix(fm, dev, 1, 5)
+    import torch
+    src = torch.zeros(100 * 100, dtype=torch.int32, device=dev)
+    with pytest.raises(fm.FmError):
+        fm.fm_layout_to_morton(src, 65, 10, 10, M.m)      # more rows than the grid
+    with pytest.raises(fm.FmError):
+        fm.fm_layout_to_morton(src, 10, 10, 5, M.m)       # ld < cols
+    with pytest.raises(fm.FmError):
+        fm.fm_permute_rows_cols(M.m, M.m, 10, 10, None, None)  # src == dst
+
+
+def test_config2_layout_full_size(env, orc):
+    # 3000 x 1700 and 1700 x 2200 row-major residues, random row and column
+    # permutations, converted to Morton-hybrid 4096 x 4096 grids at T' = 64.
+    fm, dev = env
+    p = 65521
+    for (rows, cols, seed) in ((3000, 1700, 11), (1700, 2200, 12)):
+        x = fm_inputs.uniform_residues(seed, (rows, cols), p)
+        rp = fm_inputs.permutation(seed, rows, 1)
+        cp = fm_inputs.permutation(seed, cols, 2)
+        M = MortonMatrix(fm, dev, 6, 6)
+        fm.fm_layout_to_morton_permuted(to_dev(x, dev), rows, cols, cols, to_dev(rp, dev),
+                                        to_dev(cp, dev), M.m)
+        assert np.array_equal(to_host(M.t), orc.to_morton(orc.permute(x, rp, cp), 6, 64))
