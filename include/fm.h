@@ -47,7 +47,8 @@ typedef enum fm_status {
     FM_ECUDA = -4,        /* a CUDA runtime call failed                           */
     FM_ETIMEOUT = -5,     /* a bounded device-side wait expired                   */
     FM_ENOMEM = -6,       /* workspace allocation failed                          */
-    FM_EUNSUPPORTED = -7  /* valid request this build does not implement          */
+    FM_EUNSUPPORTED = -7, /* valid request this build does not implement          */
+    FM_ETOOBIG = -8       /* larger than the fixed scratch of fm_gemm_modp_noalloc */
 } fm_status;
 
 /* A Morton-hybrid matrix (Sec. 1): n x n with n = 2^log2_grid * T',
@@ -176,6 +177,29 @@ int fm_limb_split(fm_sub X, int32_t role, uint32_t p, const fm_opts* opts, void*
  * accumulator), each drained to exact integers and reduced mod p. */
 int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K, uint32_t p,
                  int32_t op, const fm_opts* opts, fm_stream stream);
+
+/* ---- the limb product without allocation ----------------------------------
+ * The paper has no counterpart: this is a library service. fm_gemm_modp
+ * allocates its limb-plane workspace with cudaMalloc on first use. Callers that
+ * must not allocate -- code running while a CUDA graph is captured, or
+ * programs whose device memory comes only from their own allocator or a fixed
+ * budget -- use this entry point instead. It computes exactly what
+ * fm_gemm_modp with FM_ALGO_LIMB_TC computes (C <- C op A*B mod p on
+ * Morton-hybrid sub-matrices, any T', default fm_opts) and allocates nothing:
+ * its scratch is a fixed device array of 64 MiB of limb planes plus a status
+ * word, compiled into the library (every GPU that loads it holds that array
+ * until the process exits). A product whose limb planes need more than 64 MiB
+ * returns FM_ETOOBIG (e.g. M = N = K = 2048 fits for p < 2^16; for
+ * p = 2^31 - 1 the planes take 16 * K * (M + N) bytes rounded up to tiles).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the one array, so calls that can overlap on the GPU (different streams
+ * without ordering) race and must be serialised by the caller; the array
+ * keeps the last call's contents, and every call rewrites all of it that it
+ * reads. A device-side wait that expires is recorded in the array's own status
+ * word, which each call clears and no entry point reads: callers that need
+ * that report use fm_gemm_modp and fm_get_last_device_status. */
+int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, fm_stream stream);
 
 /* ---- batching form (Sec. 2.2, Prop. on work and span: the base-case
  * products are independent and may run in parallel) ---------------------- */

@@ -402,6 +402,7 @@ extern "C" const char* fm_strerror(int status)
     case FM_ETIMEOUT: return "bounded device wait expired";
     case FM_ENOMEM: return "out of device memory";
     case FM_EUNSUPPORTED: return "unsupported configuration";
+    case FM_ETOOBIG: return "product too large for the fixed scratch of fm_gemm_modp_noalloc";
     default: return "unknown status";
     }
 }

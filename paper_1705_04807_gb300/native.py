@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfm.so")
 
 FM_OK, FM_EINVAL, FM_EMODULUS, FM_ERANGE, FM_ECUDA, FM_ETIMEOUT, FM_ENOMEM, FM_EUNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6, -7)
+FM_ETOOBIG = -8
 FM_OP_SET, FM_OP_ADD, FM_OP_SUB = 0, 1, 2
 FM_ALGO_AUTO, FM_ALGO_PLAIN, FM_ALGO_LIMB_TC, FM_ALGO_LIMB_MMA_S8, FM_ALGO_DFMA = 0, 1, 2, 3, 4
 FM_LIMB_A, FM_LIMB_B = 0, 1
@@ -27,7 +28,7 @@ EXPORTS = (
     "fm_permute_rows_cols", "fm_gemm_modp", "fm_gemm_modp_workspace_size", "fm_plan_create",
     "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_destroy", "fm_decompose",
     "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
-    "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm",
+    "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
 )
 
 
@@ -92,6 +93,7 @@ def lib():
         "fm_limb_planes_size": ([I64, I64, I32, U32, ctypes.POINTER(fm_opts)], I64),
         "fm_limb_split": ([fm_sub, I32, U32, ctypes.POINTER(fm_opts), P, P], ctypes.c_int),
         "fm_limb_gemm": ([fm_sub, P, P, I64, U32, I32, ctypes.POINTER(fm_opts), P], ctypes.c_int),
+        "fm_gemm_modp_noalloc": ([fm_sub, fm_sub, fm_sub, U32, I32, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -181,6 +183,14 @@ def fm_gemm_modp(C: fm_sub, A: fm_sub, B: fm_sub, p: int, op: int = FM_OP_SUB,
     o = ctypes.byref(options) if options is not None else None
     return _check(lib().fm_gemm_modp(C, A, B, int(p), int(op), int(algo), o, _stream(stream)),
                   "fm_gemm_modp")
+
+
+def fm_gemm_modp_noalloc(C: fm_sub, A: fm_sub, B: fm_sub, p: int, op: int = FM_OP_SUB,
+                         stream=None):
+    """The limb product with no device allocation (fixed 64 MiB scratch; see
+    include/fm.h). Raises FmError(FM_ETOOBIG) for larger products."""
+    return _check(lib().fm_gemm_modp_noalloc(C, A, B, int(p), int(op), _stream(stream)),
+                  "fm_gemm_modp_noalloc")
 
 
 def fm_gemm_modp_workspace_size(C: fm_sub, A: fm_sub, B: fm_sub, p: int,
