@@ -8,7 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fm.h"
+#include "fm.h"
 
 #define FM_VERSION_NUM 100  // 0.1.0
 

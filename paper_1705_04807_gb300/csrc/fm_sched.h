@@ -19,7 +19,7 @@
 
 #include <vector>
 
-#include "../../include/fm.h"
+#include "fm.h"
 
 // Device view of one call: matrix bases and parameters.
 struct FmCallDesc {

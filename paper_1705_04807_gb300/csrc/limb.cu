@@ -203,7 +203,9 @@ struct LimbGemmArgs {
     uint32_t p, mu32, offp;
     uint64_t mu64;
     uint32_t wt[16];  // weight 256^(i+j) mod p of job index i*w + j
-    uint32_t cn[16];  // fold form: wt[idx] * wt[(idx + 2) % w^2]^-1 mod p
+    uint32_t cn[16];  // fold form: cn[idx * 4 + idx2] = wt[idx] * wt[idx2]^-1 mod p
+    float invp, pf;   // fold form: 1/p and p as float
+    uint64_t offs64;  // residue form: multiple of p >= 2^31 (makes an int32 sum non-negative)
     uint32_t* C;
     int c_lt, op;
     int64_t c_row0, c_col0, M, N;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             // ---- producer: one bulk copy per operand per stage ----
             uint32_t g = 0;
             for (int t = 0; t < njobs && !*(volatile int*)&s_abort; ++t) {
-                const int c = t / w2, idx = t % w2, i = idx / w, j = idx % w;
+                const int c = t % n_chunks, idx = t / n_chunks, i = idx / w, j = idx % w;
                 const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
                 const uint8_t* a_src = args.Ap + (size_t)i * args.a_plane_bytes +
                                        ((size_t)mb * args.KB) * kATileBytes;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             bool ok = true;
             for (int t = 0; t < njobs && ok; ++t) {
                 const int b = t & 1;
-                const int c = t / w2;
+                const int c = t % n_chunks;
                 const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
                 if (t >= 2 && !fm_mbar_wait(&acce_bar[b], ((t >> 1) - 1) & 1, args.status, &s_abort)) {
                     ok = false;
@@ -362,8 +364,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 break;
             }
             fm_tc_fence_after();
-            const int idx = t % w2;
+            const int idx = t / n_chunks, c = t % n_chunks;
             const bool last_on_buffer = (t + 2 >= njobs);
+            // fold form: the job two steps later on this buffer continues the
+            // same limb product (same weight) unless a product boundary lies between
+            const int idx2 = last_on_buffer ? idx : (t + 2) / n_chunks;
+            const bool same_next = !last_on_buffer && idx2 == idx;
+            // residue form: S (exact int32 sum of this product's chunks) is
+            // folded into R at the product's last chunk and every 120 chunks
+            const bool s_fresh = (c % 120) == 0;
+            const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 const uint32_t dcol = tmem + lane_base + (uint32_t)(b * BN + cc * 32);
@@ -371,29 +381,54 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 fm_tmem_ld32(dcol, v);
                 if (FOLD) {
                     fm_tmem_wait_ld();
-                    const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx];
+                    if (same_next) {
+                        // exact: |v| < 2^24, so v - rint(v/p)*p is computed without rounding
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
-                        const uint32_t y = barrett32(mul * xm, p, args.mu32);  // p < 2^16
-                        v[e] = last_on_buffer ? y : __float_as_uint((float)y);
+                        for (int e = 0; e < 32; ++e) {
+                            const float f = __uint_as_float(v[e]);
+                            const float q = rintf(f * args.invp);
+                            v[e] = __float_as_uint(fmaf(-q, args.pf, f));
+                        }
+                    } else {
+                        const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+                            const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
+                            const uint32_t y = barrett32(mul * xm, p, args.mu32);  // p < 2^16
+                            v[e] = last_on_buffer ? y : __float_as_uint((float)y);
+                        }
                     }
                     fm_tmem_st32(dcol, v);
                 } else {
-                    const uint32_t rcol = tmem + lane_base + (uint32_t)(2 * BN + cc * 32);
-                    uint32_t r[32];
-                    fm_tmem_ld32(rcol, r);
+                    const uint32_t scol = tmem + lane_base + (uint32_t)(3 * BN + cc * 32);
+                    uint32_t sv[32];
+                    if (!s_fresh) fm_tmem_ld32(scol, sv);
                     fm_tmem_wait_ld();
-                    const uint32_t wt = args.wt[idx];
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const int32_t d = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
-                        const uint32_t prev = t == 0 ? 0u : r[e];
-                        r[e] = barrett64((uint64_t)wt * xm + prev, p, args.mu64);
+                        sv[e] = (uint32_t)((s_fresh ? 0 : (int32_t)sv[e]) + d);
                     }
-                    fm_tmem_st32(rcol, r);
+                    if (fold_now) {
+                        const uint32_t rcol = tmem + lane_base + (uint32_t)(2 * BN + cc * 32);
+                        uint32_t r[32];
+                        const bool r_fresh = (idx == 0 && c < 120);
+                        if (!r_fresh) {
+                            fm_tmem_ld32(rcol, r);
+                            fm_tmem_wait_ld();
+                        }
+                        const uint32_t wt = args.wt[idx];
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const uint64_t x = (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
+                            const uint32_t xm = barrett64(x, p, args.mu64);
+                            r[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : r[e]), p, args.mu64);
+                        }
+                        fm_tmem_st32(rcol, r);
+                    } else {
+                        fm_tmem_st32(scol, sv);
+                    }
                 }
             }
             fm_tmem_wait_st();
@@ -430,17 +465,45 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 if (gi < args.M) {
                     const uint64_t ci = (uint64_t)(args.c_row0 + gi);
                     const int64_t j0 = (int64_t)nb * BN + cc * 32;
-                    uint64_t addr = 0;
-                    for (int e = 0; e < 32; ++e) {
-                        const int64_t j = j0 + e;
-                        if (j >= args.N) break;
-                        const uint64_t cj = (uint64_t)(args.c_col0 + j);
-                        if (e == 0 || (cj & cmask) == 0)
-                            addr = fm_encode(ci, cj, args.c_lt);
-                        else
-                            addr += 1;
-                        const uint32_t old = args.op == FM_OP_SET ? 0u : args.C[addr];
-                        args.C[addr] = op_combine(old, s[e], p, args.op);
+                    const uint64_t cj0 = (uint64_t)(args.c_col0 + j0);
+                    const uint64_t base = fm_encode(ci, cj0, args.c_lt);
+                    // the 32 columns form one contiguous run of a Morton tile row
+                    const bool run = j0 + 32 <= args.N && (cj0 & cmask) + 32 <= cmask + 1 &&
+                                     (base & 3) == 0;
+                    if (run) {
+                        uint4* dst = reinterpret_cast<uint4*>(args.C + base);
+                        uint4 old[8];
+                        if (args.op != FM_OP_SET) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) old[q] = dst[q];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            uint4 o = args.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
+                            o.x = op_combine(o.x, s[4 * q + 0], p, args.op);
+                            o.y = op_combine(o.y, s[4 * q + 1], p, args.op);
+                            o.z = op_combine(o.z, s[4 * q + 2], p, args.op);
+                            o.w = op_combine(o.w, s[4 * q + 3], p, args.op);
+                            dst[q] = o;
+                        }
+                    } else {
+                        // ragged edge or a tile boundary inside the run: gather the
+                        // addresses, then all loads, then all stores
+                        uint64_t addr[32];
+                        uint32_t old[32];
+                        uint64_t a = base;
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const uint64_t cj = cj0 + e;
+                            if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
+                            addr[e] = a;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            old[e] = (args.op != FM_OP_SET && j0 + e < args.N) ? args.C[addr[e]] : 0u;
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (j0 + e < args.N) args.C[addr[e]] = op_combine(old[e], s[e], p, args.op);
                     }
                 }
             }
@@ -519,10 +582,11 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
         if (opts->block_n != 128 && opts->block_n != 256) return FM_EINVAL;
         bn = opts->block_n;
     }
-    if (!q.fold && bn != 128) return FM_EINVAL;  // residue region needs the third TMEM slice
+    if (!q.fold && bn != 128) return FM_EINVAL;  // residue and sum regions need TMEM slices 3, 4
     q.block_n = bn;
-    // exactness: |chunk sum| + (p - 1 if folded) must stay <= 2^24 with |limb product| <= 2^14
-    const int64_t max_k = q.fold ? ((int64_t)(1 << 24) - (int64_t)(p - 1)) / (1 << 14) : 1024;
+    // exactness: |chunk sum| + |folded residue| (at most 2p) must stay <= 2^24
+    // with |limb product| <= 2^14
+    const int64_t max_k = q.fold ? ((int64_t)(1 << 24) - 2 * (int64_t)p) / (1 << 14) : 1024;
     int cs = (int)(max_k / kBK);
     if (opts && opts->k_chunk) {
         if (opts->k_chunk % kBK != 0 || opts->k_chunk / kBK > cs || opts->k_chunk <= 0)
@@ -605,11 +669,15 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
         a.wt[idx] = powmod(256, (uint64_t)(i + j), p);
     }
     if (q.fold) {
-        for (int idx = 0; idx < w2; ++idx) {
-            const uint32_t inv = invmod(a.wt[(idx + 2) % w2], p);
-            a.cn[idx] = (uint32_t)((uint64_t)a.wt[idx] * inv % p);
-        }
+        for (int idx = 0; idx < w2; ++idx)
+            for (int idx2 = 0; idx2 < w2; ++idx2) {
+                const uint32_t inv = invmod(a.wt[idx2], p);
+                a.cn[idx * 4 + idx2] = (uint32_t)((uint64_t)a.wt[idx] * inv % p);
+            }
     }
+    a.invp = 1.0f / (float)p;
+    a.pf = (float)p;
+    a.offs64 = ((((uint64_t)1 << 31) + p - 1) / p) * (uint64_t)p;
     a.C = C.m.base;
     a.c_lt = C.m.log2_T;
     a.op = op;
