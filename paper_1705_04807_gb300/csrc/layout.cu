@@ -23,11 +23,22 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
 {
     const int64_t tiles = (int64_t)1 << (2 * lg);
     const int64_t tile_elems = (int64_t)1 << (2 * lt);
-    const bool vec_ok = !kPerm && lt >= 2 && ((ld & 3) == 0) && (((uintptr_t)src & 15) == 0);
+    // 16-byte row segments whenever no column permutation scatters them
+    const bool vec_ok = (!kPerm || cp == nullptr) && lt >= 2 && ((ld & 3) == 0) &&
+                        (((uintptr_t)src & 15) == 0);
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t I = fm_compact_bits((uint64_t)t >> 1);
-        const uint64_t J = fm_compact_bits((uint64_t)t);
-        uint32_t* tile = dst + (t << (2 * lt));
+        // Z order keeps the Morton writes sequential; with a column permutation
+        // the reads are a random gather inside each source row, so tiles are
+        // walked row band by row band to keep one band of source rows in L2.
+        uint64_t I, J;
+        if (kPerm) {
+            I = (uint64_t)t >> lg;
+            J = (uint64_t)t & ((1ull << lg) - 1);
+        } else {
+            I = fm_compact_bits((uint64_t)t >> 1);
+            J = fm_compact_bits((uint64_t)t);
+        }
+        uint32_t* tile = dst + fm_tile_base(I, J, lt);
         const int64_t i_base = (int64_t)I << lt, j_base = (int64_t)J << lt;
         if (lt >= 2) {
             for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
@@ -35,10 +46,10 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
                 const int64_t j = j_base + (e & ((1 << lt) - 1));
                 uint4 v = make_uint4(0, 0, 0, 0);
                 if (i < rows) {
+                    const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
                     if (vec_ok && j + 3 < cols) {
-                        v = __ldg(reinterpret_cast<const uint4*>(src + i * ld + j));
+                        v = __ldg(reinterpret_cast<const uint4*>(src + si * ld + j));
                     } else {
-                        const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
                         uint32_t w[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {

@@ -71,7 +71,8 @@ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t kc)
 }
 
 // Loads 8 consecutive entries (row gi, columns gj..gj+7) of a Morton-hybrid
-// matrix, zero outside [0, rows) x [0, cols) of the sub-matrix.
+// matrix, zero outside [0, rows) x [0, cols) of the sub-matrix. When the 8
+// entries are one aligned run inside a tile row they come as two 16-byte loads.
 __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, int lt, int64_t row0,
                                              int64_t col0, int64_t i, int64_t j, int64_t rows,
                                              int64_t cols, uint32_t (&x)[8])
@@ -83,15 +84,21 @@ __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, 
     }
     const uint64_t gi = (uint64_t)(row0 + i);
     const uint64_t mask = (1ull << lt) - 1;
-    uint64_t addr = 0;
+    const uint64_t gj0 = (uint64_t)(col0 + j);
+    const uint64_t a0 = fm_encode(gi, gj0, lt);
+    if (j + 8 <= cols && (gj0 & mask) + 8 <= mask + 1 && (a0 & 3) == 0) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(base + a0));
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + a0) + 1);
+        x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+        x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+        return;
+    }
+    uint64_t addr = a0;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int64_t jj = j + e;
-        const uint64_t gj = (uint64_t)(col0 + jj);
-        if (e == 0 || (gj & mask) == 0)
-            addr = fm_encode(gi, gj, lt);
-        else
-            addr += 1;
+        const uint64_t gj = gj0 + e;
+        if (e > 0) addr = ((gj & mask) == 0) ? fm_encode(gi, gj, lt) : addr + 1;
         x[e] = jj < cols ? __ldg(base + addr) : 0u;
     }
 }
@@ -128,32 +135,44 @@ __global__ void __launch_bounds__(kSplitThreads)
 
 // B (K x N) -> w planes of [NB][KB] tiles, each BN rows (n) x 64 k f16 (B
 // transposed to K-major), swizzled. Staged through shared memory so that both
-// the Morton reads (along n) and the tile writes (along k) are coalesced.
+// the Morton reads (along n, 16-byte vectors) and the tile writes (along k)
+// are coalesced.
+template <int BN>
 __global__ void __launch_bounds__(kSplitThreads)
     split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
-                   int64_t N, int KB, int BN, int w, uint32_t p, int32_t hi,
+                   int64_t N, int KB, int w, uint32_t p, int32_t hi,
                    uint8_t* __restrict__ planes, size_t plane_bytes)
 {
-    extern __shared__ uint32_t sb[];  // [kBK][BN + 1]
+    extern __shared__ __align__(16) uint32_t sb[];  // [kBK][BN]
     const int tile = blockIdx.x;
     const int nb = tile / KB, kb = tile % KB;
-    const int ld = BN + 1;
     const uint64_t mask = (1ull << lt) - 1;
-    for (int idx = threadIdx.x; idx < kBK * BN; idx += kSplitThreads) {
-        const int kk = idx / BN, nn = idx % BN;
+    for (int idx = threadIdx.x; idx < kBK * BN / 4; idx += kSplitThreads) {
+        const int kk = idx / (BN / 4), nn = (idx % (BN / 4)) * 4;
         const int64_t gk = (int64_t)kb * kBK + kk, gn = (int64_t)nb * BN + nn;
-        uint32_t v = 0;
-        if (gk < K && gn < N) v = __ldg(B + fm_encode((uint64_t)(row0 + gk), (uint64_t)(col0 + gn), lt));
-        sb[kk * ld + nn] = v;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gk < K) {
+            const uint64_t gi = (uint64_t)(row0 + gk), gj = (uint64_t)(col0 + gn);
+            const uint64_t a = fm_encode(gi, gj, lt);
+            if (gn + 4 <= N && (gj & mask) + 4 <= mask + 1 && (a & 3) == 0) {
+                v = __ldg(reinterpret_cast<const uint4*>(B + a));
+            } else {
+                uint32_t t[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    t[q] = gn + q < N ? __ldg(B + fm_encode(gi, gj + q, lt)) : 0u;
+                v = make_uint4(t[0], t[1], t[2], t[3]);
+            }
+        }
+        *reinterpret_cast<uint4*>(sb + kk * BN + nn) = v;
     }
-    (void)mask;
     __syncthreads();
     uint8_t* out = planes + (size_t)tile * BN * 128;
     for (int c = threadIdx.x; c < BN * 8; c += kSplitThreads) {
         const int n = c % BN, kc = c / BN;
         int d[8][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) limb_digits(sb[(kc * 8 + e) * ld + n], p, hi, w, d[e]);
+        for (int e = 0; e < 8; ++e) limb_digits(sb[(kc * 8 + e) * BN + n], p, hi, w, d[e]);
         const uint32_t off = sw128_offset(n, kc);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -630,12 +649,11 @@ int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void*
                                                              q.a_plane_bytes);
     } else {
         if (q.NB * q.KB == 0) return FM_OK;
-        const size_t sb_smem = (size_t)kBK * (q.block_n + 1) * 4;
-        FM_CUDA_TRY(cudaFuncSetAttribute(split_b_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
-        split_b_kernel<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0,
-                                                                   X.col0, q.K, q.N, q.KB, q.block_n,
-                                                                   q.w, p, hi, out, q.b_plane_bytes);
+        const size_t sb_smem = (size_t)kBK * q.block_n * 4;
+        auto k = q.block_n == 256 ? split_b_kernel<256> : split_b_kernel<128>;
+        FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
+        k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N,
+                                                      q.KB, q.w, p, hi, out, q.b_plane_bytes);
     }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
