@@ -40,12 +40,13 @@ N_DEFAULT = 8192
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fm", choices=["fm", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip plain / DFMA comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-GEMM measurement")
     return ap.parse_args()
 
 
@@ -223,6 +224,86 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5):
+    """The batching form: count independent calls C_c -= A_c * B_c mod p with
+    M, N, K uniform in [lo, hi], each on its own cell of a large Morton C and
+    on random rectangles of shared Morton A and B (T' = 64). One persistent
+    launch (fm_gemm_modp_batched) against one fm_gemm_modp launch per call;
+    both results are checked equal."""
+    import numpy as np
+
+    import fm_inputs
+    p = P
+    lt, cell = 6, hi
+    cells = 1
+    while cells * cells < count:
+        cells *= 2
+    big = 16384
+    lgA = (big >> lt).bit_length() - 1
+    lgC = ((cells * cell) >> lt).bit_length() - 1
+    A = torch.from_numpy(fm_inputs.uniform_residues(seed, (big, big), p, 1).view(np.int32)).to(dev)
+    B = torch.from_numpy(fm_inputs.uniform_residues(seed, (big, big), p, 2).view(np.int32)).to(dev)
+    tA = torch.empty(big * big, dtype=torch.int32, device=dev)
+    tB = torch.empty_like(tA)
+    mA, mB = fm.matrix(tA, lgA, lt), fm.matrix(tB, lgA, lt)
+    fm.fm_layout_to_morton(A, big, big, big, mA)
+    fm.fm_layout_to_morton(B, big, big, big, mB)
+    del A, B
+    nC = cells * cell
+    tC = torch.zeros(nC * nC, dtype=torch.int32, device=dev)
+    mC = fm.matrix(tC, lgC, lt)
+    shapes = fm_inputs.batch_shapes(seed, count, lo, hi)
+    offs = fm_inputs.raw_u64(seed, 4 * count, 9).reshape(count, 4)
+    calls = []
+    ops = 0.0
+    for c in range(count):
+        M, N, K = (int(x) for x in shapes[c])
+        call = fm.fm_gemm_call()
+        call.C = fm.sub(mC, (c // cells) * cell, (c % cells) * cell, M, N)
+        call.A = fm.sub(mA, int(offs[c, 0]) % (big - M + 1), int(offs[c, 1]) % (big - K + 1), M, K)
+        call.B = fm.sub(mB, int(offs[c, 2]) % (big - K + 1), int(offs[c, 3]) % (big - N + 1), K, N)
+        call.op = fm.FM_OP_SUB
+        calls.append(call)
+        ops += 2.0 * M * N * K
+    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_PLAIN)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    for _ in range(2):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        plan.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / reps
+    snap = tC.clone()
+    for call in calls:  # one launch per call, from the same state
+        fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_PLAIN, None, stream)
+    per_call_result = tC.clone()
+    tC.copy_(snap)
+    plan.run(stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(tC, per_call_result))
+    del per_call_result
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for call in calls:
+            fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_PLAIN, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_call_ms = e0.elapsed_time(e1) / reps
+    items = plan.work_items
+    plan.close()
+    del tA, tB, tC, snap
+    return {"workload": f"{count} calls C -= A*B mod {p}, M,N,K ~ U[{lo},{hi}], T'=64, plain form",
+            "value": ops / (batched_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": batched_ms,
+            "per_call_ms": per_call_ms, "per_call_value": ops / (per_call_ms / 1e3) / 1e9,
+            "speedup_vs_per_call": per_call_ms / batched_ms, "work_items": items,
+            "launches": 1, "per_call_launches": count, "bit_identical_to_per_call": same}
+
+
 def run_fm(args, world, rank, local):
     import numpy as np
     import torch
@@ -419,6 +500,10 @@ def run_fm(args, world, rank, local):
                          "ms_per_step": ms / steps, "bit_identical_to_limb": same}
         del tA6, tB6, tC6
 
+    # ---- batching form: 4096 independent GEMMs, M, N, K uniform in [32, 512] ----
+    if not args.no_batched:
+        out["batched"] = run_batched(fm, torch, dev, stream, args)
+
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
     burst, sustained, hbm, src = measured_peaks()
     gemm_ms = sorted(kern["limb_gemm"])[len(kern["limb_gemm"]) // 2]
@@ -451,6 +536,8 @@ def run_fm(args, world, rank, local):
         "roofline": roofline,
         "kernels_ms": {k: sum(v) / len(v) for k, v in kern.items()},
     }
+    if "batched" in out:
+        line["batched"] = out["batched"]
     if "plain" in out:
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]

@@ -6,6 +6,8 @@
 // HBM-bound gathers: each CTA walks whole tiles of the Morton matrix, so the
 // Morton side is read or written as contiguous 16-byte vectors and the
 // row-major side in row segments of T' elements.
+#include <algorithm>
+
 #include "fm_internal.cuh"
 
 namespace {
@@ -75,6 +77,43 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
                 tile[e] = v;
             }
         }
+    }
+}
+
+// Column-permuted conversion: dst(i, j) = src[rp(i) * ld + cp(j)]. Each CTA
+// stages a whole source row in shared memory with coalesced 16-byte loads,
+// gathers the permuted columns from shared memory and writes the destination
+// row as contiguous runs of T' entries (one per Morton tile it crosses), so
+// HBM sees one read and one write per element.
+__global__ void __launch_bounds__(kThreads)
+    to_morton_rowgather_kernel(const uint32_t* __restrict__ src, int64_t rows, int64_t cols,
+                               int64_t ld, const int32_t* __restrict__ rp,
+                               const int32_t* __restrict__ cp, uint32_t* __restrict__ dst, int lg,
+                               int lt)
+{
+    extern __shared__ __align__(16) uint32_t srow[];
+    const int64_t n = (int64_t)1 << (lg + lt);
+    const bool vec = ((ld & 3) == 0) && (((uintptr_t)src & 15) == 0);
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        if (i < rows) {
+            const uint32_t* sr = src + (rp ? (int64_t)__ldg(rp + i) : i) * ld;
+            const int64_t c4 = vec ? cols / 4 : 0;
+            for (int64_t q = threadIdx.x; q < c4; q += kThreads)
+                *reinterpret_cast<uint4*>(srow + 4 * q) = __ldg(reinterpret_cast<const uint4*>(sr) + q);
+            for (int64_t j = 4 * c4 + threadIdx.x; j < cols; j += kThreads) srow[j] = __ldg(sr + j);
+        }
+        __syncthreads();
+        for (int64_t j = 4 * (int64_t)threadIdx.x; j < n; j += 4 * kThreads) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (i < rows) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j + q < cols) w[q] = srow[__ldg(cp + j + q)];
+            }
+            *reinterpret_cast<uint4*>(dst + fm_encode((uint64_t)i, (uint64_t)j, lt)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncthreads();
     }
 }
 
@@ -166,7 +205,15 @@ int to_morton_impl(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
     if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
     if ((rows > 0 && cols > 0) && src == nullptr) return FM_EINVAL;
     const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
-    if (rp || cp)
+    const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
+    if (cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
+        const int64_t n = fm_side(dst);
+        const int grid = (int)std::min<int64_t>(n, (int64_t)fm_sm_count() * 8);
+        FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        to_morton_rowgather_kernel<<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
+            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
+    } else if (rp || cp)
         to_morton_kernel<true><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
     else
