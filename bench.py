@@ -94,7 +94,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -508,14 +508,16 @@ def run_fm(args, world, rank, local):
     burst, sustained, hbm, src = measured_peaks()
     gemm_ms = sorted(kern["limb_gemm"])[len(kern["limb_gemm"]) // 2]
     gemm_avg = sum(kern["limb_gemm"]) / len(kern["limb_gemm"])
-    mma_flops = 2.0 * n * n * n * w * w
+    n_products = 3  # Karatsuba on two limbs: A0B0, (A0+A1)(B0+B1), A1B1
+    mma_flops = 2.0 * n * n * n * n_products
     achieved = mma_flops / (gemm_avg / 1e3) / 1e12
     traffic = profiled_traffic(os.path.join(ROOT, "paper_1705_04807_gb300", "csrc", "limb.cu"),
                                "limb_gemm_n8192.md")
     roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                 "frac": achieved / sustained, "traffic": traffic,
                 "kernel": "limb_gemm_kernel<256,fold>",
-                "work": f"2*M*N*K*w^2 f16 MMA flops per launch (w={w} limbs), n={n}",
+                "work": f"2*M*N*K*{n_products} f16 MMA flops per launch ({n_products} limb "
+                        f"products: Karatsuba on w={w} limbs), n={n}",
                 "peak_source": f"bf16 sustained, {src} (f16 = bf16 rate)",
                 "modular_gops": ops / (gemm_avg / 1e3) / 1e9}
 

@@ -87,7 +87,8 @@ typedef enum fm_algo {
 typedef struct fm_opts {
     int32_t k_chunk;        /* limb form: K elements per exact accumulation chunk  */
     int32_t block_n;        /* limb form: output tile width, 128 or 256            */
-    int32_t reserved[6];
+    int32_t no_karatsuba;   /* limb form: 1 = four limb products instead of three  */
+    int32_t reserved[5];
 } fm_opts;
 
 /* ---- layout and permutation (Sec. 1; HBM-bound gathers) ---------------- */
@@ -147,7 +148,10 @@ int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uint32_t p, in
  * [-128, 127] (w = least w with 256^w >= p), low digit first, of the
  * representative r = x if x <= Hi else x - p, Hi = 127 * sum_{t<w} 256^t,
  * so that r == x (mod p) and r = sum_t d_t 256^t. Digit t of every entry forms
- * plane t, stored as IEEE half (exact for these integers).
+ * plane t, stored as IEEE half (exact for these integers). When w = 2, p < 2^16
+ * is odd and fm_opts.no_karatsuba is 0, a third plane holds d_0 + d_1 and the
+ * product runs three limb GEMMs (Karatsuba: A*B = (1-256) A0*B0
+ * + 256 (A0+A1)*(B0+B1) + (2^16-256) A1*B1) instead of four.
  *   role FM_LIMB_A (an M x K operand): plane t holds ceil(M/128) x ceil(K/64)
  *     tiles in row-block-major order, each 128 rows x 64 k (16 KB).
  *   role FM_LIMB_B (a K x N operand, stored transposed): plane t holds
@@ -189,8 +193,9 @@ int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K
  * its scratch is a fixed device array of 64 MiB of limb planes plus a status
  * word, compiled into the library (every GPU that loads it holds that array
  * until the process exits). A product whose limb planes need more than 64 MiB
- * returns FM_ETOOBIG (e.g. M = N = K = 2048 fits for p < 2^16; for
- * p = 2^31 - 1 the planes take 16 * K * (M + N) bytes rounded up to tiles).
+ * returns FM_ETOOBIG (e.g. M = N = K = 2048 fits for p < 2^16; the planes take
+ * 6 * K * (M + N) bytes for odd p < 2^16 with three planes, 8 * K * (M + N) for
+ * p = 2^31 - 1, rounded up to whole tiles).
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture. All calls share
  * the one array, so calls that can overlap on the GPU (different streams

@@ -23,11 +23,15 @@ int fm_plain_occupancy(int lt, int arith);
 struct FmLimbPlan {
     int64_t M, N, K;
     int w;            // limbs per residue
+    int n_planes;     // planes per operand: w, or 3 with Karatsuba (d0, d1, d0 + d1; w = 2)
+    int n_products;   // limb products the GEMM runs
+    int prod_a[16], prod_b[16];  // plane of A and of B multiplied by product k
+    int prod_cs[16];             // 64-wide K stages per exact chunk of product k
+    uint32_t prod_w[16];         // weight of product k, mod p
     int block_n;      // 128 or 256
     int fold;         // 1: residue folded into the fp32 accumulator (p < 2^16)
-    int chunk_stages; // 64-wide K stages per exact accumulation chunk
     int MB, NB, KB;
-    size_t a_plane_bytes, b_plane_bytes;
+    size_t a_plane_bytes, b_plane_bytes;  // bytes of ONE plane
 };
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan);

@@ -29,6 +29,8 @@
 //                      written back in the Morton-hybrid layout.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "fm_internal.cuh"
 #include "fm_kernels.h"
 
@@ -38,7 +40,8 @@ constexpr int kBM = 128;                     // output rows per CTA (TMEM lanes)
 constexpr int kBK = 64;                      // K per stage: one 128-byte swizzle row of f16
 constexpr uint32_t kATileBytes = kBM * 128;  // 16 KB
 constexpr int kSplitThreads = 256;
-constexpr int kGemmThreads = 192;            // producer, MMA, 4 epilogue warps
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 
 // ---- limb digits ----------------------------------------------------------
 __device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, int w, int (&d)[4])
@@ -106,8 +109,8 @@ __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, 
 // A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
 __global__ void __launch_bounds__(kSplitThreads)
     split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
-                   int64_t K, int KB, int w, uint32_t p, int32_t hi, uint8_t* __restrict__ planes,
-                   size_t plane_bytes)
+                   int64_t K, int KB, int w, int n_planes, uint32_t p, int32_t hi,
+                   uint8_t* __restrict__ planes, size_t plane_bytes)
 {
     const int tile = blockIdx.x;
     const int mb = tile / KB, kb = tile % KB;
@@ -122,13 +125,18 @@ __global__ void __launch_bounds__(kSplitThreads)
         const uint32_t off = sw128_offset(r, kc);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            if (t >= w) break;
-            uint4 v;
-            v.x = pack_half2(d[0][t], d[1][t]);
-            v.y = pack_half2(d[2][t], d[3][t]);
-            v.z = pack_half2(d[4][t], d[5][t]);
-            v.w = pack_half2(d[6][t], d[7][t]);
-            *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+            if (t < n_planes) {
+                int q[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
+                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
+                uint4 v;
+                v.x = pack_half2(q[0], q[1]);
+                v.y = pack_half2(q[2], q[3]);
+                v.z = pack_half2(q[4], q[5]);
+                v.w = pack_half2(q[6], q[7]);
+                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+            }
         }
     }
 }
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(kSplitThreads)
 template <int BN>
 __global__ void __launch_bounds__(kSplitThreads)
     split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
-                   int64_t N, int KB, int w, uint32_t p, int32_t hi,
+                   int64_t N, int KB, int w, int n_planes, uint32_t p, int32_t hi,
                    uint8_t* __restrict__ planes, size_t plane_bytes)
 {
     extern __shared__ __align__(16) uint32_t sb[];  // [kBK][BN]
@@ -176,13 +184,18 @@ __global__ void __launch_bounds__(kSplitThreads)
         const uint32_t off = sw128_offset(n, kc);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            if (t >= w) break;
-            uint4 v;
-            v.x = pack_half2(d[0][t], d[1][t]);
-            v.y = pack_half2(d[2][t], d[3][t]);
-            v.z = pack_half2(d[4][t], d[5][t]);
-            v.w = pack_half2(d[6][t], d[7][t]);
-            *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+            if (t < n_planes) {
+                int q[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
+                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
+                uint4 v;
+                v.x = pack_half2(q[0], q[1]);
+                v.y = pack_half2(q[2], q[3]);
+                v.z = pack_half2(q[4], q[5]);
+                v.w = pack_half2(q[6], q[7]);
+                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
+            }
         }
     }
 }
@@ -218,11 +231,14 @@ struct LimbGemmArgs {
     const uint8_t* Ap;
     const uint8_t* Bp;
     uint64_t a_plane_bytes, b_plane_bytes;
-    int MB, NB, KB, w, chunk_stages;
+    int MB, NB, KB, n_products;
+    int pa[16], pb[16];  // planes of A and B of product k
+    int cs[16];          // 64-wide K stages per chunk of product k
+    int first[17];       // first job of product k; first[n_products] = number of jobs
     uint32_t p, mu32, offp;
     uint64_t mu64;
-    uint32_t wt[16];  // weight 256^(i+j) mod p of job index i*w + j
-    uint32_t cn[16];  // fold form: cn[idx * 4 + idx2] = wt[idx] * wt[idx2]^-1 mod p
+    uint32_t wt[16];  // weight of product k mod p
+    uint32_t cn[16];  // fold form: cn[k * 4 + k2] = wt[k] * wt[k2]^-1 mod p
     float invp, pf;   // fold form: 1/p and p as float
     uint64_t offs64;  // residue form: multiple of p >= 2^31 (makes an int32 sum non-negative)
     uint32_t* C;
@@ -230,6 +246,77 @@ struct LimbGemmArgs {
     int64_t c_row0, c_col0, M, N;
     int* status;
 };
+
+// Fold-form drains. fold_fp: v - rint(v/p) p in FP32, exact because |v| < 2^24
+// (the result stays a carried value of magnitude <= 2p). fold_int: the value
+// times mul mod p, as a float to carry on (to_float) or as the final residue.
+__device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
+{
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const float f = __uint_as_float(v[e]);
+        const float q = rintf(f * invp);
+        v[e] = __float_as_uint(fmaf(-q, pf, f));
+    }
+}
+
+__device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
+                                         uint32_t mu32, uint32_t offp)
+{
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+        const uint32_t xm = barrett32((uint32_t)d + offp, p, mu32);
+        const uint32_t y = barrett32(mul * xm, p, mu32);  // p < 2^16
+        v[e] = to_float ? __float_as_uint((float)y) : y;
+    }
+}
+
+// C(gi, j0 .. j0+31) <- C op sres (mod p), in the Morton-hybrid layout. Loads
+// are issued before stores; a run inside one tile row moves as 16-byte vectors.
+__device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi, int64_t j0,
+                                            uint64_t cmask, const uint32_t (&sres)[32])
+{
+    const uint32_t p = args.p;
+    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
+    const uint64_t cj0 = (uint64_t)(args.c_col0 + j0);
+    const uint64_t base = fm_encode(ci, cj0, args.c_lt);
+    const bool run = j0 + 32 <= args.N && (cj0 & cmask) + 32 <= cmask + 1 && (base & 3) == 0;
+    if (run) {
+        uint4* dst = reinterpret_cast<uint4*>(args.C + base);
+        uint4 old[8];
+        if (args.op != FM_OP_SET) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) old[q] = dst[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint4 o = args.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
+            o.x = op_combine(o.x, sres[4 * q + 0], p, args.op);
+            o.y = op_combine(o.y, sres[4 * q + 1], p, args.op);
+            o.z = op_combine(o.z, sres[4 * q + 2], p, args.op);
+            o.w = op_combine(o.w, sres[4 * q + 3], p, args.op);
+            dst[q] = o;
+        }
+        return;
+    }
+    // ragged edge or a tile boundary inside the run: all loads, then all stores
+    uint32_t old[32];
+    uint64_t a = base;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const uint64_t cj = cj0 + e;
+        if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
+        old[e] = (args.op != FM_OP_SET && j0 + e < args.N) ? args.C[a] : 0u;
+    }
+    a = base;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const uint64_t cj = cj0 + e;
+        if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
+        if (j0 + e < args.N) args.C[a] = op_combine(old[e], sres[e], p, args.op);
+    }
+}
 
 template <int BN>
 struct GemmCfg {
@@ -267,10 +354,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
     const int inner = blockIdx.x % per_group;
     const int mb = first_mb + inner % gsz, nb = inner / gsz;
 
-    const int w = args.w, w2 = w * w;
-    const int CS = args.chunk_stages;
-    const int n_chunks = (args.KB + CS - 1) / CS;
-    const int njobs = n_chunks * w2;
+    const int njobs = args.first[args.n_products];
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -279,7 +363,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         }
         for (int b = 0; b < 2; ++b) {
             fm_mbar_init(&accf_bar[b], 1);
-            fm_mbar_init(&acce_bar[b], 4);
+            fm_mbar_init(&acce_bar[b], kEpiWarps);
         }
         fm_mbar_init(&done_bar, 1);
         fm_fence_mbar_init();
@@ -300,12 +384,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         if (lane == 0) {
             // ---- producer: one bulk copy per operand per stage ----
             uint32_t g = 0;
+            int idx = 0;
             for (int t = 0; t < njobs && !*(volatile int*)&s_abort; ++t) {
-                const int c = t % n_chunks, idx = t / n_chunks, i = idx / w, j = idx % w;
-                const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
-                const uint8_t* a_src = args.Ap + (size_t)i * args.a_plane_bytes +
+                while (t >= args.first[idx + 1]) ++idx;
+                const int c = t - args.first[idx];
+                const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
                                        ((size_t)mb * args.KB) * kATileBytes;
-                const uint8_t* b_src = args.Bp + (size_t)j * args.b_plane_bytes +
+                const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
                                        ((size_t)nb * args.KB) * Cfg::kBTileBytes;
                 bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
@@ -331,10 +417,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             const uint32_t idesc = fm_idesc_f16_f32(kBM, BN);
             uint32_t g = 0;
             bool ok = true;
+            int idx = 0;
             for (int t = 0; t < njobs && ok; ++t) {
                 const int b = t & 1;
-                const int c = t % n_chunks;
-                const int kb0 = c * CS, kb1 = min(args.KB, kb0 + CS);
+                while (t >= args.first[idx + 1]) ++idx;
+                const int c = t - args.first[idx];
+                const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
                 if (t >= 2 && !fm_mbar_wait(&acce_bar[b], ((t >> 1) - 1) & 1, args.status, &s_abort)) {
                     ok = false;
                     break;
@@ -371,11 +459,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             fm_mbar_wait(&done_bar, 0, args.status, nullptr);
         }
     } else {
-        // ---- epilogue: 4 warps, warp w reads TMEM lanes 32*(w%4) .. +31 ----
+        // ---- epilogue: kEpiWarps warps. Warp w may only touch TMEM lanes
+        // 32*(w%4) .. +31, so two warps share each lane quarter and split the BN
+        // columns in halves; two warps per SM sub-partition hide each other's
+        // TMEM load latency. ----
+        const int ew = warp - 2;
         const int quarter = warp & 3;
+        const int half = ew >> 2;
+        constexpr int kCols = BN / 2;  // columns drained by this warp
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const uint32_t col0 = (uint32_t)(half * kCols);
         const uint32_t p = args.p;
         bool ok = true;
+        int idx = 0;
         for (int t = 0; t < njobs; ++t) {
             const int b = t & 1;
             if (!fm_mbar_wait(&accf_bar[b], (t >> 1) & 1, args.status, &s_abort)) {
@@ -383,46 +479,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 break;
             }
             fm_tc_fence_after();
-            const int idx = t / n_chunks, c = t % n_chunks;
+            while (t >= args.first[idx + 1]) ++idx;
+            const int c = t - args.first[idx];
+            const int n_chunks = args.first[idx + 1] - args.first[idx];
             const bool last_on_buffer = (t + 2 >= njobs);
             // fold form: the job two steps later on this buffer continues the
             // same limb product (same weight) unless a product boundary lies between
-            const int idx2 = last_on_buffer ? idx : (t + 2) / n_chunks;
+            int idx2 = idx;
+            if (!last_on_buffer)
+                while (t + 2 >= args.first[idx2 + 1]) ++idx2;
             const bool same_next = !last_on_buffer && idx2 == idx;
-            // residue form: S (exact int32 sum of this product's chunks) is
-            // folded into R at the product's last chunk and every 120 chunks
-            const bool s_fresh = (c % 120) == 0;
-            const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
+            const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
+            if (FOLD) {
+                const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; ++cc) {
-                const uint32_t dcol = tmem + lane_base + (uint32_t)(b * BN + cc * 32);
-                uint32_t v[32];
-                fm_tmem_ld32(dcol, v);
-                if (FOLD) {
+                for (int g = 0; g < kCols / 64; ++g) {  // two 32-column chunks in flight
+                    uint32_t v0[32], v1[32];
+                    fm_tmem_ld32(dbase + g * 64, v0);
+                    fm_tmem_ld32(dbase + g * 64 + 32, v1);
                     fm_tmem_wait_ld();
                     if (same_next) {
-                        // exact: |v| < 2^24, so v - rint(v/p)*p is computed without rounding
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const float f = __uint_as_float(v[e]);
-                            const float q = rintf(f * args.invp);
-                            v[e] = __float_as_uint(fmaf(-q, args.pf, f));
-                        }
+                        fold_fp(v0, args.invp, args.pf);
+                        fold_fp(v1, args.invp, args.pf);
                     } else {
-                        const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int32_t d = __float2int_rn(__uint_as_float(v[e]));
-                            const uint32_t xm = barrett32((uint32_t)d + args.offp, p, args.mu32);
-                            const uint32_t y = barrett32(mul * xm, p, args.mu32);  // p < 2^16
-                            v[e] = last_on_buffer ? y : __float_as_uint((float)y);
-                        }
+                        fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.offp);
+                        fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.offp);
                     }
-                    fm_tmem_st32(dcol, v);
-                } else {
-                    const uint32_t scol = tmem + lane_base + (uint32_t)(3 * BN + cc * 32);
-                    uint32_t sv[32];
-                    if (!s_fresh) fm_tmem_ld32(scol, sv);
+                    fm_tmem_st32(dbase + g * 64, v0);
+                    fm_tmem_st32(dbase + g * 64 + 32, v1);
+                }
+            } else {
+                // residue form: S (exact int32 sum of this product's chunks) is
+                // folded into R at the product's last chunk and every 120 chunks
+                const bool s_fresh = (c % 120) == 0;
+                const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
+                const bool r_fresh = (idx == 0 && c < 120);
+                const uint32_t sbase = tmem + lane_base + (uint32_t)(3 * BN) + col0;
+                const uint32_t rbase = tmem + lane_base + (uint32_t)(2 * BN) + col0;
+#pragma unroll 1
+                for (int cc = 0; cc < kCols / 32; ++cc) {
+                    uint32_t v[32], sv[32];
+                    fm_tmem_ld32(dbase + cc * 32, v);
+                    if (!s_fresh) fm_tmem_ld32(sbase + cc * 32, sv);
                     fm_tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
@@ -430,23 +528,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                         sv[e] = (uint32_t)((s_fresh ? 0 : (int32_t)sv[e]) + d);
                     }
                     if (fold_now) {
-                        const uint32_t rcol = tmem + lane_base + (uint32_t)(2 * BN + cc * 32);
-                        uint32_t r[32];
-                        const bool r_fresh = (idx == 0 && c < 120);
                         if (!r_fresh) {
-                            fm_tmem_ld32(rcol, r);
+                            fm_tmem_ld32(rbase + cc * 32, v);
                             fm_tmem_wait_ld();
                         }
                         const uint32_t wt = args.wt[idx];
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const uint64_t x = (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
+                            const uint64_t x =
+                                (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
                             const uint32_t xm = barrett64(x, p, args.mu64);
-                            r[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : r[e]), p, args.mu64);
+                            v[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : v[e]), p, args.mu64);
                         }
-                        fm_tmem_st32(rcol, r);
+                        fm_tmem_st32(rbase + cc * 32, v);
                     } else {
-                        fm_tmem_st32(scol, sv);
+                        fm_tmem_st32(sbase + cc * 32, sv);
                     }
                 }
             }
@@ -461,69 +557,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             const int64_t gi = (int64_t)mb * kBM + quarter * 32 + lane;
             const uint64_t cmask = (1ull << args.c_lt) - 1;
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; ++cc) {
-                uint32_t s[32];
+            for (int cc = 0; cc < kCols / 32; ++cc) {
+                uint32_t sres[32];
+                const uint32_t col = col0 + cc * 32;
                 if (FOLD) {
-                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(cc * 32), s);
+                    fm_tmem_ld32(tmem + lane_base + col, sres);
                     if (njobs >= 2) {
                         uint32_t s1[32];
-                        fm_tmem_ld32(tmem + lane_base + (uint32_t)(BN + cc * 32), s1);
+                        fm_tmem_ld32(tmem + lane_base + (uint32_t)BN + col, s1);
                         fm_tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const uint32_t x = s[e] + s1[e];
-                            s[e] = x >= p ? x - p : x;
+                            const uint32_t x = sres[e] + s1[e];
+                            sres[e] = x >= p ? x - p : x;
                         }
                     } else {
                         fm_tmem_wait_ld();
                     }
                 } else {
-                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN + cc * 32), s);
+                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN) + col, sres);
                     fm_tmem_wait_ld();
                 }
                 if (gi < args.M) {
-                    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
-                    const int64_t j0 = (int64_t)nb * BN + cc * 32;
-                    const uint64_t cj0 = (uint64_t)(args.c_col0 + j0);
-                    const uint64_t base = fm_encode(ci, cj0, args.c_lt);
-                    // the 32 columns form one contiguous run of a Morton tile row
-                    const bool run = j0 + 32 <= args.N && (cj0 & cmask) + 32 <= cmask + 1 &&
-                                     (base & 3) == 0;
-                    if (run) {
-                        uint4* dst = reinterpret_cast<uint4*>(args.C + base);
-                        uint4 old[8];
-                        if (args.op != FM_OP_SET) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) old[q] = dst[q];
-                        }
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            uint4 o = args.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
-                            o.x = op_combine(o.x, s[4 * q + 0], p, args.op);
-                            o.y = op_combine(o.y, s[4 * q + 1], p, args.op);
-                            o.z = op_combine(o.z, s[4 * q + 2], p, args.op);
-                            o.w = op_combine(o.w, s[4 * q + 3], p, args.op);
-                            dst[q] = o;
-                        }
-                    } else {
-                        // ragged edge or a tile boundary inside the run: gather the
-                        // addresses, then all loads, then all stores
-                        uint64_t addr[32];
-                        uint32_t old[32];
-                        uint64_t a = base;
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const uint64_t cj = cj0 + e;
-                            if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
-                            addr[e] = a;
-                        }
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            old[e] = (args.op != FM_OP_SET && j0 + e < args.N) ? args.C[addr[e]] : 0u;
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            if (j0 + e < args.N) args.C[addr[e]] = op_combine(old[e], s[e], p, args.op);
-                    }
+                    const int64_t j0 = (int64_t)nb * BN + col;
+                    write_c_run(args, gi, j0, cmask, sres);
                 }
             }
         }
@@ -584,6 +641,18 @@ int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
 
 }  // namespace
 
+namespace {
+uint64_t gcd_u64(uint64_t a, uint64_t b)
+{
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+}  // namespace
+
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan)
 {
@@ -604,16 +673,47 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     if (!q.fold && bn != 128) return FM_EINVAL;  // residue and sum regions need TMEM slices 3, 4
     q.block_n = bn;
     // exactness: |chunk sum| + |folded residue| (at most 2p) must stay <= 2^24
-    // with |limb product| <= 2^14
-    const int64_t max_k = q.fold ? ((int64_t)(1 << 24) - 2 * (int64_t)p) / (1 << 14) : 1024;
-    int cs = (int)(max_k / kBK);
+    // with |limb product| <= 2^14 (2^16 for the Karatsuba product)
+    const int64_t room = q.fold ? ((int64_t)1 << 24) - 2 * (int64_t)p : ((int64_t)1 << 24);
+    int cs = (int)(room / (1 << 14) / kBK);
     if (opts && opts->k_chunk) {
         if (opts->k_chunk % kBK != 0 || opts->k_chunk / kBK > cs || opts->k_chunk <= 0)
             return FM_EINVAL;
         cs = opts->k_chunk / kBK;
     }
     if (cs < 1) return FM_EUNSUPPORTED;
-    q.chunk_stages = cs;
+    // Karatsuba on two limbs: A*B = (1-256) A0B0 + 256 (A0+A1)(B0+B1) + (2^16-256) A1B1,
+    // three products instead of four; used when every weight is invertible mod p
+    // (the fold form carries residues between products through weight ratios).
+    const uint32_t wk[3] = {(uint32_t)((p + 1 - 256 % p) % p), 256u % p,
+                            (uint32_t)(((uint64_t)65536 - 256) % p)};
+    bool kara = w == 2 && q.fold && !(opts && opts->no_karatsuba == 1);
+    for (int k = 0; kara && k < 3; ++k) kara = wk[k] != 0 && gcd_u64(wk[k], p) == 1;
+    if (kara) {
+        const int cs_m = std::max(1, std::min(cs, (int)(room / (1 << 16) / kBK)));
+        q.n_planes = 3;
+        q.n_products = 3;
+        const int pa[3] = {0, 2, 1}, cks[3] = {cs, cs_m, cs};
+        const uint32_t wts[3] = {wk[0], wk[1], wk[2]};
+        for (int k = 0; k < 3; ++k) {
+            q.prod_a[k] = q.prod_b[k] = pa[k];
+            q.prod_cs[k] = cks[k];
+            q.prod_w[k] = wts[k];
+        }
+    } else {
+        q.n_planes = w;
+        q.n_products = w * w;
+        for (int k = 0; k < w * w; ++k) {
+            const int i = k / w, j = k % w;
+            q.prod_a[k] = i;
+            q.prod_b[k] = j;
+            q.prod_cs[k] = cs;
+            q.prod_w[k] = powmod(256, (uint64_t)(i + j), p);
+        }
+        if (q.fold)
+            for (int k = 0; k < w * w; ++k)
+                if (gcd_u64(q.prod_w[k], p) != 1) return FM_EUNSUPPORTED;
+    }
     q.MB = (int)((M + kBM - 1) / kBM);
     q.NB = (int)((N + bn - 1) / bn);
     q.KB = (int)((K + kBK - 1) / kBK);
@@ -625,7 +725,7 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
 
 size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
 {
-    return (size_t)q.w * (q.a_plane_bytes + q.b_plane_bytes);
+    return (size_t)q.n_planes * (q.a_plane_bytes + q.b_plane_bytes);
 }
 
 namespace {
@@ -645,15 +745,16 @@ int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void*
     if (role == FM_LIMB_A) {
         if (q.MB * q.KB == 0) return FM_OK;
         split_a_kernel<<<q.MB * q.KB, kSplitThreads, 0, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0,
-                                                             q.M, q.K, q.KB, q.w, p, hi, out,
-                                                             q.a_plane_bytes);
+                                                             q.M, q.K, q.KB, q.w, q.n_planes, p, hi,
+                                                             out, q.a_plane_bytes);
     } else {
         if (q.NB * q.KB == 0) return FM_OK;
         const size_t sb_smem = (size_t)kBK * q.block_n * 4;
         auto k = q.block_n == 256 ? split_b_kernel<256> : split_b_kernel<128>;
         FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
         k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N,
-                                                      q.KB, q.w, p, hi, out, q.b_plane_bytes);
+                                                      q.KB, q.w, q.n_planes, p, hi, out,
+                                                      q.b_plane_bytes);
     }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
@@ -671,26 +772,29 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.MB = q.MB;
     a.NB = q.NB;
     a.KB = q.KB;
-    a.w = q.w;
-    a.chunk_stages = q.chunk_stages;
+    a.n_products = q.n_products;
     a.p = p;
     a.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
     a.mu64 = ~0ull / p;
     a.offp = (uint32_t)((((uint64_t)1 << 24) + p - 1) / p * p);
-    const int w2 = q.w * q.w;
-    for (int idx = 0; idx < 16; ++idx) {
-        a.wt[idx] = 0;
-        a.cn[idx] = 0;
+    for (int k = 0; k < 16; ++k) {
+        a.pa[k] = a.pb[k] = a.cs[k] = 0;
+        a.wt[k] = a.cn[k] = 0;
     }
-    for (int idx = 0; idx < w2; ++idx) {
-        const int i = idx / q.w, j = idx % q.w;
-        a.wt[idx] = powmod(256, (uint64_t)(i + j), p);
+    a.first[0] = 0;
+    for (int k = 0; k < q.n_products; ++k) {
+        a.pa[k] = q.prod_a[k];
+        a.pb[k] = q.prod_b[k];
+        a.cs[k] = q.prod_cs[k];
+        a.wt[k] = q.prod_w[k];
+        a.first[k + 1] = a.first[k] + (q.KB + q.prod_cs[k] - 1) / q.prod_cs[k];
     }
+    for (int k = q.n_products + 1; k <= 16; ++k) a.first[k] = a.first[q.n_products];
     if (q.fold) {
-        for (int idx = 0; idx < w2; ++idx)
-            for (int idx2 = 0; idx2 < w2; ++idx2) {
-                const uint32_t inv = invmod(a.wt[idx2], p);
-                a.cn[idx * 4 + idx2] = (uint32_t)((uint64_t)a.wt[idx] * inv % p);
+        for (int k = 0; k < q.n_products; ++k)
+            for (int k2 = 0; k2 < q.n_products; ++k2) {
+                const uint32_t inv = invmod(a.wt[k2], p);
+                a.cn[k * 4 + k2] = (uint32_t)((uint64_t)a.wt[k] * inv % p);
             }
     }
     a.invp = 1.0f / (float)p;
@@ -717,7 +821,7 @@ int fm_limb_run(const FmLimbPlan& q, fm_sub C, fm_sub A, fm_sub B, uint32_t p, i
 {
     if (q.M == 0 || q.N == 0) return FM_OK;
     uint8_t* Ap = static_cast<uint8_t*>(workspace);
-    uint8_t* Bp = Ap + (size_t)q.w * q.a_plane_bytes;
+    uint8_t* Bp = Ap + (size_t)q.n_planes * q.a_plane_bytes;
     FM_TRY(fm_limb_split_run(q, A, FM_LIMB_A, p, Ap, s));
     FM_TRY(fm_limb_split_run(q, B, FM_LIMB_B, p, Bp, s));
     return fm_limb_gemm_run(q, C, Ap, Bp, p, op, status, s);
@@ -734,7 +838,7 @@ extern "C" int64_t fm_limb_planes_size(int64_t rows, int64_t cols, int32_t role,
     const int rc = role == FM_LIMB_A ? fm_limb_plan(rows, 1, cols, p, opts, &q)
                                      : fm_limb_plan(1, cols, rows, p, opts, &q);
     if (rc != FM_OK) return rc;
-    return (int64_t)q.w * (int64_t)(role == FM_LIMB_A ? q.a_plane_bytes : q.b_plane_bytes);
+    return (int64_t)q.n_planes * (int64_t)(role == FM_LIMB_A ? q.a_plane_bytes : q.b_plane_bytes);
 }
 
 extern "C" int fm_limb_split(fm_sub X, int32_t role, uint32_t p, const fm_opts* opts, void* planes,

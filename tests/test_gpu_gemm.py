@@ -81,12 +81,15 @@ def test_limb_parity(env, orc, case, p):
         assert np.array_equal(got, want), (p, op, lts)
 
 
-@pytest.mark.parametrize("k_chunk,block_n", [(64, 0), (512, 0), (960, 0), (0, 128), (320, 128)])
-def test_limb_chunk_and_tile_options(env, orc, k_chunk, block_n):
+@pytest.mark.parametrize("k_chunk,block_n,no_kara", [(64, 0, 0), (512, 0, 0), (960, 0, 0),
+                                                     (0, 128, 0), (320, 128, 0), (0, 0, 1),
+                                                     (192, 128, 1)])
+def test_limb_chunk_and_tile_options(env, orc, k_chunk, block_n, no_kara):
     fm = env[0]
-    got, want = run_case(env, orc, P16, 2, fm.FM_ALGO_LIMB_TC, 300, 520, 3000, (0, 5, 3, 0, 0, 9),
-                         (6, 6, 6), seed=4, options=fm.opts(k_chunk, block_n))
-    assert np.array_equal(got, want)
+    for p in (P16, 257):
+        got, want = run_case(env, orc, p, 2, fm.FM_ALGO_LIMB_TC, 300, 520, 3000, (0, 5, 3, 0, 0, 9),
+                             (6, 6, 6), seed=4, options=fm.opts(k_chunk, block_n, no_kara))
+        assert np.array_equal(got, want), p
 
 
 def test_limb_rejects_unsafe_chunk(env):
