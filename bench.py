@@ -511,7 +511,7 @@ def run_fm(args, world, rank, local):
     n_products = 3  # Karatsuba on two limbs: A0B0, (A0+A1)(B0+B1), A1B1
     mma_flops = 2.0 * n * n * n * n_products
     achieved = mma_flops / (gemm_avg / 1e3) / 1e12
-    traffic = profiled_traffic(os.path.join(ROOT, "paper_1705_04807_gb300", "csrc", "limb.cu"),
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_1705_04807_gb300", "csrc", "limb_gemm.cu"),
                                "limb_gemm_n8192.md")
     roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                 "frac": achieved / sustained, "traffic": traffic,

@@ -16,7 +16,7 @@ int fm_plain_launch(int lt, int arith, const FmCallDesc* calls, const FmWorkItem
                     int* status, cudaStream_t s);
 int fm_plain_occupancy(int lt, int arith);
 
-// Limb tensor-core form (limb.cu): split A and B into balanced 8-bit limb
+// Limb tensor-core form (limb_split.cu, limb_gemm.cu): split A and B into balanced 8-bit limb
 // planes in the tensor-core tile layout, then the tcgen05 GEMM with the
 // recombine / reduce / combine epilogue. workspace must hold
 // fm_limb_workspace_bytes(...).

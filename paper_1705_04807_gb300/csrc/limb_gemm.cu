@@ -1,204 +1,39 @@
-// limb.cu -- the tensor-core form of C <- C op A*B mod p.
+// limb_gemm.cu -- the tensor-core form of C <- C op A*B mod p.
 //
-// Residues are split into w balanced signed 8-bit limbs (digits in [-128, 127],
-// base 256, representative r = x if x <= Hi else x - p with
-// Hi = 127 * sum_{t<w} 256^t). Then
-//     A*B == sum_{i,j} 256^(i+j) * (A_i * B_j)      (mod p)
-// and every limb product A_i * B_j is an integer GEMM with |entry| <= 2^14.
-// GB300's tcgen05 has no integer MMA kind on sm_103a, so the 8-bit limbs are
-// carried exactly as FP16 values through tcgen05.mma kind::f16 with FP32
-// accumulation in tensor memory. FP32 holds every integer of magnitude
-// <= 2^24 exactly, so K is cut into chunks of at most 1024 (64-wide stages)
-// and each chunk's accumulator is drained into exact integers before it could
-// leave that range.
+// With residues split into balanced signed 8-bit limbs (limb_split.cu),
+//     A*B == sum_k weight_k * (A_{a(k)} * B_{b(k)})      (mod p)
+// over the limb products k: (i, j) with weight 256^(i+j) mod p, or, for two
+// limbs, the three Karatsuba products A0B0, (A0+A1)(B0+B1), A1B1 with weights
+// (1-256), 256, (2^16-256) mod p. Every limb product is an integer GEMM whose
+// entries are at most 2^14 (2^16 for the Karatsuba middle product) in
+// magnitude. sm_103a's tcgen05 has no integer MMA kind, so the limbs are carried
+// exactly as FP16 values through tcgen05.mma kind::f16 with FP32 accumulation in
+// tensor memory. FP32 holds every integer of magnitude <= 2^24 exactly, so K is
+// cut into chunks small enough that no partial sum can leave that range, and
+// each chunk's accumulator is drained into exact integers.
 //
-// Kernels:
-//   split_a / split_b  read the (sub-)matrices from the Morton-hybrid layout
-//                      (Sec. 1), re-base them to an aligned grid and write the
-//                      limb planes as tiles in the 128-byte-swizzled K-major
-//                      layout the MMA descriptors expect, so that each
-//                      pipeline stage is ONE contiguous 1-D bulk copy per
-//                      operand (the paper's contiguous base case, Sec. 2.1).
-//   limb_gemm          one 128 x BN output tile per CTA: a TMA producer warp,
-//                      an MMA warp (tcgen05.mma into TMEM) and four epilogue
-//                      warps that drain each accumulator chunk with
-//                      tcgen05.ld, reduce mod p and either fold the running
-//                      residue back into the accumulator (p < 2^16) or add it
-//                      to a residue region of TMEM (any p < 2^31); the final
-//                      residue is combined with C (set / add / subtract) and
-//                      written back in the Morton-hybrid layout.
+// One 128 x BN output tile per CTA: a producer warp (one 1-D bulk copy per
+// operand per 64-wide K stage), an MMA warp (tcgen05.mma into TMEM, two
+// accumulators alternating between jobs = (limb product, K chunk)) and eight
+// epilogue warps that drain each chunk with tcgen05.ld / st. Fold form
+// (p < 2^16): the running residue is folded back into the FP32 accumulator, with
+// an exact FP32 reduction between chunks of one product and a weight change at
+// product boundaries. Residue form (any p < 2^31): an exact int32 sum per
+// product, folded into a residue region of TMEM once per product. The final
+// residue is combined with C (set / add / subtract) in the Morton-hybrid layout.
 #include <cuda_fp16.h>
 
 #include <algorithm>
 
 #include "fm_internal.cuh"
 #include "fm_kernels.h"
+#include "limb_common.cuh"
 
 namespace {
 
-constexpr int kBM = 128;                     // output rows per CTA (TMEM lanes)
-constexpr int kBK = 64;                      // K per stage: one 128-byte swizzle row of f16
-constexpr uint32_t kATileBytes = kBM * 128;  // 16 KB
-constexpr int kSplitThreads = 256;
+using namespace fm_limb;
 constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
-
-// ---- limb digits ----------------------------------------------------------
-__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, int w, int (&d)[4])
-{
-    int32_t r = (x <= (uint32_t)hi) ? (int32_t)x : (int32_t)((int64_t)x - (int64_t)p);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        if (t < w) {
-            const int32_t dt = ((r + 128) & 255) - 128;
-            d[t] = dt;
-            r = (r - dt) >> 8;
-        } else {
-            d[t] = 0;
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_half2(int lo, int hi)
-{
-    const __half a = __int2half_rn(lo), b = __int2half_rn(hi);
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
-
-// Byte offset of the 16-byte chunk kc (8 f16 values) of row r inside a tile
-// whose rows are 128 bytes, in the 128-byte swizzle pattern (chunk index XOR
-// row index mod 8), identical to what a TMA SWIZZLE_128B load produces.
-__device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t kc)
-{
-    return r * 128u + ((kc ^ (r & 7u)) << 4);
-}
-
-// Loads 8 consecutive entries (row gi, columns gj..gj+7) of a Morton-hybrid
-// matrix, zero outside [0, rows) x [0, cols) of the sub-matrix. When the 8
-// entries are one aligned run inside a tile row they come as two 16-byte loads.
-__device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, int lt, int64_t row0,
-                                             int64_t col0, int64_t i, int64_t j, int64_t rows,
-                                             int64_t cols, uint32_t (&x)[8])
-{
-    if (i >= rows) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = 0;
-        return;
-    }
-    const uint64_t gi = (uint64_t)(row0 + i);
-    const uint64_t mask = (1ull << lt) - 1;
-    const uint64_t gj0 = (uint64_t)(col0 + j);
-    const uint64_t a0 = fm_encode(gi, gj0, lt);
-    if (j + 8 <= cols && (gj0 & mask) + 8 <= mask + 1 && (a0 & 3) == 0) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4*>(base + a0));
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + a0) + 1);
-        x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
-        x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
-        return;
-    }
-    uint64_t addr = a0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int64_t jj = j + e;
-        const uint64_t gj = gj0 + e;
-        if (e > 0) addr = ((gj & mask) == 0) ? fm_encode(gi, gj, lt) : addr + 1;
-        x[e] = jj < cols ? __ldg(base + addr) : 0u;
-    }
-}
-
-// A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
-__global__ void __launch_bounds__(kSplitThreads)
-    split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
-                   int64_t K, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
-{
-    const int tile = blockIdx.x;
-    const int mb = tile / KB, kb = tile % KB;
-    uint8_t* out = planes + (size_t)tile * kATileBytes;
-    for (int c = threadIdx.x; c < kBM * 8; c += kSplitThreads) {
-        const int r = c >> 3, kc = c & 7;
-        uint32_t x[8];
-        load8_morton(A, lt, row0, col0, (int64_t)mb * kBM + r, (int64_t)kb * kBK + kc * 8, M, K, x);
-        int d[8][4];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) limb_digits(x[e], p, hi, w, d[e]);
-        const uint32_t off = sw128_offset(r, kc);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (t < n_planes) {
-                int q[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
-                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
-                uint4 v;
-                v.x = pack_half2(q[0], q[1]);
-                v.y = pack_half2(q[2], q[3]);
-                v.z = pack_half2(q[4], q[5]);
-                v.w = pack_half2(q[6], q[7]);
-                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
-            }
-        }
-    }
-}
-
-// B (K x N) -> w planes of [NB][KB] tiles, each BN rows (n) x 64 k f16 (B
-// transposed to K-major), swizzled. Staged through shared memory so that both
-// the Morton reads (along n, 16-byte vectors) and the tile writes (along k)
-// are coalesced.
-template <int BN>
-__global__ void __launch_bounds__(kSplitThreads)
-    split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
-                   int64_t N, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
-{
-    extern __shared__ __align__(16) uint32_t sb[];  // [kBK][BN]
-    const int tile = blockIdx.x;
-    const int nb = tile / KB, kb = tile % KB;
-    const uint64_t mask = (1ull << lt) - 1;
-    for (int idx = threadIdx.x; idx < kBK * BN / 4; idx += kSplitThreads) {
-        const int kk = idx / (BN / 4), nn = (idx % (BN / 4)) * 4;
-        const int64_t gk = (int64_t)kb * kBK + kk, gn = (int64_t)nb * BN + nn;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gk < K) {
-            const uint64_t gi = (uint64_t)(row0 + gk), gj = (uint64_t)(col0 + gn);
-            const uint64_t a = fm_encode(gi, gj, lt);
-            if (gn + 4 <= N && (gj & mask) + 4 <= mask + 1 && (a & 3) == 0) {
-                v = __ldg(reinterpret_cast<const uint4*>(B + a));
-            } else {
-                uint32_t t[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    t[q] = gn + q < N ? __ldg(B + fm_encode(gi, gj + q, lt)) : 0u;
-                v = make_uint4(t[0], t[1], t[2], t[3]);
-            }
-        }
-        *reinterpret_cast<uint4*>(sb + kk * BN + nn) = v;
-    }
-    __syncthreads();
-    uint8_t* out = planes + (size_t)tile * BN * 128;
-    for (int c = threadIdx.x; c < BN * 8; c += kSplitThreads) {
-        const int n = c % BN, kc = c / BN;
-        int d[8][4];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) limb_digits(sb[(kc * 8 + e) * BN + n], p, hi, w, d[e]);
-        const uint32_t off = sw128_offset(n, kc);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (t < n_planes) {
-                int q[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
-                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
-                uint4 v;
-                v.x = pack_half2(q[0], q[1]);
-                v.y = pack_half2(q[2], q[3]);
-                v.z = pack_half2(q[4], q[5]);
-                v.w = pack_half2(q[6], q[7]);
-                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
-            }
-        }
-    }
-}
 
 // ---- modular helpers --------------------------------------------------------
 __device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t p, uint32_t mu)
@@ -728,38 +563,6 @@ size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
     return (size_t)q.n_planes * (q.a_plane_bytes + q.b_plane_bytes);
 }
 
-namespace {
-int32_t limb_hi(int w)
-{
-    int32_t hi = 0;
-    for (int t = 0; t < w; ++t) hi += 127 * (1 << (8 * t));  // 127 * sum 256^t
-    return hi;
-}
-}  // namespace
-
-int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void* planes,
-                      cudaStream_t s)
-{
-    uint8_t* out = static_cast<uint8_t*>(planes);
-    const int32_t hi = limb_hi(q.w);
-    if (role == FM_LIMB_A) {
-        if (q.MB * q.KB == 0) return FM_OK;
-        split_a_kernel<<<q.MB * q.KB, kSplitThreads, 0, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0,
-                                                             q.M, q.K, q.KB, q.w, q.n_planes, p, hi,
-                                                             out, q.a_plane_bytes);
-    } else {
-        if (q.NB * q.KB == 0) return FM_OK;
-        const size_t sb_smem = (size_t)kBK * q.block_n * 4;
-        auto k = q.block_n == 256 ? split_b_kernel<256> : split_b_kernel<128>;
-        FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
-        k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N,
-                                                      q.KB, q.w, q.n_planes, p, hi, out,
-                                                      q.b_plane_bytes);
-    }
-    FM_CUDA_TRY(cudaGetLastError());
-    return FM_OK;
-}
-
 int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const void* b_planes,
                      uint32_t p, int op, int* status, cudaStream_t s)
 {
@@ -839,18 +642,6 @@ extern "C" int64_t fm_limb_planes_size(int64_t rows, int64_t cols, int32_t role,
                                      : fm_limb_plan(1, cols, rows, p, opts, &q);
     if (rc != FM_OK) return rc;
     return (int64_t)q.n_planes * (int64_t)(role == FM_LIMB_A ? q.a_plane_bytes : q.b_plane_bytes);
-}
-
-extern "C" int fm_limb_split(fm_sub X, int32_t role, uint32_t p, const fm_opts* opts, void* planes,
-                             fm_stream stream)
-{
-    if (role != FM_LIMB_A && role != FM_LIMB_B) return FM_EINVAL;
-    FM_TRY(fm_check_sub(X));
-    if (!planes || ((uintptr_t)planes & 15)) return FM_EINVAL;
-    FmLimbPlan q;
-    FM_TRY(role == FM_LIMB_A ? fm_limb_plan(X.rows, 1, X.cols, p, opts, &q)
-                             : fm_limb_plan(1, X.cols, X.rows, p, opts, &q));
-    return fm_limb_split_run(q, X, role, p, planes, (cudaStream_t)stream);
 }
 
 extern "C" int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K,
