@@ -206,6 +206,23 @@ int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K
  * that report use fm_gemm_modp and fm_get_last_device_status. */
 int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, fm_stream stream);
 
+/* ---- TU decomposition (Sec. 1: the consumer of the product) ------------
+ * Rank-revealing PLUQ over the prime field GF(p) of the leading m x n corner
+ * of the Morton-hybrid matrix A (T' >= 4), in place: P A Q = L U with L unit
+ * lower trapezoidal (m x r), U upper trapezoidal (r x n, nonzero diagonal),
+ * r = rank(A). On return A holds L strictly below the diagonal of its first r
+ * columns and U on and above the diagonal of its first r rows (entries of rows
+ * >= r outside L are zero); row_perm (device, m) and col_perm (device, n) are
+ * gathers: (P A Q)(i, j) = A_in(row_perm[i], col_perm[j]). *rank (host) gets r.
+ * Blocked right-looking elimination with 128-column panels (first-nonzero
+ * pivoting, zero columns moved behind the pivot columns); every trailing
+ * update is one fm_gemm_modp call (C <- C - L21 * U12 on sub-matrices of A).
+ * p must be prime; n <= 51200. Synchronous: returns after the factorisation.
+ * The paper defers the TU algorithm itself (TURBO) to its reference; this is
+ * the textbook elimination that produces the same kind of result. */
+int fm_pluq(fm_matrix A, int64_t m, int64_t n, uint32_t p, int32_t* row_perm, int32_t* col_perm,
+            int64_t* rank, fm_stream stream);
+
 /* ---- batching form (Sec. 2.2, Prop. on work and span: the base-case
  * products are independent and may run in parallel) ---------------------- */
 
@@ -235,6 +252,42 @@ int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream);
 int64_t fm_plan_work_items(const fm_plan* plan);
 
 int fm_plan_destroy(fm_plan* plan);
+
+/* ---- autotuning ---------------------------------------------------------
+ * Sec. 1 takes the Morton-hybrid threshold T' from prior measurements; here the
+ * threshold of the decomposed forms and the limb form's options (output tile
+ * width, K chunk, Karatsuba) are measured on the device instead. */
+typedef struct fm_tune_result {
+    int32_t algo;        /* FM_ALGO_PLAIN or FM_ALGO_LIMB_TC                       */
+    int32_t log2_T;      /* T' the winner ran with (for the plain form: the layout) */
+    fm_opts opts;        /* options of the winning limb form (zero for plain)        */
+    double ms;           /* one call of the winner, milliseconds                     */
+    double gops;         /* 2 M N K / time, Gop/s                                    */
+    int32_t candidates;  /* candidates that ran                                      */
+    int32_t reserved;
+} fm_tune_result;
+
+enum { FM_TUNE_NO_LIMB = 1, FM_TUNE_NO_PLAIN = 2 };
+
+/* Times every candidate form for C (M x N) -= A (M x K) * B (K x N) mod p on
+ * scratch Morton matrices it allocates (and frees) on the current device:
+ * the plain form at T' = 32 and 64, the limb form with output tile width 256 and
+ * 128, the full and half exact K chunk, with and without Karatsuba. Writes the
+ * fastest to *out and remembers it for the problem class (M, N, K rounded up to
+ * powers of two; p < 2^8, odd p < 2^16, other p); fm_gemm_modp with
+ * FM_ALGO_AUTO and opts == NULL then uses the remembered choice when the
+ * caller's operands allow it. Synchronises stream. */
+int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t flags, fm_stream stream,
+                fm_tune_result* out);
+
+/* 1 and *out filled if the problem class has a remembered choice, else 0. */
+int fm_autotune_lookup(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result* out);
+
+/* Saves / loads the remembered choices as text (host only). load returns the
+ * number of classes read or a negative fm_status. */
+int fm_autotune_save(const char* path);
+int fm_autotune_load(const char* path);
+int fm_autotune_clear(void);
 
 /* ---- decomposition (host only; Sec. 2.2 Steps 1-4) ---------------------- */
 

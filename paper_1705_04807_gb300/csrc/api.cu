@@ -231,6 +231,23 @@ extern "C" int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op
         }
         return FM_OK;
     }
+    fm_opts tuned_opts;
+    if (algo == FM_ALGO_AUTO && opts == nullptr) {
+        fm_tune_result r;
+        if (fm_tuned_choice(M, N, K, p, &r)) {
+            const bool same = A.m.log2_T == C.m.log2_T && B.m.log2_T == C.m.log2_T;
+            const bool plain_ok = same && (C.m.log2_T == 5 || C.m.log2_T == 6);
+            if (r.algo == FM_ALGO_LIMB_TC || !plain_ok) {
+                algo = FM_ALGO_LIMB_TC;
+                if (r.algo == FM_ALGO_LIMB_TC) {
+                    tuned_opts = r.opts;
+                    opts = &tuned_opts;
+                }
+            } else {
+                algo = FM_ALGO_PLAIN;
+            }
+        }
+    }
     algo = resolve_algo(C, A, B, algo);
     if (algo == FM_ALGO_LIMB_MMA_S8) return FM_EUNSUPPORTED;
     if (algo == FM_ALGO_LIMB_TC) {

@@ -42,3 +42,6 @@ int fm_limb_split_run(const FmLimbPlan& plan, fm_sub X, int role, uint32_t p, vo
                       cudaStream_t s);
 int fm_limb_gemm_run(const FmLimbPlan& plan, fm_sub C, const void* a_planes,
                      const void* b_planes, uint32_t p, int op, int* status, cudaStream_t s);
+
+// Remembered autotune choice for a problem class (autotune.cu).
+bool fm_tuned_choice(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result* out);

@@ -1,0 +1,451 @@
+// pluq.cu -- rank-revealing TU / PLUQ decomposition over GF(p) on the device.
+//
+// Sec. 1: the matrix product serves TU decomposition of rectangular, possibly
+// singular matrices over finite fields (TURBO), which also yields the rank; the
+// paper defers the algorithm itself to its reference. This is a blocked
+// right-looking elimination with the same kind of result, P A Q = L U with L
+// unit lower trapezoidal (m x r), U upper trapezoidal (r x n), r = rank:
+//
+//   for each panel of 128 columns:
+//     1. factor the panel (rows r..m-1): pivot = first row with a nonzero in
+//        the column, row swap, exact modular rank-1 update; a column with no
+//        nonzero below row r is skipped (it belongs to the non-pivot columns);
+//     2. move the panel's pivot columns in front of its skipped ones;
+//     3. apply the panel's row swaps to the rest of the matrix;
+//     4. U12 <- L11^-1 A12 (unit lower triangular solve);
+//     5. A22 <- A22 - L21 U12 mod p: one fm_gemm_modp call on three disjoint
+//        sub-matrices of the Morton-hybrid matrix -- the MM call the paper's
+//        decomposition issues (Sec. 2: S_A = S_B * S_C on sub-matrices).
+//   finally the skipped columns of every panel are moved behind all pivot
+//   columns.
+//
+// Step 1 runs as one cooperative launch with a grid barrier per column. The
+// barrier is bounded: a wait that expires raises FM_ETIMEOUT and every CTA
+// leaves the kernel.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "fm_internal.cuh"
+#include "fm_kernels.h"
+
+namespace {
+
+constexpr int kNb = 128;          // panel width
+constexpr int kPanelThreads = 256;
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
+{
+    const uint64_t t = (uint64_t)a * b;
+    const uint64_t q = __umul64hi(t, mu);
+    uint64_t r = t - q * p;
+    while (r >= p) r -= p;
+    return (uint32_t)r;
+}
+
+__device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, uint32_t p)
+{
+    return a >= b ? a - b : a + (p - b);
+}
+
+// a^(p-2) mod p: the inverse of a unit of the prime field GF(p).
+__device__ uint32_t invmod_prime(uint32_t a, uint32_t p, uint64_t mu)
+{
+    uint32_t r = 1, b = a;
+    uint32_t e = p - 2;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, p, mu);
+        b = mulmod(b, b, p, mu);
+        e >>= 1;
+    }
+    return r;
+}
+
+struct PanelArgs {
+    uint32_t* A;
+    int lt;
+    int64_t m;       // rows of the matrix
+    int64_t r0;      // first row of the panel region (rank found so far)
+    int64_t c0;      // first column of the panel
+    int w;           // panel width (<= kNb)
+    uint32_t p;
+    uint64_t mu;
+    int* piv_slot;   // [w] first nonzero row per column (INT_MAX before the search)
+    int* piv_row;    // out [w]: pivot row of panel column t, or -1 if skipped
+    int* n_piv;      // out: pivots found
+    unsigned* bar;   // [2]: arrival count, generation
+    int* status;
+};
+
+// Bounded grid-wide barrier (all CTAs co-resident: cooperative launch).
+__device__ bool grid_barrier(unsigned* bar, int* status, volatile int* s_abort)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*s_abort) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = fm_globaltimer();
+            while (*gen == g) {
+                if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
+                    fm_raise(status, FM_ETIMEOUT);
+                    *s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !*s_abort;
+}
+
+__device__ __forceinline__ uint32_t* elem(const PanelArgs& a, int64_t i, int64_t j)
+{
+    return a.A + fm_encode((uint64_t)i, (uint64_t)j, a.lt);
+}
+
+// Factors rows [r0, m) x columns [c0, c0 + w) in place (see the file comment).
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
+{
+    __shared__ uint32_t prow[kNb];
+    __shared__ int s_abort;
+    __shared__ int s_piv;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gwarp = (int64_t)blockIdx.x * (kPanelThreads / 32) + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * (kPanelThreads / 32);
+    int64_t r = a.r0;
+    int found = 0;
+    for (int t = 0; t < a.w; ++t) {
+        const int64_t j = a.c0 + t;
+        if (!grid_barrier(a.bar, a.status, &s_abort)) return;  // updates of column t-1 done
+        if (r >= a.m) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = -1;
+            continue;
+        }
+        // pivot: row r itself when nonzero, else the first nonzero row below
+        int piv;
+        if (*elem(a, r, j) != 0) {
+            piv = (int)r;
+        } else {
+            for (int64_t base = r + 1 + gwarp * 32; base < a.m; base += nwarps * 32) {
+                const int64_t i = base + lane;
+                const bool nz = i < a.m && *elem(a, i, j) != 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, nz);
+                if (bal) {
+                    if (lane == 0) atomicMin(&a.piv_slot[t], (int)(base + __ffs(bal) - 1));
+                    break;
+                }
+            }
+            if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+            piv = *(volatile int*)&a.piv_slot[t];
+            if (piv == INT_MAX) {  // no nonzero below row r: a non-pivot column
+                if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = -1;
+                continue;
+            }
+            if (blockIdx.x == 0) {  // swap rows r and piv across the panel
+                for (int c = threadIdx.x; c < a.w; c += kPanelThreads) {
+                    uint32_t* x = elem(a, r, a.c0 + c);
+                    uint32_t* y = elem(a, piv, a.c0 + c);
+                    const uint32_t tmp = *x;
+                    *x = *y;
+                    *y = tmp;
+                }
+            }
+            if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = piv;
+        // pivot row to shared memory
+        for (int c = threadIdx.x; c < a.w; c += kPanelThreads) prow[c] = *elem(a, r, a.c0 + c);
+        __syncthreads();
+        const uint32_t inv = invmod_prime(prow[t], a.p, a.mu);
+        // rank-1 update of rows below r: a_i <- a_i - l_i * pivot row, l_i stored in column t
+        for (int64_t i = r + 1 + gwarp; i < a.m; i += nwarps) {
+            const uint32_t l = mulmod(*elem(a, i, j), inv, a.p, a.mu);
+            for (int c = t + 1 + lane; c < a.w; c += 32) {
+                uint32_t* x = elem(a, i, a.c0 + c);
+                *x = submod(*x, mulmod(l, prow[c], a.p, a.mu), a.p);
+            }
+            __syncwarp();
+            if (lane == 0) *elem(a, i, j) = l;
+        }
+        ++r;
+        ++found;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.n_piv = found;
+}
+
+// Columns [c0, c0 + w) of rows [0, m) reordered: new column t = old order[t].
+__global__ void permute_panel_cols_kernel(uint32_t* A, int lt, int64_t m, int64_t c0, int w,
+                                          const int* __restrict__ order)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x / 32) + warp; i < m;
+         i += (int64_t)gridDim.x * (blockDim.x / 32)) {
+        uint32_t v[kNb / 32];
+#pragma unroll
+        for (int q = 0; q < kNb / 32; ++q) {
+            const int t = lane + 32 * q;
+            v[q] = t < w ? A[fm_encode((uint64_t)i, (uint64_t)(c0 + order[t]), lt)] : 0u;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kNb / 32; ++q) {
+            const int t = lane + 32 * q;
+            if (t < w) A[fm_encode((uint64_t)i, (uint64_t)(c0 + t), lt)] = v[q];
+        }
+    }
+}
+
+// The panel's row swaps (in order) applied to columns outside [c0, c0 + w).
+__global__ void row_swaps_kernel(uint32_t* A, int lt, int64_t n, int64_t c0, int w, int64_t r0,
+                                 const int* __restrict__ piv_row, int w_piv)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j >= c0 && j < c0 + w) continue;
+        int64_t r = r0;
+        for (int t = 0; t < w_piv; ++t) {
+            const int pv = piv_row[t];
+            if (pv < 0) continue;
+            if (pv != r) {
+                uint32_t* x = A + fm_encode((uint64_t)r, (uint64_t)j, lt);
+                uint32_t* y = A + fm_encode((uint64_t)pv, (uint64_t)j, lt);
+                const uint32_t tmp = *x;
+                *x = *y;
+                *y = tmp;
+            }
+            ++r;
+        }
+    }
+}
+
+// The same swaps on the row permutation (gather convention).
+__global__ void perm_swaps_kernel(int32_t* rp, int64_t r0, const int* __restrict__ piv_row, int w)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t r = r0;
+        for (int t = 0; t < w; ++t) {
+            const int pv = piv_row[t];
+            if (pv < 0) continue;
+            if (pv != r) {
+                const int32_t tmp = rp[r];
+                rp[r] = rp[pv];
+                rp[pv] = tmp;
+            }
+            ++r;
+        }
+    }
+}
+
+// U12 <- L11^-1 A12: rows [r0, r0 + k) x columns [cl, n), L11 = the unit lower
+// triangle of rows [r0, r0 + k) x columns [c0, c0 + k). One thread per column,
+// forward substitution; L11 and the solved column live in shared memory.
+constexpr int kTrsmThreads = 128;
+__global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(uint32_t* A, int lt, int64_t r0,
+                                                            int64_t c0, int k, int64_t cl, int64_t n,
+                                                            uint32_t p, int narrow)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t* L = sm;                       // [k][k]
+    uint32_t* xs = sm + kNb * kNb;          // [k][kTrsmThreads]
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, t = e % k;
+        L[i * kNb + t] = t < i ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
+    }
+    __syncthreads();
+    for (int64_t jb = cl + blockIdx.x * (int64_t)blockDim.x; jb < n; jb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = jb + threadIdx.x;
+        if (j < n) {
+            for (int i = 0; i < k; ++i) {
+                uint32_t s;
+                if (narrow) {  // (p-1)^2 * k < 2^64
+                    uint64_t acc = 0;
+                    for (int t = 0; t < i; ++t) acc += (uint64_t)L[i * kNb + t] * xs[t * kTrsmThreads + threadIdx.x];
+                    s = (uint32_t)(acc % p);
+                } else {
+                    unsigned __int128 acc = 0;
+                    for (int t = 0; t < i; ++t) acc += (uint64_t)L[i * kNb + t] * xs[t * kTrsmThreads + threadIdx.x];
+                    s = (uint32_t)(acc % p);
+                }
+                uint32_t* a = A + fm_encode((uint64_t)(r0 + i), (uint64_t)j, lt);
+                const uint32_t x = submod(*a, s, p);
+                xs[i * kTrsmThreads + threadIdx.x] = x;
+                *a = x;
+            }
+        }
+    }
+}
+
+// Columns of rows [0, m) reordered in place: new column t = old column ord[t],
+// t < n. One CTA per row at a time, the row staged in shared memory.
+__global__ void permute_cols_rows_kernel(uint32_t* A, int lt, int64_t m, int64_t n,
+                                         const int32_t* __restrict__ ord)
+{
+    extern __shared__ uint32_t row[];
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+            row[j] = A[fm_encode((uint64_t)i, (uint64_t)j, lt)];
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
+            A[fm_encode((uint64_t)i, (uint64_t)t, lt)] = row[ord[t]];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* row_perm,
+                       int32_t* col_perm, int64_t* rank, fm_stream stream)
+{
+    if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
+    FM_TRY(fm_check_matrix(Am));
+    if (m < 0 || n < 0 || m > fm_side(Am) || n > fm_side(Am) || !rank) return FM_EINVAL;
+    if (m >= INT_MAX || n >= INT_MAX) return FM_EINVAL;
+    if ((m > 0 && !row_perm) || (n > 0 && !col_perm)) return FM_EINVAL;
+    if (Am.log2_T < 2) return FM_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* status = fm_device_status();
+    if (!status) return FM_ECUDA;
+    *rank = 0;
+    // identity row permutation
+    {
+        std::vector<int32_t> id((size_t)m);
+        for (int64_t i = 0; i < m; ++i) id[(size_t)i] = (int32_t)i;
+        if (m) FM_CUDA_TRY(cudaMemcpyAsync(row_perm, id.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+        FM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // small device workspace: piv_slot[kNb], piv_row[kNb], order[kNb], n_piv, barrier[2]
+    int* ws = static_cast<int*>(fm_workspace(1, sizeof(int) * (3 * kNb + 4)));
+    if (!ws) return FM_ENOMEM;
+    int* d_slot = ws;
+    int* d_piv = ws + kNb;
+    int* d_order = ws + 2 * kNb;
+    int* d_npiv = ws + 3 * kNb;
+    unsigned* d_bar = reinterpret_cast<unsigned*>(ws + 3 * kNb + 2);
+    FM_CUDA_TRY(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
+
+    // cooperative grid for the panel kernel
+    int dev = 0, coop = 0, per_sm = 0;
+    FM_CUDA_TRY(cudaGetDevice(&dev));
+    FM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return FM_EUNSUPPORTED;
+    FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, kPanelThreads, 0));
+    if (per_sm < 1) return FM_EUNSUPPORTED;
+    const int grid = fm_sm_count() * std::min(per_sm, 2);
+    const uint64_t mu = ~0ull / p;
+
+    std::vector<int> colid((size_t)n);  // original column at each storage position
+    for (int64_t j = 0; j < n; ++j) colid[(size_t)j] = (int)j;
+    std::vector<int> pivot_pos, skipped_pos;
+    int64_t r = 0;
+    for (int64_t c0 = 0; c0 < n; c0 += kNb) {
+        const int w = (int)std::min<int64_t>(kNb, n - c0);
+        if (r >= m) {
+            for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
+            continue;
+        }
+        std::vector<int> slots(kNb, INT_MAX);
+        FM_CUDA_TRY(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int) * kNb, cudaMemcpyHostToDevice, s));
+        PanelArgs pa;
+        pa.A = Am.base;
+        pa.lt = Am.log2_T;
+        pa.m = m;
+        pa.r0 = r;
+        pa.c0 = c0;
+        pa.w = w;
+        pa.p = p;
+        pa.mu = mu;
+        pa.piv_slot = d_slot;
+        pa.piv_row = d_piv;
+        pa.n_piv = d_npiv;
+        pa.bar = d_bar;
+        pa.status = status;
+        void* kargs[] = {&pa};
+        FM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, grid, kPanelThreads, kargs,
+                                                0, s));
+        std::vector<int> piv(kNb);
+        int npiv = 0;
+        FM_CUDA_TRY(cudaMemcpyAsync(piv.data(), d_piv, sizeof(int) * w, cudaMemcpyDeviceToHost, s));
+        FM_CUDA_TRY(cudaMemcpyAsync(&npiv, d_npiv, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FM_CUDA_TRY(cudaStreamSynchronize(s));
+        int st = 0;
+        FM_CUDA_TRY(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st != 0) return st;
+        // pivot columns of the panel first, then its skipped columns
+        std::vector<int> order;
+        for (int t = 0; t < w; ++t)
+            if (piv[t] >= 0) order.push_back(t);
+        const int k = (int)order.size();
+        for (int t = 0; t < w; ++t)
+            if (piv[t] < 0) order.push_back(t);
+        bool moved = false;
+        for (int t = 0; t < w; ++t) moved |= order[t] != t;
+        if (moved) {
+            FM_CUDA_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * w, cudaMemcpyHostToDevice, s));
+            permute_panel_cols_kernel<<<std::max<int64_t>(1, std::min<int64_t>((m + 7) / 8, 4096)), 256, 0, s>>>(
+                Am.base, Am.log2_T, m, c0, w, d_order);
+            FM_CUDA_TRY(cudaGetLastError());
+            std::vector<int> ids(colid.begin() + c0, colid.begin() + c0 + w);
+            for (int t = 0; t < w; ++t) colid[(size_t)(c0 + t)] = ids[(size_t)order[t]];
+        }
+        for (int t = 0; t < k; ++t) pivot_pos.push_back((int)(c0 + t));
+        for (int t = k; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
+        if (k > 0) {
+            row_swaps_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)), 256, 0, s>>>(
+                Am.base, Am.log2_T, n, c0, w, r, d_piv, w);
+            FM_CUDA_TRY(cudaGetLastError());
+            perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
+            FM_CUDA_TRY(cudaGetLastError());
+            const int64_t cl = c0 + w;
+            if (cl < n) {
+                const int64_t cols = n - cl;
+                const size_t tsmem = (size_t)(kNb * kNb + kNb * kTrsmThreads) * 4;
+                FM_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tsmem));
+                const int narrow = (unsigned __int128)(p - 1) * (p - 1) * kNb < ((unsigned __int128)1 << 64);
+                trsm_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((cols + kTrsmThreads - 1) / kTrsmThreads, 4096)),
+                              kTrsmThreads, tsmem, s>>>(Am.base, Am.log2_T, r, c0, k, cl, n, p, narrow);
+                FM_CUDA_TRY(cudaGetLastError());
+                if (r + k < m) {
+                    const fm_sub C{Am, r + k, cl, m - r - k, cols};
+                    const fm_sub L21{Am, r + k, c0, m - r - k, k};
+                    const fm_sub U12{Am, r, cl, k, cols};
+                    FM_TRY(fm_gemm_modp(C, L21, U12, p, FM_OP_SUB, FM_ALGO_AUTO, nullptr, stream));
+                }
+            }
+        }
+        r += k;
+    }
+    // move every skipped column behind all pivot columns
+    std::vector<int> final_order(pivot_pos);
+    final_order.insert(final_order.end(), skipped_pos.begin(), skipped_pos.end());
+    bool moved = false;
+    for (int64_t t = 0; t < n; ++t) moved |= final_order[(size_t)t] != t;
+    std::vector<int32_t> cp((size_t)n);
+    for (int64_t t = 0; t < n; ++t) cp[(size_t)t] = colid[(size_t)final_order[(size_t)t]];
+    if (n) FM_CUDA_TRY(cudaMemcpyAsync(col_perm, cp.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    if (moved) {
+        if ((size_t)n * 4 > 200 * 1024) return FM_EUNSUPPORTED;  // a row must fit in shared memory
+        int32_t* d_ord = static_cast<int32_t*>(fm_workspace(3, (size_t)n * 4));
+        if (!d_ord) return FM_ENOMEM;
+        std::vector<int32_t> ord32(final_order.begin(), final_order.end());
+        FM_CUDA_TRY(cudaMemcpyAsync(d_ord, ord32.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        const size_t rsmem = (size_t)n * 4;
+        FM_CUDA_TRY(cudaFuncSetAttribute(permute_cols_rows_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
+        permute_cols_rows_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(m, (int64_t)fm_sm_count() * 4)),
+                                   256, rsmem, s>>>(Am.base, Am.log2_T, m, n, d_ord);
+        FM_CUDA_TRY(cudaGetLastError());
+    }
+    FM_CUDA_TRY(cudaStreamSynchronize(s));
+    *rank = r;
+    return FM_OK;
+}

@@ -29,6 +29,8 @@ EXPORTS = (
     "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_destroy", "fm_decompose",
     "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
+    "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
+    "fm_pluq",
 )
 
 
@@ -51,6 +53,15 @@ class fm_sub(ctypes.Structure):
 class fm_opts(ctypes.Structure):
     _fields_ = [("k_chunk", ctypes.c_int32), ("block_n", ctypes.c_int32),
                 ("no_karatsuba", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class fm_tune_result(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("log2_T", ctypes.c_int32), ("opts", fm_opts),
+                ("ms", ctypes.c_double), ("gops", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+FM_TUNE_NO_LIMB, FM_TUNE_NO_PLAIN = 1, 2
 
 
 class fm_gemm_call(ctypes.Structure):
@@ -94,6 +105,12 @@ def lib():
         "fm_limb_split": ([fm_sub, I32, U32, ctypes.POINTER(fm_opts), P, P], ctypes.c_int),
         "fm_limb_gemm": ([fm_sub, P, P, I64, U32, I32, ctypes.POINTER(fm_opts), P], ctypes.c_int),
         "fm_gemm_modp_noalloc": ([fm_sub, fm_sub, fm_sub, U32, I32, P], ctypes.c_int),
+        "fm_autotune": ([I64, I64, I64, U32, I32, P, ctypes.POINTER(fm_tune_result)], ctypes.c_int),
+        "fm_autotune_lookup": ([I64, I64, I64, U32, ctypes.POINTER(fm_tune_result)], ctypes.c_int),
+        "fm_autotune_save": ([ctypes.c_char_p], ctypes.c_int),
+        "fm_autotune_load": ([ctypes.c_char_p], ctypes.c_int),
+        "fm_autotune_clear": ([], ctypes.c_int),
+        "fm_pluq": ([fm_matrix, I64, I64, U32, P, P, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -276,6 +293,45 @@ def fm_limb_gemm(C: fm_sub, a_planes, b_planes, K: int, p: int, op: int = FM_OP_
     o = ctypes.byref(options) if options is not None else None
     return _check(lib().fm_limb_gemm(C, _ptr(a_planes), _ptr(b_planes), int(K), int(p), int(op),
                                      o, _stream(stream)), "fm_limb_gemm")
+
+
+def fm_autotune(M: int, N: int, K: int, p: int, flags: int = 0, stream=None) -> fm_tune_result:
+    """Times the candidate forms on scratch operands and remembers the fastest."""
+    r = fm_tune_result()
+    _check(lib().fm_autotune(int(M), int(N), int(K), int(p), int(flags), _stream(stream),
+                             ctypes.byref(r)), "fm_autotune")
+    return r
+
+
+def fm_autotune_lookup(M: int, N: int, K: int, p: int):
+    r = fm_tune_result()
+    hit = int(lib().fm_autotune_lookup(int(M), int(N), int(K), int(p), ctypes.byref(r)))
+    if hit < 0:
+        raise FmError(hit, "fm_autotune_lookup")
+    return r if hit else None
+
+
+def fm_autotune_save(path: str):
+    return _check(lib().fm_autotune_save(os.fsencode(path)), "fm_autotune_save")
+
+
+def fm_autotune_load(path: str) -> int:
+    r = int(lib().fm_autotune_load(os.fsencode(path)))
+    if r < 0:
+        raise FmError(r, "fm_autotune_load")
+    return r
+
+
+def fm_autotune_clear():
+    return _check(lib().fm_autotune_clear(), "fm_autotune_clear")
+
+
+def fm_pluq(A: fm_matrix, m: int, n: int, p: int, row_perm, col_perm, stream=None) -> int:
+    """In-place rank-revealing PLUQ of the leading m x n corner; returns the rank."""
+    r = ctypes.c_int64(0)
+    _check(lib().fm_pluq(A, int(m), int(n), int(p), _ptr(row_perm), _ptr(col_perm),
+                         ctypes.byref(r), _stream(stream)), "fm_pluq")
+    return int(r.value)
 
 
 def fm_get_last_device_status(stream=None) -> int:

@@ -87,3 +87,29 @@ def test_decompose_rejects_bad_operands(fm):
 def test_aligned_decomposition_is_one_product_per_tile_triple(fm):
     C, A, B = _subs(fm, 3, 5, (128, 64, 96, 32, 64, 0, 32, 64, 0))
     assert len(fm.fm_decompose(C, A, B)) == (128 // 32) * (64 // 32) * (96 // 32)
+
+
+def test_autotune_table_roundtrip(fm, tmp_path):
+    # host only: a saved table loads back, drives lookups, and malformed input is refused
+    fm.fm_autotune_clear()
+    assert fm.fm_autotune_lookup(8192, 8192, 8192, 65521) is None
+    table = tmp_path / "tune.txt"
+    table.write_text("# libfm autotune table v1\n"
+                     "13 13 13 1 2 7 256 960 0 2.500000 439804.651\n"
+                     "9 9 9 2 1 6 0 0 0 0.800000 335.544\n")
+    assert fm.fm_autotune_load(str(table)) == 2
+    r = fm.fm_autotune_lookup(8000, 5000, 4097, 65521)     # rounds up to 2^13 each
+    assert r is not None and r.algo == fm.FM_ALGO_LIMB_TC and r.opts.block_n == 256
+    assert r.opts.k_chunk == 960 and abs(r.ms - 2.5) < 1e-9
+    r2 = fm.fm_autotune_lookup(300, 400, 500, 2147483647)
+    assert r2 is not None and r2.algo == fm.FM_ALGO_PLAIN and r2.log2_T == 6
+    assert fm.fm_autotune_lookup(300, 400, 500, 65521) is None  # other modulus class
+    out = tmp_path / "tune2.txt"
+    fm.fm_autotune_save(str(out))
+    fm.fm_autotune_clear()
+    assert fm.fm_autotune_load(str(out)) == 2
+    bad = tmp_path / "bad.txt"
+    bad.write_text("1 2 3\n")
+    with pytest.raises(fm.FmError):
+        fm.fm_autotune_load(str(bad))
+    fm.fm_autotune_clear()
