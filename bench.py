@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip plain / DFMA comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-GEMM measurement")
+    ap.add_argument("--no-tu", action="store_true", help="skip the TU decomposition measurement")
     return ap.parse_args()
 
 
@@ -304,6 +305,61 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
             "launches": 1, "per_call_launches": count, "bit_identical_to_per_call": same}
 
 
+def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
+    """The TU decomposition workload: rank-revealing PLUQ over GF(65521) of an
+    m x n matrix built as the product of seeded uniform m x k and k x n factors
+    (rank k). Every trailing update is one fm_gemm_modp call. Timed once after
+    one warm-up factorisation of the same matrix."""
+    import numpy as np
+
+    import fm_inputs
+    p = P
+    lt = 7
+
+    def grid(r, c):
+        lg = 0
+        while (1 << lg) << lt < max(r, c):
+            lg += 1
+        return lg
+
+    def morton_from(x):
+        g = grid(*x.shape)
+        side = (1 << g) << lt
+        t = torch.zeros(side * side, dtype=torch.int32, device=dev)
+        mm = fm.matrix(t, g, lt)
+        src = torch.from_numpy(np.ascontiguousarray(x).view(np.int32)).to(dev)
+        fm.fm_layout_to_morton(src, x.shape[0], x.shape[1], x.shape[1], mm, stream)
+        return t, mm
+
+    tX, mX = morton_from(fm_inputs.uniform_residues(seed, (m, k), p, 1))
+    tY, mY = morton_from(fm_inputs.uniform_residues(seed, (k, n), p, 2))
+    g = grid(m, n)
+    side = (1 << g) << lt
+    tA = torch.zeros(side * side, dtype=torch.int32, device=dev)
+    mA = fm.matrix(tA, g, lt)
+    fm.fm_gemm_modp(fm.sub(mA, 0, 0, m, n), fm.sub(mX, 0, 0, m, k), fm.sub(mY, 0, 0, k, n), p,
+                    fm.FM_OP_SET, fm.FM_ALGO_LIMB_TC, None, stream)
+    del tX, tY
+    orig = tA.clone()
+    rp = torch.zeros(m, dtype=torch.int32, device=dev)
+    cp = torch.zeros(n, dtype=torch.int32, device=dev)
+    fm.fm_pluq(mA, m, n, p, rp, cp, stream)  # warm-up
+    tA.copy_(orig)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fm.fm_pluq(mA, m, n, p, rp, cp, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ops = 2.0 * (m * n * r - (m + n) * r * r / 2.0 + r ** 3 / 3.0)
+    del tA, orig
+    return {"workload": f"rank-revealing PLUQ over GF({p}) of {m}x{n}, rank {k} (product of "
+                        f"seeded uniform factors), 128-column panels, trailing updates via fm_gemm_modp",
+            "ms": ms, "rank": r, "rank_expected": k, "value": ops / (ms / 1e3) / 1e9, "unit": "Gop/s",
+            "ops": "2*(m n r - (m+n) r^2/2 + r^3/3)"}
+
+
 def run_fm(args, world, rank, local):
     import numpy as np
     import torch
@@ -503,6 +559,9 @@ def run_fm(args, world, rank, local):
     # ---- batching form: 4096 independent GEMMs, M, N, K uniform in [32, 512] ----
     if not args.no_batched:
         out["batched"] = run_batched(fm, torch, dev, stream, args)
+    # ---- TU decomposition of a rank-10000 16384 x 12288 matrix ----
+    if not args.no_tu:
+        out["tu"] = run_tu(fm, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
     burst, sustained, hbm, src = measured_peaks()
@@ -540,6 +599,8 @@ def run_fm(args, world, rank, local):
     }
     if "batched" in out:
         line["batched"] = out["batched"]
+    if "tu" in out:
+        line["tu"] = out["tu"]
     if "plain" in out:
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]

@@ -161,6 +161,10 @@ struct GemmCfg {
     static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 };
 
+// Persistent: one CTA per SM walks the output tiles blockIdx.x, + gridDim.x, ...
+// The producer and MMA warps run ahead into the next tile while the epilogue
+// finishes the previous one; barrier phases and the two TMEM accumulators carry
+// on across tiles (job counter T).
 template <int BN, bool FOLD>
 __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGemmArgs args)
 {
@@ -179,17 +183,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
     __shared__ uint32_t s_issued, s_consumed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = args.MB * args.NB;
+    const int njobs = args.first[args.n_products];  // jobs per tile
 
-    // output tile, grouped raster (groups of 8 row blocks) for L2 reuse
-    const int GROUP = 8;
-    const int per_group = GROUP * args.NB;
-    const int gidx = blockIdx.x / per_group;
-    const int first_mb = gidx * GROUP;
-    const int gsz = min(args.MB - first_mb, GROUP);
-    const int inner = blockIdx.x % per_group;
-    const int mb = first_mb + inner % gsz, nb = inner / gsz;
-
-    const int njobs = args.first[args.n_products];
+    // tile -> (mb, nb): grouped raster (groups of 8 row blocks) for L2 reuse
+    auto coords = [&](int tile, int& mb, int& nb) {
+        const int GROUP = 8;
+        const int per_group = GROUP * args.NB;
+        const int first_mb = (tile / per_group) * GROUP;
+        const int gsz = min(args.MB - first_mb, GROUP);
+        const int inner = tile % per_group;
+        mb = first_mb + inner % gsz;
+        nb = inner / gsz;
+    };
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -219,30 +225,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         if (lane == 0) {
             // ---- producer: one bulk copy per operand per stage ----
             uint32_t g = 0;
-            int idx = 0;
-            for (int t = 0; t < njobs && !*(volatile int*)&s_abort; ++t) {
-                while (t >= args.first[idx + 1]) ++idx;
-                const int c = t - args.first[idx];
-                const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
-                const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
-                                       ((size_t)mb * args.KB) * kATileBytes;
-                const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
-                                       ((size_t)nb * args.KB) * Cfg::kBTileBytes;
-                bool ok = true;
-                for (int kb = kb0; kb < kb1; ++kb, ++g) {
-                    const int s = g % S;
-                    const uint32_t ph = (g / S) & 1;
-                    if (!fm_mbar_wait(&empty_bar[s], ph ^ 1, args.status, &s_abort)) {
-                        ok = false;
-                        break;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int mb, nb;
+                coords(tile, mb, nb);
+                int idx = 0;
+                for (int t = 0; t < njobs && ok; ++t) {
+                    while (t >= args.first[idx + 1]) ++idx;
+                    const int c = t - args.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
+                                           ((size_t)mb * args.KB) * kATileBytes;
+                    const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
+                                           ((size_t)nb * args.KB) * Cfg::kBTileBytes;
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int s = g % S;
+                        const uint32_t ph = (g / S) & 1;
+                        if (!fm_mbar_wait(&empty_bar[s], ph ^ 1, args.status, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* sa = smem + (size_t)s * Cfg::kStageBytes;
+                        fm_mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
+                        fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
+                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * Cfg::kBTileBytes,
+                                    Cfg::kBTileBytes, &full_bar[s]);
                     }
-                    uint8_t* sa = smem + (size_t)s * Cfg::kStageBytes;
-                    fm_mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
-                    fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
-                    fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * Cfg::kBTileBytes,
-                                Cfg::kBTileBytes, &full_bar[s]);
                 }
-                if (!ok) break;
             }
             s_issued = g;
         }
@@ -250,43 +259,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         if (lane == 0) {
             // ---- MMA issuer ----
             const uint32_t idesc = fm_idesc_f16_f32(kBM, BN);
-            uint32_t g = 0;
+            uint32_t g = 0, T = 0;
             bool ok = true;
-            int idx = 0;
-            for (int t = 0; t < njobs && ok; ++t) {
-                const int b = t & 1;
-                while (t >= args.first[idx + 1]) ++idx;
-                const int c = t - args.first[idx];
-                const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
-                if (t >= 2 && !fm_mbar_wait(&acce_bar[b], ((t >> 1) - 1) & 1, args.status, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                fm_tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
-                bool first = true;
-                for (int kb = kb0; kb < kb1; ++kb, ++g) {
-                    const int s = g % S;
-                    const uint32_t ph = (g / S) & 1;
-                    if (!fm_mbar_wait(&full_bar[s], ph, args.status, &s_abort)) {
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int idx = 0;
+                for (int t = 0; t < njobs && ok; ++t, ++T) {
+                    const int b = T & 1;
+                    while (t >= args.first[idx + 1]) ++idx;
+                    const int c = t - args.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    if (T >= 2 &&
+                        !fm_mbar_wait(&acce_bar[b], ((T >> 1) - 1) & 1, args.status, &s_abort)) {
                         ok = false;
                         break;
                     }
                     fm_tc_fence_after();
-                    const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * Cfg::kStageBytes);
-                    const uint32_t b_addr = a_addr + kATileBytes;
+                    const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
+                    bool first = true;
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int s = g % S;
+                        const uint32_t ph = (g / S) & 1;
+                        if (!fm_mbar_wait(&full_bar[s], ph, args.status, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        fm_tc_fence_after();
+                        const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * Cfg::kStageBytes);
+                        const uint32_t b_addr = a_addr + kATileBytes;
 #pragma unroll
-                    for (int k = 0; k < kBK / 16; ++k) {
-                        const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
-                        const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
-                        const uint32_t acc = ((FOLD && t >= 2) || !first || k > 0) ? 1u : 0u;
-                        fm_mma_f16(d_tmem, ad, bd, idesc, acc);
+                        for (int k = 0; k < kBK / 16; ++k) {
+                            const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
+                            const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
+                            // fold form: from the third job of a tile on, each job
+                            // accumulates onto the residue folded back by the epilogue
+                            const uint32_t acc = ((FOLD && t >= 2) || !first || k > 0) ? 1u : 0u;
+                            fm_mma_f16(d_tmem, ad, bd, idesc, acc);
+                        }
+                        fm_mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+                        first = false;
                     }
-                    fm_mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
-                    first = false;
+                    if (!ok) break;
+                    fm_mma_commit(&accf_bar[b]);  // accumulator b complete for job T
                 }
-                if (!ok) break;
-                fm_mma_commit(&accf_bar[b]);  // accumulator b complete for job t
             }
             s_consumed = g;
             // every MMA issued by this thread has completed before TMEM is freed
@@ -301,122 +315,145 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const int half = ew >> 2;
-        constexpr int kCols = BN / 2;  // columns drained by this warp
+        constexpr int kCols = BN / 2;  // columns handled by this warp
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const uint32_t col0 = (uint32_t)(half * kCols);
         const uint32_t p = args.p;
+        const uint64_t cmask = (1ull << args.c_lt) - 1;
+        uint32_t T = 0;
         bool ok = true;
-        int idx = 0;
-        for (int t = 0; t < njobs; ++t) {
-            const int b = t & 1;
-            if (!fm_mbar_wait(&accf_bar[b], (t >> 1) & 1, args.status, &s_abort)) {
-                ok = false;
-                break;
-            }
-            fm_tc_fence_after();
-            while (t >= args.first[idx + 1]) ++idx;
-            const int c = t - args.first[idx];
-            const int n_chunks = args.first[idx + 1] - args.first[idx];
-            const bool last_on_buffer = (t + 2 >= njobs);
-            // fold form: the job two steps later on this buffer continues the
-            // same limb product (same weight) unless a product boundary lies between
-            int idx2 = idx;
-            if (!last_on_buffer)
-                while (t + 2 >= args.first[idx2 + 1]) ++idx2;
-            const bool same_next = !last_on_buffer && idx2 == idx;
-            const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
-            if (FOLD) {
-                const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
-#pragma unroll 1
-                for (int g = 0; g < kCols / 64; ++g) {  // two 32-column chunks in flight
-                    uint32_t v0[32], v1[32];
-                    fm_tmem_ld32(dbase + g * 64, v0);
-                    fm_tmem_ld32(dbase + g * 64 + 32, v1);
-                    fm_tmem_wait_ld();
-                    if (same_next) {
-                        fold_fp(v0, args.invp, args.pf);
-                        fold_fp(v1, args.invp, args.pf);
-                    } else {
-                        fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.offp);
-                        fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.offp);
-                    }
-                    fm_tmem_st32(dbase + g * 64, v0);
-                    fm_tmem_st32(dbase + g * 64 + 32, v1);
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            int mb, nb;
+            coords(tile, mb, nb);
+            int idx = 0;
+            for (int t = 0; t < njobs; ++t, ++T) {
+                const int b = T & 1;
+                if (!fm_mbar_wait(&accf_bar[b], (T >> 1) & 1, args.status, &s_abort)) {
+                    ok = false;
+                    break;
                 }
-            } else {
-                // residue form: S (exact int32 sum of this product's chunks) is
-                // folded into R at the product's last chunk and every 120 chunks
-                const bool s_fresh = (c % 120) == 0;
-                const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
-                const bool r_fresh = (idx == 0 && c < 120);
-                const uint32_t sbase = tmem + lane_base + (uint32_t)(3 * BN) + col0;
-                const uint32_t rbase = tmem + lane_base + (uint32_t)(2 * BN) + col0;
+                fm_tc_fence_after();
+                while (t >= args.first[idx + 1]) ++idx;
+                const int c = t - args.first[idx];
+                const int n_chunks = args.first[idx + 1] - args.first[idx];
+                const bool last_on_buffer = (t + 2 >= njobs);
+                // fold form: the job two steps later on this buffer continues the
+                // same limb product (same weight) unless a product boundary lies between
+                int idx2 = idx;
+                if (!last_on_buffer)
+                    while (t + 2 >= args.first[idx2 + 1]) ++idx2;
+                const bool same_next = !last_on_buffer && idx2 == idx;
+                const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
+                if (FOLD) {
+                    const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
-                for (int cc = 0; cc < kCols / 32; ++cc) {
-                    uint32_t v[32], sv[32];
-                    fm_tmem_ld32(dbase + cc * 32, v);
-                    if (!s_fresh) fm_tmem_ld32(sbase + cc * 32, sv);
-                    fm_tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
-                        sv[e] = (uint32_t)((s_fresh ? 0 : (int32_t)sv[e]) + d);
-                    }
-                    if (fold_now) {
-                        if (!r_fresh) {
-                            fm_tmem_ld32(rbase + cc * 32, v);
-                            fm_tmem_wait_ld();
+                    for (int g = 0; g < kCols / 64; ++g) {  // two 32-column chunks in flight
+                        uint32_t v0[32], v1[32];
+                        fm_tmem_ld32(dbase + g * 64, v0);
+                        fm_tmem_ld32(dbase + g * 64 + 32, v1);
+                        fm_tmem_wait_ld();
+                        if (same_next) {
+                            fold_fp(v0, args.invp, args.pf);
+                            fold_fp(v1, args.invp, args.pf);
+                        } else {
+                            fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.offp);
+                            fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.offp);
                         }
-                        const uint32_t wt = args.wt[idx];
+                        fm_tmem_st32(dbase + g * 64, v0);
+                        fm_tmem_st32(dbase + g * 64 + 32, v1);
+                    }
+                } else {
+                    // residue form: S (exact int32 sum of this product's chunks) is
+                    // folded into R at the product's last chunk and every 120 chunks
+                    const bool s_fresh = (c % 120) == 0;
+                    const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
+                    const bool r_fresh = (idx == 0 && c < 120);
+                    const uint32_t sbase = tmem + lane_base + (uint32_t)(3 * BN) + col0;
+                    const uint32_t rbase = tmem + lane_base + (uint32_t)(2 * BN) + col0;
+#pragma unroll 1
+                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                        uint32_t v[32], sv[32];
+                        fm_tmem_ld32(dbase + cc * 32, v);
+                        if (!s_fresh) fm_tmem_ld32(sbase + cc * 32, sv);
+                        fm_tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
-                            const uint64_t x =
-                                (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
-                            const uint32_t xm = barrett64(x, p, args.mu64);
-                            v[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : v[e]), p, args.mu64);
+                            const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+                            sv[e] = (uint32_t)((s_fresh ? 0 : (int32_t)sv[e]) + d);
                         }
-                        fm_tmem_st32(rbase + cc * 32, v);
-                    } else {
-                        fm_tmem_st32(sbase + cc * 32, sv);
+                        if (fold_now) {
+                            if (!r_fresh) {
+                                fm_tmem_ld32(rbase + cc * 32, v);
+                                fm_tmem_wait_ld();
+                            }
+                            const uint32_t wt = args.wt[idx];
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const uint64_t x =
+                                    (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
+                                const uint32_t xm = barrett64(x, p, args.mu64);
+                                v[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : v[e]), p,
+                                                 args.mu64);
+                            }
+                            fm_tmem_st32(rbase + cc * 32, v);
+                        } else {
+                            fm_tmem_st32(sbase + cc * 32, sv);
+                        }
                     }
                 }
+                fm_tmem_wait_st();
+                fm_tc_fence_before();
+                __syncwarp();
+                // fold form: a buffer holding one of the tile's two final residues is
+                // released only after the tile end below has read it
+                if (!(FOLD && last_on_buffer) && lane == 0) fm_mbar_arrive(&acce_bar[b]);
             }
-            fm_tmem_wait_st();
-            fm_tc_fence_before();
-            __syncwarp();
-            if (lane == 0) fm_mbar_arrive(&acce_bar[b]);
-        }
+            if (!ok) break;
 
-        // final residue -> combine with C -> Morton-hybrid write
-        if (ok) {
+            // ---- tile end: final residue -> combine with C -> Morton-hybrid write
             const int64_t gi = (int64_t)mb * kBM + quarter * 32 + lane;
-            const uint64_t cmask = (1ull << args.c_lt) - 1;
+            uint32_t rsrc;  // TMEM column base of the final residue
+            if (FOLD) {
+                const int by = (T - 1) & 1;  // buffer of the tile's last job
+                const int bx = by ^ 1;       // buffer of its second-to-last job
+                rsrc = (uint32_t)(by * BN);
+                if (njobs >= 2) {
+                    // y <- x + y mod p, then x is free for the next tile's first job
+                    const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
+                    const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
+#pragma unroll 1
+                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                        uint32_t xv[32], yv[32];
+                        fm_tmem_ld32(xb + cc * 32, xv);
+                        fm_tmem_ld32(yb + cc * 32, yv);
+                        fm_tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const uint32_t x = xv[e] + yv[e];
+                            yv[e] = x >= p ? x - p : x;
+                        }
+                        fm_tmem_st32(yb + cc * 32, yv);
+                    }
+                    fm_tmem_wait_st();
+                    fm_tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) fm_mbar_arrive(&acce_bar[bx]);
+                }
+            } else {
+                rsrc = (uint32_t)(2 * BN);
+            }
 #pragma unroll 1
             for (int cc = 0; cc < kCols / 32; ++cc) {
                 uint32_t sres[32];
                 const uint32_t col = col0 + cc * 32;
-                if (FOLD) {
-                    fm_tmem_ld32(tmem + lane_base + col, sres);
-                    if (njobs >= 2) {
-                        uint32_t s1[32];
-                        fm_tmem_ld32(tmem + lane_base + (uint32_t)BN + col, s1);
-                        fm_tmem_wait_ld();
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const uint32_t x = sres[e] + s1[e];
-                            sres[e] = x >= p ? x - p : x;
-                        }
-                    } else {
-                        fm_tmem_wait_ld();
-                    }
-                } else {
-                    fm_tmem_ld32(tmem + lane_base + (uint32_t)(2 * BN) + col, sres);
-                    fm_tmem_wait_ld();
-                }
-                if (gi < args.M) {
-                    const int64_t j0 = (int64_t)nb * BN + col;
-                    write_c_run(args, gi, j0, cmask, sres);
-                }
+                fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
+                fm_tmem_wait_ld();
+                if (gi < args.M) write_c_run(args, gi, (int64_t)nb * BN + col, cmask, sres);
+            }
+            if (FOLD) {
+                fm_tc_fence_before();
+                __syncwarp();
+                if (lane == 0) fm_mbar_arrive(&acce_bar[(T - 1) & 1]);
             }
         }
     }
@@ -611,7 +648,7 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.M = q.M;
     a.N = q.N;
     a.status = status;
-    const int grid = q.MB * q.NB;
+    const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);
         return launch_gemm<128, true>(a, grid, s);
