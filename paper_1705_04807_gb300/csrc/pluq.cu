@@ -19,11 +19,14 @@
 //   finally the skipped columns of every panel are moved behind all pivot
 //   columns.
 //
-// Step 1 runs as one cooperative launch with a grid barrier per column. The
-// barrier is bounded: a wait that expires raises FM_ETIMEOUT and every CTA
-// leaves the kernel.
+// Step 1 runs as one cooperative launch: each CTA keeps its share of the panel
+// rows in shared memory and one grid barrier per column selects the pivot (a
+// global-memory variant serves panels too tall for shared memory). The barrier
+// is bounded: a wait that expires raises FM_ETIMEOUT and every CTA leaves the
+// kernel.
 #include <algorithm>
 #include <climits>
+#include <unordered_map>
 #include <vector>
 
 #include "fm_internal.cuh"
@@ -245,45 +248,6 @@ __global__ void perm_swaps_kernel(int32_t* rp, int64_t r0, const int* __restrict
     }
 }
 
-// U12 <- L11^-1 A12: rows [r0, r0 + k) x columns [cl, n), L11 = the unit lower
-// triangle of rows [r0, r0 + k) x columns [c0, c0 + k). One thread per column,
-// forward substitution; L11 and the solved column live in shared memory.
-constexpr int kTrsmThreads = 128;
-__global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(uint32_t* A, int lt, int64_t r0,
-                                                            int64_t c0, int k, int64_t cl, int64_t n,
-                                                            uint32_t p, int narrow)
-{
-    extern __shared__ uint32_t sm[];
-    uint32_t* L = sm;                       // [k][k]
-    uint32_t* xs = sm + kNb * kNb;          // [k][kTrsmThreads]
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        const int i = e / k, t = e % k;
-        L[i * kNb + t] = t < i ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
-    }
-    __syncthreads();
-    for (int64_t jb = cl + blockIdx.x * (int64_t)blockDim.x; jb < n; jb += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = jb + threadIdx.x;
-        if (j < n) {
-            for (int i = 0; i < k; ++i) {
-                uint32_t s;
-                if (narrow) {  // (p-1)^2 * k < 2^64
-                    uint64_t acc = 0;
-                    for (int t = 0; t < i; ++t) acc += (uint64_t)L[i * kNb + t] * xs[t * kTrsmThreads + threadIdx.x];
-                    s = (uint32_t)(acc % p);
-                } else {
-                    unsigned __int128 acc = 0;
-                    for (int t = 0; t < i; ++t) acc += (uint64_t)L[i * kNb + t] * xs[t * kTrsmThreads + threadIdx.x];
-                    s = (uint32_t)(acc % p);
-                }
-                uint32_t* a = A + fm_encode((uint64_t)(r0 + i), (uint64_t)j, lt);
-                const uint32_t x = submod(*a, s, p);
-                xs[i * kTrsmThreads + threadIdx.x] = x;
-                *a = x;
-            }
-        }
-    }
-}
-
 // Columns of rows [0, m) reordered in place: new column t = old column ord[t],
 // t < n. One CTA per row at a time, the row staged in shared memory.
 __global__ void permute_cols_rows_kernel(uint32_t* A, int lt, int64_t m, int64_t n,
@@ -297,6 +261,194 @@ __global__ void permute_cols_rows_kernel(uint32_t* A, int lt, int64_t m, int64_t
         for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
             A[fm_encode((uint64_t)i, (uint64_t)t, lt)] = row[ord[t]];
         __syncthreads();
+    }
+}
+
+// Extended Euclid: inverse of a unit a modulo p < 2^31, in 32-bit arithmetic
+// (every remainder and coefficient stays below p in magnitude).
+__host__ __device__ __forceinline__ uint32_t inv_euclid(uint32_t a, uint32_t p)
+{
+    int32_t t = 0, nt = 1;
+    uint32_t r = p, nr = a;
+    while (nr != 0) {
+        const uint32_t q = r / nr;
+        const int32_t tmp = t - (int32_t)q * nt;
+        t = nt;
+        nt = tmp;
+        const uint32_t rr = r - q * nr;
+        r = nr;
+        nr = rr;
+    }
+    return (uint32_t)(t < 0 ? t + (int32_t)p : t);
+}
+
+struct SmemPanelArgs {
+    uint32_t* A;
+    int lt;
+    int64_t m, r0, c0;
+    int w;
+    int rows_per_cta;  // R: CTA b owns rows [r0 + b R, r0 + (b+1) R) of the panel
+    uint32_t p;
+    uint64_t mu;
+    int* slot;         // [w] smallest candidate row per column (INT_MAX before)
+    uint32_t* cand;    // [2][gridDim.x][w + 2]: candidate row values, inverse, row
+    int* piv_row;      // out [w]: pivot row of column t (original index) or -1
+    int* n_piv;        // out
+    unsigned* bar;
+    int* status;
+};
+
+// Panel factorisation with the panel rows resident in shared memory: per column
+// each CTA offers its first non-pivot row with a nonzero entry, one grid
+// barrier picks the smallest row index, every CTA reads that row and updates
+// its own non-pivot rows. Rows are not moved; the pivot order is returned.
+__global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const SmemPanelArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    const int R = a.rows_per_cta, w = a.w;
+    uint32_t* rows = sm;                                   // [R][w]
+    uint32_t* prow = rows + (size_t)R * w;                 // [w]
+    int* piv_flag = reinterpret_cast<int*>(prow + kNb);    // [R]
+    __shared__ int s_abort, s_first;
+    __shared__ uint32_t s_inv;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = a.r0 + (int64_t)blockIdx.x * R;
+    const int64_t left = a.m - row0;
+    const int nrows = left <= 0 ? 0 : (left < R ? (int)left : R);
+    if (tid == 0) s_abort = 0;
+    for (int e = tid; e < R * w; e += kPanelThreads) {
+        const int i = e / w, c = e % w;
+        rows[e] = i < nrows ? a.A[fm_encode((uint64_t)(row0 + i), (uint64_t)(a.c0 + c), a.lt)] : 0u;
+    }
+    for (int i = tid; i < R; i += kPanelThreads) piv_flag[i] = 0;
+    __syncthreads();
+    int found = 0;
+    for (int t = 0; t < w; ++t) {
+        uint32_t* cbuf = a.cand + ((size_t)(t & 1) * gridDim.x + blockIdx.x) * (w + 2);
+        // 1. this CTA's candidate: first non-pivot row with a nonzero in column t
+        if (tid == 0) s_first = INT_MAX;
+        __syncthreads();
+        for (int i = tid; i < nrows; i += kPanelThreads)
+            if (!piv_flag[i] && rows[(size_t)i * w + t] != 0) atomicMin(&s_first, i);
+        __syncthreads();
+        const int li = s_first;
+        if (li != INT_MAX) {
+            for (int c = tid; c < w; c += kPanelThreads) cbuf[c] = rows[(size_t)li * w + c];
+            if (tid == 0) {
+                cbuf[w] = inv_euclid(rows[(size_t)li * w + t], a.p);
+                cbuf[w + 1] = (uint32_t)(row0 + li);
+            }
+            __threadfence();  // every writer: the candidate is visible before its index
+            __syncthreads();
+            if (tid == 0) atomicMin(&a.slot[t], (int)(row0 + li));
+        }
+        // 2. one barrier: every candidate is published
+        if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+        const int piv = *(volatile int*)&a.slot[t];
+        if (piv == INT_MAX) {  // no nonzero left in this column: a non-pivot column
+            if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = -1;
+            continue;
+        }
+        // 3. the pivot row from its owner's candidate slot
+        const int owner = (int)((piv - a.r0) / R);
+        const volatile uint32_t* ob =
+            a.cand + ((size_t)(t & 1) * gridDim.x + owner) * (w + 2);
+        for (int c = tid; c < w; c += kPanelThreads) prow[c] = ob[c];
+        if (tid == 0) s_inv = ob[w];
+        if (owner == (int)blockIdx.x && tid == 0) piv_flag[piv - row0] = 1;
+        if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = piv;
+        __syncthreads();
+        const uint32_t inv = s_inv;
+        // 4. update the non-pivot rows: a_i <- a_i - l_i * pivot row (columns > t), l_i in column t
+        for (int i = warp; i < nrows; i += kPanelThreads / 32) {
+            if (piv_flag[i]) continue;
+            uint32_t* ri = rows + (size_t)i * w;
+            const uint32_t l = mulmod(ri[t], inv, a.p, a.mu);
+            if (l != 0)
+                for (int c = t + 1 + lane; c < w; c += 32)
+                    ri[c] = submod(ri[c], mulmod(l, prow[c], a.p, a.mu), a.p);
+            __syncwarp();
+            if (lane == 0) ri[t] = l;
+        }
+        __syncthreads();
+        ++found;
+    }
+    for (int e = tid; e < nrows * w; e += kPanelThreads) {
+        const int i = e / w, c = e % w;
+        a.A[fm_encode((uint64_t)(row0 + i), (uint64_t)(a.c0 + c), a.lt)] = rows[e];
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.n_piv = found;
+}
+
+// Row swaps (pairs (x, y) in order) on columns [0, n) and on the permutation.
+__global__ void swap_pairs_kernel(uint32_t* A, int lt, int64_t n, const int* __restrict__ pairs,
+                                  int npairs, int32_t* rp)
+{
+    if (rp && blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int q = 0; q < npairs; ++q) {
+            const int x = pairs[2 * q], y = pairs[2 * q + 1];
+            const int32_t tmp = rp[x];
+            rp[x] = rp[y];
+            rp[y] = tmp;
+        }
+    }
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        for (int q = 0; q < npairs; ++q) {
+            uint32_t* x = A + fm_encode((uint64_t)pairs[2 * q], (uint64_t)j, lt);
+            uint32_t* y = A + fm_encode((uint64_t)pairs[2 * q + 1], (uint64_t)j, lt);
+            const uint32_t tmp = *x;
+            *x = *y;
+            *y = tmp;
+        }
+    }
+}
+
+// U12 <- L11^-1 A12 on rows [r0, r0+k) x columns [cl, n), L11 the unit lower
+// triangle of rows [r0, r0+k) x columns [c0, c0+k). Each CTA stages L11 and a
+// block of 32 columns in shared memory and runs the forward substitution row by
+// row, 8 threads sharing each column's dot product.
+constexpr int kTrsmCols = 32;
+constexpr int kTrsmThreads = 256;
+__global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(uint32_t* A, int lt, int64_t r0, int64_t c0,
+                                                            int k, int64_t cl, int64_t n, uint32_t p,
+                                                            uint64_t mu)
+{
+    extern __shared__ uint32_t smx[];
+    uint32_t* L = smx;                    // [k][k]
+    uint32_t* X = smx + (size_t)k * k;    // [k][kTrsmCols]
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, t = e % k;
+        L[e] = t < i ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
+    }
+    const int c = threadIdx.x >> 3, sub = threadIdx.x & 7;  // column in block, share of the sum
+    for (int64_t jb = cl + (int64_t)blockIdx.x * kTrsmCols; jb < n; jb += (int64_t)gridDim.x * kTrsmCols) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < k * kTrsmCols; e += blockDim.x) {
+            const int i = e / kTrsmCols, cc = e % kTrsmCols;
+            X[e] = jb + cc < n ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(jb + cc), lt)] : 0u;
+        }
+        __syncthreads();
+        for (int i = 1; i < k; ++i) {
+            // x_i -= sum_{t<i} L[i][t] x_t; partial sums reduced mod p before combining
+            uint64_t acc = 0;
+            for (int t = sub; t < i; t += 8) {
+                acc += (uint64_t)mulmod(L[i * k + t], X[t * kTrsmCols + c], p, mu);
+            }
+            uint32_t part = (uint32_t)(acc % p);
+#pragma unroll
+            for (int o = 4; o >= 1; o >>= 1) {
+                const uint32_t other = __shfl_xor_sync(0xffffffffu, part, o);
+                const uint32_t sum = part + other;
+                part = sum >= p ? sum - p : sum;
+            }
+            if (sub == 0) X[i * kTrsmCols + c] = submod(X[i * kTrsmCols + c], part, p);
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < k * kTrsmCols; e += blockDim.x) {
+            const int i = e / kTrsmCols, cc = e % kTrsmCols;
+            if (jb + cc < n) A[fm_encode((uint64_t)(r0 + i), (uint64_t)(jb + cc), lt)] = X[e];
+        }
     }
 }
 
@@ -322,24 +474,29 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         if (m) FM_CUDA_TRY(cudaMemcpyAsync(row_perm, id.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
         FM_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // small device workspace: piv_slot[kNb], piv_row[kNb], order[kNb], n_piv, barrier[2]
-    int* ws = static_cast<int*>(fm_workspace(1, sizeof(int) * (3 * kNb + 4)));
+    // device workspace: piv_slot[kNb], piv_row[kNb], order[kNb], n_piv, barrier[2],
+    // swap pairs[2 kNb], candidate rows [2][grid][kNb + 2]
+    int dev = 0, coop = 0, per_sm = 0, max_smem = 0;
+    FM_CUDA_TRY(cudaGetDevice(&dev));
+    FM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    FM_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (!coop) return FM_EUNSUPPORTED;
+    const int sms = fm_sm_count();
+    const size_t ws_ints = 3 * kNb + 4 + 2 * kNb + 2 * (size_t)sms * (kNb + 2);
+    int* ws = static_cast<int*>(fm_workspace(1, sizeof(int) * ws_ints));
     if (!ws) return FM_ENOMEM;
     int* d_slot = ws;
     int* d_piv = ws + kNb;
     int* d_order = ws + 2 * kNb;
     int* d_npiv = ws + 3 * kNb;
     unsigned* d_bar = reinterpret_cast<unsigned*>(ws + 3 * kNb + 2);
+    int* d_pairs = ws + 3 * kNb + 4;
+    uint32_t* d_cand = reinterpret_cast<uint32_t*>(ws + 5 * kNb + 4);
     FM_CUDA_TRY(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
 
-    // cooperative grid for the panel kernel
-    int dev = 0, coop = 0, per_sm = 0;
-    FM_CUDA_TRY(cudaGetDevice(&dev));
-    FM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    if (!coop) return FM_EUNSUPPORTED;
     FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, kPanelThreads, 0));
     if (per_sm < 1) return FM_EUNSUPPORTED;
-    const int grid = fm_sm_count() * std::min(per_sm, 2);
+    const int grid_g = sms * std::min(per_sm, 2);  // global-memory panel kernel
     const uint64_t mu = ~0ull / p;
 
     std::vector<int> colid((size_t)n);  // original column at each storage position
@@ -354,23 +511,51 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         }
         std::vector<int> slots(kNb, INT_MAX);
         FM_CUDA_TRY(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int) * kNb, cudaMemcpyHostToDevice, s));
-        PanelArgs pa;
-        pa.A = Am.base;
-        pa.lt = Am.log2_T;
-        pa.m = m;
-        pa.r0 = r;
-        pa.c0 = c0;
-        pa.w = w;
-        pa.p = p;
-        pa.mu = mu;
-        pa.piv_slot = d_slot;
-        pa.piv_row = d_piv;
-        pa.n_piv = d_npiv;
-        pa.bar = d_bar;
-        pa.status = status;
-        void* kargs[] = {&pa};
-        FM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, grid, kPanelThreads, kargs,
-                                                0, s));
+        // panel rows resident in shared memory when a CTA's share fits
+        const int R = (int)((m - r + sms - 1) / sms);
+        const size_t psmem = ((size_t)R * w + kNb + R) * 4;
+        const bool smem_path = psmem <= (size_t)max_smem;
+        if (smem_path) {
+            SmemPanelArgs pa;
+            pa.A = Am.base;
+            pa.lt = Am.log2_T;
+            pa.m = m;
+            pa.r0 = r;
+            pa.c0 = c0;
+            pa.w = w;
+            pa.rows_per_cta = R;
+            pa.p = p;
+            pa.mu = mu;
+            pa.slot = d_slot;
+            pa.cand = d_cand;
+            pa.piv_row = d_piv;
+            pa.n_piv = d_npiv;
+            pa.bar = d_bar;
+            pa.status = status;
+            FM_CUDA_TRY(cudaFuncSetAttribute(smem_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)psmem));
+            void* kargs[] = {&pa};
+            FM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)smem_panel_kernel, sms, kPanelThreads,
+                                                    kargs, psmem, s));
+        } else {
+            PanelArgs pa;
+            pa.A = Am.base;
+            pa.lt = Am.log2_T;
+            pa.m = m;
+            pa.r0 = r;
+            pa.c0 = c0;
+            pa.w = w;
+            pa.p = p;
+            pa.mu = mu;
+            pa.piv_slot = d_slot;
+            pa.piv_row = d_piv;
+            pa.n_piv = d_npiv;
+            pa.bar = d_bar;
+            pa.status = status;
+            void* kargs[] = {&pa};
+            FM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, grid_g, kPanelThreads,
+                                                    kargs, 0, s));
+        }
         std::vector<int> piv(kNb);
         int npiv = 0;
         FM_CUDA_TRY(cudaMemcpyAsync(piv.data(), d_piv, sizeof(int) * w, cudaMemcpyDeviceToHost, s));
@@ -399,20 +584,56 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         for (int t = 0; t < k; ++t) pivot_pos.push_back((int)(c0 + t));
         for (int t = k; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
         if (k > 0) {
-            row_swaps_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)), 256, 0, s>>>(
-                Am.base, Am.log2_T, n, c0, w, r, d_piv, w);
-            FM_CUDA_TRY(cudaGetLastError());
-            perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
-            FM_CUDA_TRY(cudaGetLastError());
+            const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048));
+            if (smem_path) {
+                // the panel left rows in place: bring the k pivot rows to r .. r+k-1
+                std::unordered_map<int, int> pos_of, row_at;  // rows moved so far
+                auto where = [&](int row) {
+                    auto it = pos_of.find(row);
+                    return it == pos_of.end() ? row : it->second;
+                };
+                auto who = [&](int pos) {
+                    auto it = row_at.find(pos);
+                    return it == row_at.end() ? pos : it->second;
+                };
+                std::vector<int> pairs;
+                int q = 0;
+                for (int t = 0; t < w; ++t) {
+                    if (piv[t] < 0) continue;
+                    const int target = (int)(r + q);
+                    const int cur = where(piv[t]);
+                    if (cur != target) {
+                        const int displaced = who(target);
+                        pairs.push_back(target);
+                        pairs.push_back(cur);
+                        pos_of[piv[t]] = target;
+                        row_at[target] = piv[t];
+                        pos_of[displaced] = cur;
+                        row_at[cur] = displaced;
+                    }
+                    ++q;
+                }
+                const int npairs = (int)pairs.size() / 2;
+                if (npairs > 0) {
+                    FM_CUDA_TRY(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int) * pairs.size(),
+                                                cudaMemcpyHostToDevice, s));
+                    swap_pairs_kernel<<<sgrid, 256, 0, s>>>(Am.base, Am.log2_T, n, d_pairs, npairs, row_perm);
+                    FM_CUDA_TRY(cudaGetLastError());
+                }
+            } else {
+                row_swaps_kernel<<<sgrid, 256, 0, s>>>(Am.base, Am.log2_T, n, c0, w, r, d_piv, w);
+                FM_CUDA_TRY(cudaGetLastError());
+                perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
+                FM_CUDA_TRY(cudaGetLastError());
+            }
             const int64_t cl = c0 + w;
             if (cl < n) {
                 const int64_t cols = n - cl;
-                const size_t tsmem = (size_t)(kNb * kNb + kNb * kTrsmThreads) * 4;
+                const size_t tsmem = ((size_t)k * k + (size_t)k * kTrsmCols) * 4;
                 FM_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)tsmem));
-                const int narrow = (unsigned __int128)(p - 1) * (p - 1) * kNb < ((unsigned __int128)1 << 64);
-                trsm_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((cols + kTrsmThreads - 1) / kTrsmThreads, 4096)),
-                              kTrsmThreads, tsmem, s>>>(Am.base, Am.log2_T, r, c0, k, cl, n, p, narrow);
+                trsm_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((cols + kTrsmCols - 1) / kTrsmCols, 4096)),
+                              kTrsmThreads, tsmem, s>>>(Am.base, Am.log2_T, r, c0, k, cl, n, p, mu);
                 FM_CUDA_TRY(cudaGetLastError());
                 if (r + k < m) {
                     const fm_sub C{Am, r + k, cl, m - r - k, cols};
