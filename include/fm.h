@@ -88,7 +88,10 @@ typedef struct fm_opts {
     int32_t k_chunk;        /* limb form: K elements per exact accumulation chunk  */
     int32_t block_n;        /* limb form: output tile width, 128 or 256            */
     int32_t no_karatsuba;   /* limb form: 1 = four limb products instead of three  */
-    int32_t reserved[5];
+    int32_t cta_pair;       /* limb form, block_n 256, p < 2^16: 1 = a CTA pair
+                               (cta_group::2) per 256 x 256 output tile instead
+                               of one CTA per 128 x 256 tile                    */
+    int32_t reserved[4];
 } fm_opts;
 
 /* ---- layout and permutation (Sec. 1; HBM-bound gathers) ---------------- */
@@ -152,8 +155,9 @@ int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uint32_t p, in
  * is odd and fm_opts.no_karatsuba is 0, a third plane holds d_0 + d_1 and the
  * product runs three limb GEMMs (Karatsuba: A*B = (1-256) A0*B0
  * + 256 (A0+A1)*(B0+B1) + (2^16-256) A1*B1) instead of four.
- *   role FM_LIMB_A (an M x K operand): plane t holds ceil(M/128) x ceil(K/64)
- *     tiles in row-block-major order, each 128 rows x 64 k (16 KB).
+ *   role FM_LIMB_A (an M x K operand): plane t holds MB x ceil(K/64) tiles in
+ *     row-block-major order, each 128 rows x 64 k (16 KB); MB = ceil(M/128),
+ *     rounded up to even when BN = 256 (a CTA pair takes two row blocks).
  *   role FM_LIMB_B (a K x N operand, stored transposed): plane t holds
  *     ceil(N/BN) x ceil(K/64) tiles, each BN rows (n) x 64 k (BN * 128 bytes),
  *     BN = the product's output tile width (fm_opts.block_n; default 256 when

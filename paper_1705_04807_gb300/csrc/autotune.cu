@@ -106,7 +106,7 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
     cudaStream_t s = (cudaStream_t)stream;
     // candidates
     std::vector<Candidate> cands;
-    auto limb = [&](int bn, int kchunk, int no_kara) {
+    auto limb = [&](int bn, int kchunk, int no_kara, int pair) {
         Candidate c;
         std::memset(&c, 0, sizeof(c));
         c.algo = FM_ALGO_LIMB_TC;
@@ -114,6 +114,7 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
         c.opts.block_n = bn;
         c.opts.k_chunk = kchunk;
         c.opts.no_karatsuba = no_kara;
+        c.opts.cta_pair = pair;
         cands.push_back(c);
     };
     if (!(flags & FM_TUNE_NO_LIMB)) {
@@ -124,8 +125,11 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
                 if (!q.fold && bn == 256) continue;
                 for (int kc : {full, full / 2}) {
                     if (kc < 64 || kc % 64) continue;
-                    limb(bn, kc, 0);
-                    if (q.n_planes == 3) limb(bn, kc, 1);
+                    for (int pair : {0, 1}) {
+                        if (pair && bn != 256) continue;
+                        limb(bn, kc, 0, pair);
+                        if (q.n_planes == 3) limb(bn, kc, 1, pair);
+                    }
                 }
             }
         }
@@ -207,7 +211,8 @@ bool fm_tuned_choice(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result
 }
 
 // Text format, one class per line:
-//   mc nc kc pc algo log2_T block_n k_chunk no_karatsuba ms gops
+//   mc nc kc pc algo log2_T block_n k_chunk no_karatsuba ms gops [cta_pair]
+// (a missing last field reads as 0).
 extern "C" int fm_autotune_save(const char* path)
 {
     if (!path) return FM_EINVAL;
@@ -215,12 +220,13 @@ extern "C" int fm_autotune_save(const char* path)
     if (!f) return FM_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     std::fprintf(f, "# libfm autotune table v1: mc nc kc pc algo log2_T block_n k_chunk "
-                    "no_karatsuba ms gops\n");
+                    "no_karatsuba ms gops cta_pair\n");
     for (const auto& kv : g_tune) {
         const TuneKey& k = kv.first;
         const fm_tune_result& r = kv.second;
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f %.3f\n", k.mc, k.nc, k.kc, k.pc, r.algo,
-                     r.log2_T, r.opts.block_n, r.opts.k_chunk, r.opts.no_karatsuba, r.ms, r.gops);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f %.3f %d\n", k.mc, k.nc, k.kc, k.pc, r.algo,
+                     r.log2_T, r.opts.block_n, r.opts.k_chunk, r.opts.no_karatsuba, r.ms, r.gops,
+                     r.opts.cta_pair);
     }
     std::fclose(f);
     return FM_OK;
@@ -239,9 +245,11 @@ extern "C" int fm_autotune_load(const char* path)
         TuneKey k;
         fm_tune_result r;
         std::memset(&r, 0, sizeof(r));
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %lf %lf", &k.mc, &k.nc, &k.kc, &k.pc,
-                        &r.algo, &r.log2_T, &r.opts.block_n, &r.opts.k_chunk,
-                        &r.opts.no_karatsuba, &r.ms, &r.gops) != 11) {
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %lf %lf %d", &k.mc, &k.nc,
+                                    &k.kc, &k.pc, &r.algo, &r.log2_T, &r.opts.block_n,
+                                    &r.opts.k_chunk, &r.opts.no_karatsuba, &r.ms, &r.gops,
+                                    &r.opts.cta_pair);
+        if (got != 11 && got != 12) {
             std::fclose(f);
             return FM_EINVAL;
         }

@@ -286,6 +286,118 @@ __device__ __forceinline__ void fm_tmem_st32(uint32_t taddr, const uint32_t (&r)
         : "memory");
 }
 
+// ---- clusters and the CTA-pair (cta_group::2) forms ----
+__device__ __forceinline__ uint32_t fm_cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t fm_mapa(uint32_t saddr, uint32_t rank)
+{
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
+    return d;
+}
+
+// Arrive on an mbarrier of any CTA of the cluster (release at cluster scope).
+__device__ __forceinline__ void fm_mbar_arrive_cluster(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+
+// Arrive on an mbarrier of any CTA of the cluster with the default (CTA-scope
+// release) semantics: orders this thread's tcgen05 work fenced before it, not
+// its global stores, so it costs no cluster-wide fence.
+__device__ __forceinline__ void fm_mbar_arrive_remote(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool fm_mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(fm_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait with cluster-scope acquire (arrivals may come from the peer CTA).
+__device__ __forceinline__ bool fm_mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* status,
+                                                     volatile int* abort)
+{
+    if (fm_mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = fm_globaltimer();
+    while (true) {
+        if (fm_mbar_try_wait_cluster(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
+            fm_raise(status, FM_ETIMEOUT);
+            if (abort) *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fm_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                     "memory");
+}
+
+// Tensor memory of a CTA pair: one warp of each CTA of the pair executes these together.
+__device__ __forceinline__ void fm_tmem_alloc_pair(uint32_t* smem_dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     fm_smem_u32(smem_dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fm_tmem_relinquish_pair()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fm_tmem_dealloc_pair(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// D (+)= A * B on a CTA pair (issued by the even CTA): A and D split by rows
+// (each CTA holds M/2 rows of A at the same shared-memory offset and M/2 lanes
+// of D), B split by columns (each CTA holds N/2 rows of the K-major B tile).
+__device__ __forceinline__ void fm_mma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the mbarrier at this shared-memory offset in every CTA of cta_mask
+// once all previously issued tcgen05 ops of this thread have completed.
+__device__ __forceinline__ void fm_mma_commit_pair(uint64_t* bar, uint16_t cta_mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(fm_smem_u32(bar)),
+        "h"(cta_mask)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor for a K-major operand in the 128-byte
 // swizzled layout: rows of 64 f16 (128 B), 8-row groups 1024 B apart. The tile
 // base must be 1024-byte aligned; advancing along K by 16 elements adds 32 B

@@ -30,6 +30,7 @@ struct FmLimbPlan {
     uint32_t prod_w[16];         // weight of product k, mod p
     int block_n;      // 128 or 256
     int fold;         // 1: residue folded into the fp32 accumulator (p < 2^16)
+    int pair;         // 1: CTA pairs (cta_group::2) on 256 x 256 tiles (fold form, BN 256)
     int MB, NB, KB;
     size_t a_plane_bytes, b_plane_bytes;  // bytes of ONE plane
 };

@@ -70,7 +70,7 @@ struct LimbGemmArgs {
     int pa[16], pb[16];  // planes of A and B of product k
     int cs[16];          // 64-wide K stages per chunk of product k
     int first[17];       // first job of product k; first[n_products] = number of jobs
-    uint32_t p, mu32, offp;
+    uint32_t p, mu32;
     uint64_t mu64;
     uint32_t wt[16];  // weight of product k mod p
     uint32_t cn[16];  // fold form: cn[k * 4 + k2] = wt[k] * wt[k2]^-1 mod p
@@ -82,50 +82,66 @@ struct LimbGemmArgs {
     int* status;
 };
 
-// Fold-form drains. fold_fp: v - rint(v/p) p in FP32, exact because |v| < 2^24
-// (the result stays a carried value of magnitude <= 2p). fold_int: the value
-// times mul mod p, as a float to carry on (to_float) or as the final residue.
+// Fold-form drains. Every accumulator value v is an integer with |v| <= 2^24
+// and |v / p| < 2^22: for p > 4 because |v| <= 2^24, for p <= 4 because the
+// limbs are then below p in magnitude, so |v| <= 960 p^2 + 2p. In that range
+// round-to-nearest of v / p is one FMA with the constant 1.5 * 2^23 (the sum
+// lands where the float spacing is 1) and one subtraction, both on the FMA
+// pipe; conversions between small integers and floats use the same bias.
+// fold_fp: v - round(v/p) p, exact, a carried value of magnitude <= p/2 + 1.
+// fold_int: that value times mul mod p, as a float to carry on (to_float) or
+// as the final residue in [0, p).
+constexpr float kRoundBias = 12582912.0f;  // 1.5 * 2^23
+constexpr uint32_t kRoundBiasBits = 0x4B400000u;
+
+__device__ __forceinline__ float fold_round(float f, float invp, float pf)
+{
+    const float q = __fsub_rn(__fmaf_rn(f, invp, kRoundBias), kRoundBias);
+    return __fmaf_rn(-q, pf, f);
+}
+
 __device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
 {
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const float f = __uint_as_float(v[e]);
-        const float q = rintf(f * invp);
-        v[e] = __float_as_uint(fmaf(-q, pf, f));
-    }
+    for (int e = 0; e < 32; ++e) v[e] = __float_as_uint(fold_round(__uint_as_float(v[e]), invp, pf));
 }
 
 __device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
-                                         uint32_t mu32, uint32_t offp)
+                                         uint32_t mu32, float invp, float pf)
 {
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-        const int32_t d = __float2int_rn(__uint_as_float(v[e]));
-        const uint32_t xm = barrett32((uint32_t)d + offp, p, mu32);
-        const uint32_t y = barrett32(mul * xm, p, mu32);  // p < 2^16
-        v[e] = to_float ? __float_as_uint((float)y) : y;
+        const float r = fold_round(__uint_as_float(v[e]), invp, pf);
+        int32_t x = (int32_t)(__float_as_uint(__fadd_rn(r, kRoundBias)) - kRoundBiasBits);
+        x += x < 0 ? (int32_t)p : 0;
+        x -= x >= (int32_t)p ? (int32_t)p : 0;
+        const uint32_t y = barrett32(mul * (uint32_t)x, p, mu32);  // mul, x < p < 2^16
+        // y < 2^16: its float is 2^23 + y with the low mantissa bits = y, minus 2^23
+        v[e] = to_float ? __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | y), 8388608.0f))
+                        : y;
     }
 }
 
-// C(gi, j0 .. j0+31) <- C op sres (mod p), in the Morton-hybrid layout. Loads
+// C(gi, j0 .. j0+W-1) <- C op sres (mod p), in the Morton-hybrid layout. Loads
 // are issued before stores; a run inside one tile row moves as 16-byte vectors.
+template <int W>
 __device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi, int64_t j0,
-                                            uint64_t cmask, const uint32_t (&sres)[32])
+                                            uint64_t cmask, const uint32_t (&sres)[W])
 {
     const uint32_t p = args.p;
     const uint64_t ci = (uint64_t)(args.c_row0 + gi);
     const uint64_t cj0 = (uint64_t)(args.c_col0 + j0);
     const uint64_t base = fm_encode(ci, cj0, args.c_lt);
-    const bool run = j0 + 32 <= args.N && (cj0 & cmask) + 32 <= cmask + 1 && (base & 3) == 0;
+    const bool run = j0 + W <= args.N && (cj0 & cmask) + W <= cmask + 1 && (base & 3) == 0;
     if (run) {
         uint4* dst = reinterpret_cast<uint4*>(args.C + base);
-        uint4 old[8];
+        uint4 old[W / 4];
         if (args.op != FM_OP_SET) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) old[q] = dst[q];
+            for (int q = 0; q < W / 4; ++q) old[q] = dst[q];
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < W / 4; ++q) {
             uint4 o = args.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
             o.x = op_combine(o.x, sres[4 * q + 0], p, args.op);
             o.y = op_combine(o.y, sres[4 * q + 1], p, args.op);
@@ -135,21 +151,21 @@ __device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi
         }
         return;
     }
-    // ragged edge or a tile boundary inside the run: all loads, then all stores
-    uint32_t old[32];
-    uint64_t a = base;
+    // ragged edge or a tile boundary inside the run: groups of 8, loads then
+    // stores (a group's stores keep the next group's loads from being hoisted,
+    // which bounds the live registers)
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const uint64_t cj = cj0 + e;
-        if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
-        old[e] = (args.op != FM_OP_SET && j0 + e < args.N) ? args.C[a] : 0u;
-    }
-    a = base;
+    for (int g = 0; g < W; g += 8) {
+        uint32_t old[8];
+        uint64_t a[8];
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const uint64_t cj = cj0 + e;
-        if (e > 0) a = ((cj & cmask) == 0) ? fm_encode(ci, cj, args.c_lt) : a + 1;
-        if (j0 + e < args.N) args.C[a] = op_combine(old[e], sres[e], p, args.op);
+        for (int e = 0; e < 8; ++e) {
+            a[e] = fm_encode(ci, cj0 + g + e, args.c_lt);
+            old[e] = (args.op != FM_OP_SET && j0 + g + e < args.N) ? args.C[a[e]] : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (j0 + g + e < args.N) args.C[a[e]] = op_combine(old[e], sres[g + e], p, args.op);
     }
 }
 
@@ -356,8 +372,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                             fold_fp(v0, args.invp, args.pf);
                             fold_fp(v1, args.invp, args.pf);
                         } else {
-                            fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.offp);
-                            fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.offp);
+                            fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
+                            fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
                         }
                         fm_tmem_st32(dbase + g * 64, v0);
                         fm_tmem_st32(dbase + g * 64 + 32, v1);
@@ -448,7 +464,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < args.M) write_c_run(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                if (gi < args.M) write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
             }
             if (FOLD) {
                 fm_tc_fence_before();
@@ -468,6 +484,291 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
     if (warp == 1) {
         fm_tc_fence_after();
         fm_tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-pair form (fold form only): a cluster of two CTAs computes a 256 x 256
+// output tile with tcgen05.mma.cta_group::2. CTA r of the pair stages A rows
+// [128 r, 128 r + 128) and B rows (n) [128 r, 128 r + 128) of the tile -- 32 KB
+// per 64-wide K stage instead of 48 KB -- and holds D rows [128 r, 128 r + 128)
+// in its tensor memory. The even CTA issues the MMAs; its commits are multicast
+// to both CTAs. Each CTA's bulk copies complete on its own full barrier; a
+// forwarder thread of the odd CTA then arrives on the even CTA's full barrier,
+// and the odd CTA's epilogue warps arrive on the even CTA's accumulator-empty
+// barriers.
+constexpr int kPairStages = 6;
+constexpr uint32_t kPairStageBytes = 2 * kATileBytes;  // A half + B half, 16 KB each
+constexpr size_t kPairSmem = (size_t)kPairStages * kPairStageBytes + 1024;
+
+__global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const LimbGemmArgs args)
+{
+    constexpr int BN = 256;
+    constexpr int S = kPairStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    __shared__ __align__(8) uint64_t full_bar[S];
+    __shared__ __align__(8) uint64_t empty_bar[S];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    __shared__ uint32_t s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = fm_cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const int MB2 = args.MB >> 1;  // A planes are padded to an even number of row blocks
+    const int n_tiles = MB2 * args.NB;
+    const int njobs = args.first[args.n_products];
+
+    auto coords = [&](int tile, int& mb2, int& nb) {
+        const int GROUP = 4;
+        const int per_group = GROUP * args.NB;
+        const int first = (tile / per_group) * GROUP;
+        const int gsz = min(MB2 - first, GROUP);
+        const int inner = tile % per_group;
+        mb2 = first + inner % gsz;
+        nb = inner / gsz;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            fm_mbar_init(&full_bar[s], leader ? 2 : 1);
+            fm_mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            fm_mbar_init(&accf_bar[b], 1);
+            fm_mbar_init(&acce_bar[b], 2 * kEpiWarps);
+        }
+        fm_mbar_init(&done_bar, 1);
+        fm_fence_mbar_init();
+        s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    if (warp == 1) {
+        fm_tmem_alloc_pair(&tmem_slot, 512);
+        fm_tmem_relinquish_pair();
+    }
+    fm_tc_fence_before();
+    __syncthreads();
+    fm_cluster_sync();  // both CTAs' barriers exist before any cross-CTA arrive
+    fm_tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer (both CTAs): this CTA's A half and B half per stage ----
+            uint32_t g = 0;
+            bool ok = true;
+            for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
+                int mb2, nb;
+                coords(tile, mb2, nb);
+                int idx = 0;
+                for (int t = 0; t < njobs && ok; ++t) {
+                    while (t >= args.first[idx + 1]) ++idx;
+                    const int c = t - args.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
+                                           ((size_t)(2 * mb2 + rank) * args.KB) * kATileBytes;
+                    const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
+                                           ((size_t)nb * args.KB) * (2 * kATileBytes) +
+                                           (size_t)rank * kATileBytes;
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int s = g % S;
+                        const uint32_t ph = (g / S) & 1;
+                        if (!fm_mbar_wait(&empty_bar[s], ph ^ 1, args.status, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* sa = smem + (size_t)s * kPairStageBytes;
+                        fm_mbar_arrive_expect_tx(&full_bar[s], kPairStageBytes);
+                        fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
+                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * (2 * kATileBytes), kATileBytes,
+                                    &full_bar[s]);
+                    }
+                }
+            }
+            s_issued = g;
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---- MMA issuer (even CTA) ----
+            const uint32_t idesc = fm_idesc_f16_f32(2 * kBM, BN);
+            uint32_t g = 0, T = 0;
+            bool ok = true;
+            for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
+                int idx = 0;
+                for (int t = 0; t < njobs && ok; ++t, ++T) {
+                    const int b = T & 1;
+                    while (t >= args.first[idx + 1]) ++idx;
+                    const int c = t - args.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    if (T >= 2 &&
+                        !fm_mbar_wait(&acce_bar[b], ((T >> 1) - 1) & 1, args.status, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fm_tc_fence_after();
+                    const uint32_t d_tmem = tmem + (uint32_t)(b * BN);
+                    bool first = true;
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int s = g % S;
+                        const uint32_t ph = (g / S) & 1;
+                        if (!fm_mbar_wait_cluster(&full_bar[s], ph, args.status, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        fm_tc_fence_after();
+                        const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * kPairStageBytes);
+                        const uint32_t b_addr = a_addr + kATileBytes;
+#pragma unroll
+                        for (int k = 0; k < kBK / 16; ++k) {
+                            const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
+                            const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
+                            const uint32_t acc = (t >= 2 || !first || k > 0) ? 1u : 0u;
+                            fm_mma_f16_pair(d_tmem, ad, bd, idesc, acc);
+                        }
+                        fm_mma_commit_pair(&empty_bar[s], 0x3);  // stage free in both CTAs
+                        first = false;
+                    }
+                    if (!ok) break;
+                    fm_mma_commit_pair(&accf_bar[b], 0x3);  // accumulator b complete in both CTAs
+                }
+            }
+            s_consumed = g;
+            fm_mma_commit_pair(&done_bar, 0x1);
+            fm_mbar_wait(&done_bar, 0, args.status, nullptr);
+        } else if (lane == 0) {
+            // ---- forwarder (odd CTA): this CTA's stage landed -> even CTA's full barrier ----
+            const uint32_t leader_full = fm_mapa(fm_smem_u32(&full_bar[0]), 0);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
+                int idx = 0;
+                for (int t = 0; t < njobs && ok; ++t) {
+                    while (t >= args.first[idx + 1]) ++idx;
+                    const int c = t - args.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int s = g % S;
+                        if (!fm_mbar_wait(&full_bar[s], (g / S) & 1, args.status, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        fm_mbar_arrive_cluster(leader_full + (uint32_t)(s * sizeof(uint64_t)));
+                    }
+                }
+            }
+            s_consumed = g;
+        }
+    } else {
+        // ---- epilogue (both CTAs): as in the single-CTA kernel, for this CTA's 128 rows ----
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int half = ew >> 2;
+        constexpr int kCols = BN / 2;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const uint32_t col0 = (uint32_t)(half * kCols);
+        const uint32_t p = args.p;
+        const uint64_t cmask = (1ull << args.c_lt) - 1;
+        const uint32_t acce_leader = fm_mapa(fm_smem_u32(&acce_bar[0]), 0);
+        uint32_t T = 0;
+        bool ok = true;
+        for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
+            int mb2, nb;
+            coords(tile, mb2, nb);
+            int idx = 0;
+            for (int t = 0; t < njobs; ++t, ++T) {
+                const int b = T & 1;
+                if (!fm_mbar_wait(&accf_bar[b], (T >> 1) & 1, args.status, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                fm_tc_fence_after();
+                while (t >= args.first[idx + 1]) ++idx;
+                const bool last_on_buffer = (t + 2 >= njobs);
+                int idx2 = idx;
+                if (!last_on_buffer)
+                    while (t + 2 >= args.first[idx2 + 1]) ++idx2;
+                const bool same_next = !last_on_buffer && idx2 == idx;
+                const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
+                const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
+#pragma unroll 1
+                for (int g = 0; g < kCols / 64; ++g) {
+                    uint32_t v0[32], v1[32];
+                    fm_tmem_ld32(dbase + g * 64, v0);
+                    fm_tmem_ld32(dbase + g * 64 + 32, v1);
+                    fm_tmem_wait_ld();
+                    if (same_next) {
+                        fold_fp(v0, args.invp, args.pf);
+                        fold_fp(v1, args.invp, args.pf);
+                    } else {
+                        fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
+                        fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
+                    }
+                    fm_tmem_st32(dbase + g * 64, v0);
+                    fm_tmem_st32(dbase + g * 64 + 32, v1);
+                }
+                fm_tmem_wait_st();
+                fm_tc_fence_before();
+                __syncwarp();
+                if (!last_on_buffer && lane == 0)
+                    fm_mbar_arrive_remote(acce_leader + (uint32_t)(b * sizeof(uint64_t)));
+            }
+            if (!ok) break;
+            // tile end: merge the two final residues, release, write C
+            const int64_t gi = (int64_t)(2 * mb2 + rank) * kBM + quarter * 32 + lane;
+            const int by = (T - 1) & 1, bx = by ^ 1;
+            if (njobs >= 2) {
+                const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
+                const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
+#pragma unroll 1
+                for (int cc = 0; cc < kCols / 32; ++cc) {
+                    uint32_t xv[32], yv[32];
+                    fm_tmem_ld32(xb + cc * 32, xv);
+                    fm_tmem_ld32(yb + cc * 32, yv);
+                    fm_tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const uint32_t x = xv[e] + yv[e];
+                        yv[e] = x >= p ? x - p : x;
+                    }
+                    fm_tmem_st32(yb + cc * 32, yv);
+                }
+                fm_tmem_wait_st();
+                fm_tc_fence_before();
+                __syncwarp();
+                if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(bx * sizeof(uint64_t)));
+            }
+#pragma unroll 1
+            for (int cc = 0; cc < kCols / 32; ++cc) {
+                uint32_t sres[32];
+                const uint32_t col = col0 + cc * 32;
+                fm_tmem_ld32(tmem + lane_base + (uint32_t)(by * BN) + col, sres);
+                fm_tmem_wait_ld();
+                if (gi < args.M) write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+            }
+            fm_tc_fence_before();
+            __syncwarp();
+            if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(by * sizeof(uint64_t)));
+        }
+    }
+
+    fm_tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        for (uint32_t g = s_consumed; g < s_issued; ++g)
+            fm_mbar_wait(&full_bar[g % S], (g / S) & 1, args.status, nullptr);
+    }
+    fm_cluster_sync();  // the even CTA's MMAs are complete before either CTA frees TMEM
+    if (warp == 1) {
+        fm_tc_fence_after();
+        fm_tmem_dealloc_pair(tmem, 512);
     }
 }
 
@@ -508,6 +809,38 @@ int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, kGemmThreads, smem, s>>>(a);
     FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+// Clusters of two CTAs, one per pair tile up to the number of pairs that fit
+// on the device at once (the kernel walks further tiles itself).
+int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
+{
+    static int max_pairs[64] = {0};
+    int dev = 0;
+    FM_CUDA_TRY(cudaGetDevice(&dev));
+    auto k = limb_gemm_pair_kernel;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = kPairSmem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (dev < 64 && max_pairs[dev] == 0) {
+        cfg.gridDim = dim3(2 * pair_tiles);
+        int n = 0;
+        FM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, k, &cfg));
+        max_pairs[dev] = n > 0 ? n : fm_sm_count() / 2;
+    }
+    const int pairs = std::max(1, std::min(pair_tiles, dev < 64 ? max_pairs[dev] : fm_sm_count() / 2));
+    cfg.gridDim = dim3(2 * pairs);
+    FM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a));
     return FM_OK;
 }
 
@@ -562,7 +895,12 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     bool kara = w == 2 && q.fold && !(opts && opts->no_karatsuba == 1);
     for (int k = 0; kara && k < 3; ++k) kara = wk[k] != 0 && gcd_u64(wk[k], p) == 1;
     if (kara) {
-        const int cs_m = std::max(1, std::min(cs, (int)(room / (1 << 16) / kBK)));
+        // middle product: for p < 2^16 the representative is >= 32640 - p > -32896,
+        // so d0 = d1 = -128 never occurs and |d0 + d1| <= 255; a term is at most
+        // 255^2, and the value carried into a chunk is below p in magnitude (a
+        // residue from a product change, or v - round(v/p) p within a product)
+        const int64_t room_m = ((int64_t)1 << 24) - (int64_t)p;
+        const int cs_m = std::max(1, std::min(cs, (int)(room_m / (255 * 255) / kBK)));
         q.n_planes = 3;
         q.n_products = 3;
         const int pa[3] = {0, 2, 1}, cks[3] = {cs, cs_m, cs};
@@ -586,7 +924,10 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
             for (int k = 0; k < w * w; ++k)
                 if (gcd_u64(q.prod_w[k], p) != 1) return FM_EUNSUPPORTED;
     }
+    if (opts && opts->cta_pair && (!q.fold || bn != 256)) return FM_EINVAL;
+    q.pair = (opts && opts->cta_pair == 1) ? 1 : 0;
     q.MB = (int)((M + kBM - 1) / kBM);
+    if (bn == 256) q.MB += q.MB & 1;  // the A plane layout depends on BN only
     q.NB = (int)((N + bn - 1) / bn);
     q.KB = (int)((K + kBK - 1) / kBK);
     q.a_plane_bytes = (size_t)q.MB * q.KB * kATileBytes;
@@ -616,7 +957,6 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.p = p;
     a.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
     a.mu64 = ~0ull / p;
-    a.offp = (uint32_t)((((uint64_t)1 << 24) + p - 1) / p * p);
     for (int k = 0; k < 16; ++k) {
         a.pa[k] = a.pb[k] = a.cs[k] = 0;
         a.wt[k] = a.cn[k] = 0;
@@ -648,6 +988,7 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.M = q.M;
     a.N = q.N;
     a.status = status;
+    if (q.pair) return launch_gemm_pair(a, q.MB / 2 * q.NB, s);
     const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);

@@ -118,7 +118,6 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
 {
     __shared__ uint32_t prow[kNb];
     __shared__ int s_abort;
-    __shared__ int s_piv;
     if (threadIdx.x == 0) s_abort = 0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -52,7 +52,8 @@ class fm_sub(ctypes.Structure):
 
 class fm_opts(ctypes.Structure):
     _fields_ = [("k_chunk", ctypes.c_int32), ("block_n", ctypes.c_int32),
-                ("no_karatsuba", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("no_karatsuba", ctypes.c_int32), ("cta_pair", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class fm_tune_result(ctypes.Structure):
@@ -163,11 +164,12 @@ def sub(m: fm_matrix, row0: int, col0: int, rows: int, cols: int) -> fm_sub:
     return fm_sub(m, int(row0), int(col0), int(rows), int(cols))
 
 
-def opts(k_chunk: int = 0, block_n: int = 0, no_karatsuba: int = 0) -> fm_opts:
+def opts(k_chunk: int = 0, block_n: int = 0, no_karatsuba: int = 0, cta_pair: int = 0) -> fm_opts:
     o = fm_opts()
     o.k_chunk = int(k_chunk)
     o.block_n = int(block_n)
     o.no_karatsuba = int(no_karatsuba)
+    o.cta_pair = int(cta_pair)
     return o
 
 

@@ -81,15 +81,29 @@ def test_limb_parity(env, orc, case, p):
         assert np.array_equal(got, want), (p, op, lts)
 
 
-@pytest.mark.parametrize("k_chunk,block_n,no_kara", [(64, 0, 0), (512, 0, 0), (960, 0, 0),
-                                                     (0, 128, 0), (320, 128, 0), (0, 0, 1),
-                                                     (192, 128, 1)])
-def test_limb_chunk_and_tile_options(env, orc, k_chunk, block_n, no_kara):
+@pytest.mark.parametrize("k_chunk,block_n,no_kara,pair", [
+    (64, 0, 0, 0), (512, 0, 0, 0), (960, 0, 0, 0), (0, 128, 0, 0), (320, 128, 0, 0),
+    (0, 0, 1, 0), (192, 128, 1, 0), (0, 256, 0, 1), (960, 256, 1, 1), (64, 256, 0, 1)])
+def test_limb_chunk_and_tile_options(env, orc, k_chunk, block_n, no_kara, pair):
     fm = env[0]
     for p in (P16, 257):
         got, want = run_case(env, orc, p, 2, fm.FM_ALGO_LIMB_TC, 300, 520, 3000, (0, 5, 3, 0, 0, 9),
-                             (6, 6, 6), seed=4, options=fm.opts(k_chunk, block_n, no_kara))
+                             (6, 6, 6), seed=4, options=fm.opts(k_chunk, block_n, no_kara, pair))
         assert np.array_equal(got, want), p
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (129, 256, 960), (300, 520, 1000),
+                                   (2560, 2048, 128), (1000, 3000, 200)])
+def test_limb_cta_pair_and_single_cta(env, orc, M, N, K):
+    # 256 x 256 tiles on CTA pairs against 128 x 256 tiles on single CTAs: an
+    # odd number of 128-row blocks (the pair's second half past M), one tile,
+    # and more pair tiles than pairs resident on the device (the persistent walk)
+    fm = env[0]
+    for p in (P16, 251, 2):
+        for pair in (0, 1):
+            got, want = run_case(env, orc, p, 2, fm.FM_ALGO_LIMB_TC, M, N, K, (0, 3, 5, 0, 0, 7),
+                                 (7, 7, 7), seed=M + N + p, options=fm.opts(0, 256, 0, pair))
+            assert np.array_equal(got, want), (p, pair)
 
 
 def test_limb_rejects_unsafe_chunk(env):
@@ -99,6 +113,9 @@ def test_limb_rejects_unsafe_chunk(env):
     with pytest.raises(fm.FmError):   # 1024 > the exact bound 960 when folding p = 65521
         fm.fm_gemm_modp(M.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), P16, 0,
                         fm.FM_ALGO_LIMB_TC, fm.opts(1024, 0))
+    with pytest.raises(fm.FmError):   # CTA pairs need the fold form on 256-wide tiles
+        fm.fm_gemm_modp(M.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), P16, 0,
+                        fm.FM_ALGO_LIMB_TC, fm.opts(0, 128, 0, 1))
 
 
 def _constant_case(env, orc, p, a, b, K, algo, options=None):
@@ -121,9 +138,12 @@ def test_limb_accumulator_extremes_p16(env, orc, K):
     # Inputs whose limbs are all -128 make every limb product +2^14, the largest
     # magnitude; a chunk of 960 with a folded residue reaches 960*2^14 + p - 1,
     # just under 2^24. 65393 = p - 128 has limbs (-128, 0); 32753 = p - 32768
-    # has limbs (0, -128); 127 has limbs (127, 0).
+    # has limbs (0, -128); 127 has limbs (127, 0). 32881 = p - 32640 has limbs
+    # (-128, -127): its Karatsuba middle term is (-255)^2 = 65025, and a 256-term
+    # middle chunk with its carried value reaches 16,646,400 + |carry| < 2^24.
     fm = env[0]
-    for a, b in ((65393, 65393), (32753, 32753), (65393, 32753), (127, 65393), (32639, 32753)):
+    for a, b in ((65393, 65393), (32753, 32753), (65393, 32753), (127, 65393), (32639, 32753),
+                 (32881, 32881), (32881, 32639), (32639, 32639)):
         _constant_case(env, orc, P16, a, b, K, fm.FM_ALGO_LIMB_TC)
 
 

@@ -27,6 +27,20 @@ def test_split_exhaustive_65521():
     assert np.array_equal(r[hi + 1:], x[hi + 1:] - p)
 
 
+@pytest.mark.parametrize("p", [257, 4099, 32771, 65521, 65533, 65535])
+def test_two_limb_digit_sum_bound(p):
+    # every two-limb modulus p < 2^16 keeps d0 + d1 in [-255, 254] (d0 = d1 = -128
+    # would need the representative -32896 < 32640 - p), so a Karatsuba middle
+    # term (d0 + d1)(e0 + e1) is at most 255^2 = 65025 in magnitude
+    from oracle import limbs
+    d = limbs.split(np.arange(p, dtype=np.int64), p).astype(np.int64)
+    s = d[0] + d[1]
+    assert s.min() >= -255 and s.max() <= 254
+    if p >= 65280:  # representative -32640 (d0 = -128, d1 = -127) is x = p - 32640
+        assert s[p - 32640] == -255
+    assert 256 * 255 * 255 + p <= 1 << 24  # a 256-term middle chunk plus the carry is exact
+
+
 def test_split_31bit_random_and_extremes():
     from oracle import limbs
     p = 2147483647
