@@ -303,6 +303,48 @@ int fm_autotune_clear(void);
  * negative fm_status. Needs no GPU. */
 int64_t fm_decompose(fm_sub C, fm_sub A, fm_sub B, int64_t* out, int64_t cap);
 
+/* ---- GF(2) on bit-packed matrices ---------------------------------------
+ * The field of the paper's experiments (Sec. 2.2, "Performance Analysis":
+ * random sub-matrix products in Morton-hybrid matrices with T' = 32 over the
+ * binary field). A bit-packed Morton-hybrid matrix has T' = 32 fixed, so a
+ * tile row is one 32-bit word: n x n entries, n = 32 * 2^log2_grid, stored as
+ * 4^log2_grid tiles of 32 words (128 bytes); tile (I, J) starts at word
+ * Z(I, J) * 32 (Z as for fm_matrix), word u of a tile is tile row u and its
+ * bit v is entry (32 I + u, 32 J + v). The matrix takes n * n / 8 bytes; base
+ * must be 16-byte aligned. Sub-matrices use any row, column, size. */
+typedef struct fm_gf2_matrix {
+    uint32_t* base;     /* device pointer, 16-byte aligned                     */
+    int32_t log2_grid;  /* 2^log2_grid tiles per side, 0..15                   */
+    int32_t reserved;
+} fm_gf2_matrix;
+
+typedef struct fm_gf2_sub {
+    fm_gf2_matrix m;
+    int64_t row0, col0, rows, cols;
+} fm_gf2_sub;
+
+/* Row-major entries (device, leading dimension ld >= cols; bit 0 of each entry
+ * is taken) -> the bit-packed matrix dst; entries outside rows x cols become 0. */
+int fm_gf2_pack(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld, fm_gf2_matrix dst,
+                fm_stream stream);
+
+/* The leading rows x cols entries of src -> row-major 0 / 1 words at dst. */
+int fm_gf2_unpack(fm_gf2_matrix src, int64_t rows, int64_t cols, uint32_t* dst, int64_t ld,
+                  fm_stream stream);
+
+/* C <- A*B (FM_OP_SET) or C <- C + A*B (FM_OP_ADD; FM_OP_SUB is the same in
+ * GF(2)) on bit-packed sub-matrices: C is rows x cols, A is C.rows x K, B is
+ * K x C.cols. A and B may share a matrix; C must not overlap A or B
+ * (FM_EINVAL). Bits of C outside the sub-matrix are unchanged, also where they
+ * share a word with it. Runs on the tensor cores with E4M3 0 / 1 operands and
+ * FP32 accumulation (exact: at most 2^24 - 2 terms per accumulation, folded
+ * to parity between chunks). Workspace: fm_gf2_workspace_size bytes, cached
+ * per device as for fm_gemm_modp. */
+int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, fm_stream stream);
+
+/* Device workspace bytes of fm_gf2_gemm for an M x N x K product. */
+int64_t fm_gf2_workspace_size(int64_t M, int64_t N, int64_t K);
+
 /* ---- status ------------------------------------------------------------- */
 
 /* Synchronises stream, returns and clears the device status word that

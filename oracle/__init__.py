@@ -26,6 +26,11 @@ What the oracle computes, each part citing the passage it follows:
   and rank; the paper defers TURBO's details to its reference, so the textbook
   elimination stands in).
 * ``freivalds``: probabilistic check of a product through ``matvec_modp``.
+* ``gf2_pack`` / ``gf2_unpack``: the bit-packed Morton-hybrid matrix over GF(2)
+  (the field of the experiments, Sec. 2.2 "Performance Analysis", T' = 32): the
+  Morton-hybrid element order with 32 consecutive entries per word, entry e of
+  the order at bit e % 32 of word e // 32. The product over GF(2) is
+  ``gemm_modp`` with p = 2.
 """
 
 from __future__ import annotations
@@ -168,6 +173,21 @@ def from_morton(src: np.ndarray, m: int, T: int, rows: int, cols: int) -> np.nda
     dst = np.empty((rows, cols), dtype=np.uint32)
     _load().or_from_morton(_ptr(src), int(m), int(T), rows, cols, _ptr(dst), cols)
     return dst
+
+
+def gf2_pack(src: np.ndarray, m: int) -> np.ndarray:
+    """Row-major 0/1 array (bit 0 of each entry) -> words of the bit-packed
+    Morton-hybrid matrix of side 2^m * 32: element e of the Morton-hybrid order
+    with T' = 32 is bit e % 32 of word e // 32."""
+    flat = to_morton(_u32(src) & 1, m, 32).reshape(-1, 32).astype(np.uint64)
+    return (flat << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
+
+
+def gf2_unpack(words: np.ndarray, m: int, rows: int, cols: int) -> np.ndarray:
+    """Inverse of gf2_pack for the leading rows x cols corner."""
+    w = _u32(words).astype(np.uint64).reshape(-1, 1)
+    flat = ((w >> np.arange(32, dtype=np.uint64)) & 1).astype(np.uint32).reshape(-1)
+    return from_morton(flat, m, 32, rows, cols)
 
 
 def permute(src: np.ndarray, rp=None, cp=None) -> np.ndarray:

@@ -6,6 +6,6 @@ used by callers for device memory and streams.
 """
 
 from .native import *  # noqa: F401,F403
-from .native import EXPORTS, FmError, lib, matrix, opts, sub  # noqa: F401
+from .native import EXPORTS, FmError, gf2_matrix, gf2_sub, lib, matrix, opts, sub  # noqa: F401
 
 __version__ = "0.1.0"

@@ -234,6 +234,21 @@ __device__ __forceinline__ void fm_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
         : "memory");
 }
 
+// D (+)= A * B with 8-bit E4M3 operands (kind::f8f6f4, FP32 accumulation). In
+// the 128-byte swizzled K-major layout a row holds 128 elements; one MMA takes
+// K = 32 of them (32 bytes), so descriptors advance as for the f16 kind. The
+// instruction descriptor is the f16 one: format code 0 is E4M3 for this kind.
+__device__ __forceinline__ void fm_mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on an mbarrier once all previously issued tcgen05 ops of this thread
 // have completed.
 __device__ __forceinline__ void fm_mma_commit(uint64_t* bar)

@@ -30,12 +30,17 @@ struct FmLimbPlan {
     uint32_t prod_w[16];         // weight of product k, mod p
     int block_n;      // 128 or 256
     int fold;         // 1: residue folded into the fp32 accumulator (p < 2^16)
-    int pair;         // 1: CTA pairs (cta_group::2) on 256 x 256 tiles (fold form, BN 256)
+    int pair = 0;     // 1: CTA pairs (cta_group::2) on 256 x 256 tiles (fold form, BN 256)
+    int gf2 = 0;      // 1: GF(2), one E4M3 plane per operand, 128 elements per K stage
     int MB, NB, KB;
     size_t a_plane_bytes, b_plane_bytes;  // bytes of ONE plane
 };
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan);
+// GF(2) product on bit-packed operands: one E4M3 0/1 plane per operand (tiles of
+// 128 rows x 128 k bytes), one product, parity folded over p = 2 (gf2.cu splits,
+// limb_gemm.cu multiplies).
+int fm_gf2_plan(int64_t M, int64_t N, int64_t K, FmLimbPlan* plan);
 size_t fm_limb_workspace_bytes(const FmLimbPlan& plan);
 int fm_limb_run(const FmLimbPlan& plan, fm_sub C, fm_sub A, fm_sub B, uint32_t p, int op,
                 void* workspace, int* status, cudaStream_t s);

@@ -169,6 +169,50 @@ __device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi
     }
 }
 
+// GF(2) output: the residues (0 or 1) of columns j0 .. j0+31 of row gi become
+// one word of bits, combined into the bit-packed Morton-hybrid C (T' = 32: word
+// Z(I, J) * 32 + u holds tile row u). SET replaces the bits, ADD and SUB flip
+// them (+1 = -1 in GF(2)). A run not starting on a word boundary spans two
+// words shared with the neighbouring runs, updated with atomics; a whole word
+// belongs to this thread alone.
+__device__ __forceinline__ void gf2_apply(uint32_t* w, uint32_t m, uint32_t x, int op)
+{
+    if (m == 0u) return;
+    if (m == ~0u) {
+        if (op == FM_OP_SET)
+            *w = x;
+        else
+            *w ^= x;
+        return;
+    }
+    if (op == FM_OP_SET) {
+        atomicAnd(w, ~m);
+        atomicOr(w, x & m);
+    } else {
+        atomicXor(w, x & m);
+    }
+}
+
+__device__ __forceinline__ void write_gf2_run(const LimbGemmArgs& args, int64_t gi, int64_t j0,
+                                              const uint32_t (&r)[32])
+{
+    const int64_t nvalid = args.N - j0;
+    if (nvalid <= 0) return;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) bits |= (r[e] & 1u) << e;
+    const uint32_t vmask = nvalid >= 32 ? ~0u : ((1u << nvalid) - 1u);
+    bits &= vmask;
+    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
+    const uint64_t cj = (uint64_t)(args.c_col0 + j0);
+    const uint32_t b = (uint32_t)(cj & 31);
+    gf2_apply(args.C + (fm_encode(ci, cj, 5) >> 5), vmask << b, bits << b, args.op);
+    if (b != 0) {
+        const uint32_t m1 = vmask >> (32 - b);
+        if (m1) gf2_apply(args.C + (fm_encode(ci, cj + (32 - b), 5) >> 5), m1, bits >> (32 - b), args.op);
+    }
+}
+
 template <int BN>
 struct GemmCfg {
     static constexpr int kStages = BN == 256 ? 4 : 6;
@@ -181,7 +225,11 @@ struct GemmCfg {
 // The producer and MMA warps run ahead into the next tile while the epilogue
 // finishes the previous one; barrier phases and the two TMEM accumulators carry
 // on across tiles (job counter T).
-template <int BN, bool FOLD>
+// KIND: kF16Res = f16 limb planes, residues written to a uint32 Morton-hybrid C;
+// kE4M3Gf2 = E4M3 0/1 planes (GF(2)), parity bits written to a bit-packed C.
+enum { kF16Res = 0, kE4M3Gf2 = 1 };
+
+template <int BN, bool FOLD, int KIND>
 __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGemmArgs args)
 {
     using Cfg = GemmCfg<BN>;
@@ -309,7 +357,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                             // fold form: from the third job of a tile on, each job
                             // accumulates onto the residue folded back by the epilogue
                             const uint32_t acc = ((FOLD && t >= 2) || !first || k > 0) ? 1u : 0u;
-                            fm_mma_f16(d_tmem, ad, bd, idesc, acc);
+                            if (KIND == kE4M3Gf2)
+                                fm_mma_e4m3(d_tmem, ad, bd, idesc, acc);
+                            else
+                                fm_mma_f16(d_tmem, ad, bd, idesc, acc);
                         }
                         fm_mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
                         first = false;
@@ -464,7 +515,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < args.M) write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                if (gi < args.M) {
+                    if (KIND == kE4M3Gf2)
+                        write_gf2_run(args, gi, (int64_t)nb * BN + col, sres);
+                    else
+                        write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                }
             }
             if (FOLD) {
                 fm_tc_fence_before();
@@ -801,10 +857,10 @@ uint32_t invmod(uint32_t a, uint32_t m)
     return (uint32_t)(t % m);
 }
 
-template <int BN, bool FOLD>
+template <int BN, bool FOLD, int KIND = kF16Res>
 int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
 {
-    auto k = limb_gemm_kernel<BN, FOLD>;
+    auto k = limb_gemm_kernel<BN, FOLD, KIND>;
     const size_t smem = GemmCfg<BN>::kSmem;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, kGemmThreads, smem, s>>>(a);
@@ -936,6 +992,33 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     return FM_OK;
 }
 
+int fm_gf2_plan(int64_t M, int64_t N, int64_t K, FmLimbPlan* plan)
+{
+    FmLimbPlan q;
+    q.M = M;
+    q.N = N;
+    q.K = K;
+    q.w = 1;
+    q.n_planes = 1;
+    q.n_products = 1;
+    q.prod_a[0] = q.prod_b[0] = 0;
+    q.prod_w[0] = 1;
+    q.block_n = 256;
+    q.fold = 1;
+    q.gf2 = 1;
+    q.MB = (int)((M + kBM - 1) / kBM);
+    q.MB += q.MB & 1;
+    q.NB = (int)((N + 255) / 256);
+    q.KB = (int)((K + 127) / 128);  // 128 E4M3 elements per 128-byte stage row
+    // 0/1 products: a chunk of c stages adds at most 128 c; with the carried
+    // parity (|v| <= 1) every partial sum stays below 2^24
+    q.prod_cs[0] = std::max(1, std::min(q.KB, (int)((((int64_t)1 << 24) - 2) / 128)));
+    q.a_plane_bytes = (size_t)q.MB * q.KB * kATileBytes;
+    q.b_plane_bytes = (size_t)q.NB * q.KB * 256 * 128;
+    *plan = q;
+    return FM_OK;
+}
+
 size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
 {
     return (size_t)q.n_planes * (q.a_plane_bytes + q.b_plane_bytes);
@@ -988,6 +1071,7 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.M = q.M;
     a.N = q.N;
     a.status = status;
+    if (q.gf2) return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
     if (q.pair) return launch_gemm_pair(a, q.MB / 2 * q.NB, s);
     const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {

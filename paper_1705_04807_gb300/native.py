@@ -30,7 +30,7 @@ EXPORTS = (
     "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
     "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
-    "fm_pluq",
+    "fm_pluq", "fm_gf2_pack", "fm_gf2_unpack", "fm_gf2_gemm", "fm_gf2_workspace_size",
 )
 
 
@@ -47,6 +47,16 @@ class fm_matrix(ctypes.Structure):
 
 class fm_sub(ctypes.Structure):
     _fields_ = [("m", fm_matrix), ("row0", ctypes.c_int64), ("col0", ctypes.c_int64),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64)]
+
+
+class fm_gf2_matrix(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_void_p), ("log2_grid", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class fm_gf2_sub(ctypes.Structure):
+    _fields_ = [("m", fm_gf2_matrix), ("row0", ctypes.c_int64), ("col0", ctypes.c_int64),
                 ("rows", ctypes.c_int64), ("cols", ctypes.c_int64)]
 
 
@@ -112,6 +122,10 @@ def lib():
         "fm_autotune_load": ([ctypes.c_char_p], ctypes.c_int),
         "fm_autotune_clear": ([], ctypes.c_int),
         "fm_pluq": ([fm_matrix, I64, I64, U32, P, P, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
+        "fm_gf2_pack": ([P, I64, I64, I64, fm_gf2_matrix, P], ctypes.c_int),
+        "fm_gf2_unpack": ([fm_gf2_matrix, I64, I64, P, I64, P], ctypes.c_int),
+        "fm_gf2_gemm": ([fm_gf2_sub, fm_gf2_sub, fm_gf2_sub, I32, P], ctypes.c_int),
+        "fm_gf2_workspace_size": ([I64, I64, I64], I64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -162,6 +176,14 @@ def matrix(base, log2_grid: int, log2_T: int) -> fm_matrix:
 
 def sub(m: fm_matrix, row0: int, col0: int, rows: int, cols: int) -> fm_sub:
     return fm_sub(m, int(row0), int(col0), int(rows), int(cols))
+
+
+def gf2_matrix(base, log2_grid: int) -> fm_gf2_matrix:
+    return fm_gf2_matrix(_ptr(base), int(log2_grid), 0)
+
+
+def gf2_sub(m: fm_gf2_matrix, row0: int, col0: int, rows: int, cols: int) -> fm_gf2_sub:
+    return fm_gf2_sub(m, int(row0), int(col0), int(rows), int(cols))
 
 
 def opts(k_chunk: int = 0, block_n: int = 0, no_karatsuba: int = 0, cta_pair: int = 0) -> fm_opts:
@@ -334,6 +356,26 @@ def fm_pluq(A: fm_matrix, m: int, n: int, p: int, row_perm, col_perm, stream=Non
     _check(lib().fm_pluq(A, int(m), int(n), int(p), _ptr(row_perm), _ptr(col_perm),
                          ctypes.byref(r), _stream(stream)), "fm_pluq")
     return int(r.value)
+
+
+def fm_gf2_pack(src, rows, cols, ld, dst: fm_gf2_matrix, stream=None):
+    return _check(lib().fm_gf2_pack(_ptr(src), rows, cols, ld, dst, _stream(stream)), "fm_gf2_pack")
+
+
+def fm_gf2_unpack(src: fm_gf2_matrix, rows, cols, dst, ld, stream=None):
+    return _check(lib().fm_gf2_unpack(src, rows, cols, _ptr(dst), ld, _stream(stream)),
+                  "fm_gf2_unpack")
+
+
+def fm_gf2_gemm(C: fm_gf2_sub, A: fm_gf2_sub, B: fm_gf2_sub, op: int = FM_OP_SET, stream=None):
+    return _check(lib().fm_gf2_gemm(C, A, B, int(op), _stream(stream)), "fm_gf2_gemm")
+
+
+def fm_gf2_workspace_size(M: int, N: int, K: int) -> int:
+    r = lib().fm_gf2_workspace_size(int(M), int(N), int(K))
+    if r < 0:
+        raise FmError(int(r), "fm_gf2_workspace_size")
+    return int(r)
 
 
 def fm_get_last_device_status(stream=None) -> int:
