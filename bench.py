@@ -11,9 +11,13 @@ Sec. 2.2, T' = 64) and the FP64 DFMA form run the same step for comparison.
 value     = 2 M N K / (device time of one step), Gop/s (algorithmic ops only)
 e2e       = same, through host buffers: pinned H2D of A, B, C and D2H of C
             inside the timed region
-roofline  = the limb GEMM kernel: tensor work 2 M N K w^2 (w = 2 limbs) per
-            launch / its CUDA-event duration, against the measured bf16 peak
-            (f16 runs at the bf16 rate)
+roofline  = the limb GEMM kernel: tensor work 2 M N K x (limb products: 3
+            with Karatsuba on w = 2 limbs) per launch / its CUDA-event
+            duration, against the measured bf16 sustained peak (f16 runs at
+            the bf16 rate)
+gf2       = C += A*B over GF(2) on bit-packed Morton-hybrid matrices (the
+            paper's experimental field; E4M3 tensor cores), and the paper's
+            workload of 468 random sub-matrix products in 2048 x 2048 matrices
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fm|reference]
 For N > 1 launch with torchrun; every rank runs an independent replica.
@@ -48,6 +52,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip plain / DFMA comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-GEMM measurement")
     ap.add_argument("--no-tu", action="store_true", help="skip the TU decomposition measurement")
+    ap.add_argument("--no-gf2", action="store_true", help="skip the GF(2) measurements")
     return ap.parse_args()
 
 
@@ -360,6 +365,108 @@ def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
             "ops": "2*(m n r - (m+n) r^2/2 + r^3/3)"}
 
 
+def run_gf2(fm, torch, dev, stream, n=8192, paper_n=2048, paper_calls=468, seed=7):
+    """GF(2) on bit-packed Morton-hybrid matrices (T' = 32): C += A*B at n, checked
+    bit-identical to the uint32 limb form at p = 2 on the same inputs, then timed
+    (3 warm-up + 10 timed calls, CUDA events); and the experiments' workload,
+    paper_calls products of random sub-matrices of paper_n x paper_n matrices,
+    timed back to back after one warm-up pass."""
+    import numpy as np
+
+    import fm_inputs
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    lg = 0
+    while (32 << lg) < n:
+        lg += 1
+    words = (32 << lg) ** 2 // 32
+
+    def packed(x):
+        t = torch.zeros(words, dtype=torch.int32, device=dev)
+        m = fm.gf2_matrix(t, lg)
+        src = torch.from_numpy(np.ascontiguousarray(x).view(np.int32)).to(dev)
+        fm.fm_gf2_pack(src, n, n, n, m, stream)
+        return t, m, src
+
+    tA, mA, sA = packed(fm_inputs.uniform_residues(seed, (n, n), 2, 1))
+    tB, mB, sB = packed(fm_inputs.uniform_residues(seed, (n, n), 2, 2))
+    tC, mC, sC = packed(fm_inputs.uniform_residues(seed, (n, n), 2, 3))
+    C, A, B = fm.gf2_sub(mC, 0, 0, n, n), fm.gf2_sub(mA, 0, 0, n, n), fm.gf2_sub(mB, 0, 0, n, n)
+    # the same product through the uint32 limb form at p = 2
+    lt = 7
+    lgm = 0
+    while (1 << lgm) << lt < n:
+        lgm += 1
+    side = (1 << lgm) << lt
+    mats = []
+    for src in (sA, sB, sC):
+        t = torch.zeros(side * side, dtype=torch.int32, device=dev)
+        mm = fm.matrix(t, lgm, lt)
+        fm.fm_layout_to_morton(src, n, n, n, mm, stream)
+        mats.append((t, mm))
+    fm.fm_gemm_modp(fm.sub(mats[2][1], 0, 0, n, n), fm.sub(mats[0][1], 0, 0, n, n),
+                    fm.sub(mats[1][1], 0, 0, n, n), 2, fm.FM_OP_ADD, fm.FM_ALGO_LIMB_TC, None, stream)
+    limb_out = torch.empty(n * n, dtype=torch.int32, device=dev)
+    fm.fm_layout_from_morton(mats[2][1], n, n, limb_out, n, stream)
+    fm.fm_gf2_gemm(C, A, B, fm.FM_OP_ADD, None, stream)
+    gf2_out = torch.empty(n * n, dtype=torch.int32, device=dev)
+    fm.fm_gf2_unpack(mC, n, n, gf2_out, n, stream)
+    torch.cuda.synchronize()
+    identical = bool(torch.equal(limb_out, gf2_out))
+    del mats, limb_out, gf2_out
+    for _ in range(3):
+        fm.fm_gf2_gemm(C, A, B, fm.FM_OP_ADD, None, stream)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        fm.fm_gf2_gemm(C, A, B, fm.FM_OP_ADD, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    e0.record(stream)
+    for _ in range(10):
+        fm.fm_gf2_pack(sC, n, n, n, mC, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pack = e0.elapsed_time(e1) / 10
+    status = fm.fm_get_last_device_status(stream)
+    del tA, tB, tC, sA, sB, sC
+    # the experiments' workload: random sub-matrix products in paper_n x paper_n matrices
+    plg = 0
+    while (32 << plg) < paper_n:
+        plg += 1
+    pw = (32 << plg) ** 2 // 32
+    pm = []
+    for q in range(3):
+        t = torch.zeros(pw, dtype=torch.int32, device=dev)
+        src = torch.from_numpy(fm_inputs.uniform_residues(seed + 1, (paper_n, paper_n), 2, q)
+                               .view(np.int32)).to(dev)
+        fm.fm_gf2_pack(src, paper_n, paper_n, paper_n, fm.gf2_matrix(t, plg), stream)
+        pm.append((t, fm.gf2_matrix(t, plg)))
+    rects = fm_inputs.sub_rectangles(seed, paper_calls, paper_n)
+    calls = [(fm.gf2_sub(pm[0][1], int(r[3]), int(r[4]), int(r[0]), int(r[1])),
+              fm.gf2_sub(pm[1][1], int(r[5]), int(r[6]), int(r[0]), int(r[2])),
+              fm.gf2_sub(pm[2][1], int(r[7]), int(r[8]), int(r[2]), int(r[1]))) for r in rects]
+    ops = float(sum(2.0 * int(r[0]) * int(r[1]) * int(r[2]) for r in rects))
+    for c in calls:
+        fm.fm_gf2_gemm(*c, fm.FM_OP_ADD, None, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for c in calls:
+        fm.fm_gf2_gemm(*c, fm.FM_OP_ADD, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    del pm
+    return {"workload": f"C += A*B over GF(2), n={n}, bit-packed Morton-hybrid T'=32, E4M3 tensor cores",
+            "value": 2.0 * n ** 3 / (ms / 1e3) / 1e9, "unit": "Gop/s", "ms": ms, "pack_ms": ms_pack,
+            "bit_identical_to_limb_p2": identical, "status": status,
+            "paper_workload": {"workload": f"{paper_calls} products of random sub-matrices of "
+                                           f"{paper_n}x{paper_n} bit-packed Morton-hybrid matrices, T'=32",
+                               "ms": pms, "value": ops / (pms / 1e3) / 1e9, "unit": "Gop/s",
+                               "mean_call_us": pms * 1e3 / paper_calls}}
+
+
 def run_fm(args, world, rank, local):
     import numpy as np
     import torch
@@ -562,6 +669,8 @@ def run_fm(args, world, rank, local):
     # ---- TU decomposition of a rank-10000 16384 x 12288 matrix ----
     if not args.no_tu:
         out["tu"] = run_tu(fm, torch, dev, stream)
+    if not args.no_gf2:
+        out["gf2"] = run_gf2(fm, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
     burst, sustained, hbm, src = measured_peaks()
@@ -601,6 +710,8 @@ def run_fm(args, world, rank, local):
         line["batched"] = out["batched"]
     if "tu" in out:
         line["tu"] = out["tu"]
+    if "gf2" in out:
+        line["gf2"] = out["gf2"]
     if "plain" in out:
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]

@@ -338,9 +338,11 @@ int fm_gf2_unpack(fm_gf2_matrix src, int64_t rows, int64_t cols, uint32_t* dst, 
  * (FM_EINVAL). Bits of C outside the sub-matrix are unchanged, also where they
  * share a word with it. Runs on the tensor cores with E4M3 0 / 1 operands and
  * FP32 accumulation (exact: at most 2^24 - 2 terms per accumulation, folded
- * to parity between chunks). Workspace: fm_gf2_workspace_size bytes, cached
- * per device as for fm_gemm_modp. */
-int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, fm_stream stream);
+ * to parity between chunks). opts may be NULL; only opts->cta_pair is read
+ * (1 = CTA pairs on 256 x 256 output tiles). Workspace: fm_gf2_workspace_size
+ * bytes, cached per device as for fm_gemm_modp. */
+int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, const fm_opts* opts,
+                fm_stream stream);
 
 /* Device workspace bytes of fm_gf2_gemm for an M x N x K product. */
 int64_t fm_gf2_workspace_size(int64_t M, int64_t N, int64_t K);

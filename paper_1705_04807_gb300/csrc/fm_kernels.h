@@ -40,7 +40,7 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
 // GF(2) product on bit-packed operands: one E4M3 0/1 plane per operand (tiles of
 // 128 rows x 128 k bytes), one product, parity folded over p = 2 (gf2.cu splits,
 // limb_gemm.cu multiplies).
-int fm_gf2_plan(int64_t M, int64_t N, int64_t K, FmLimbPlan* plan);
+int fm_gf2_plan(int64_t M, int64_t N, int64_t K, bool pair, FmLimbPlan* plan);
 size_t fm_limb_workspace_bytes(const FmLimbPlan& plan);
 int fm_limb_run(const FmLimbPlan& plan, fm_sub C, fm_sub A, fm_sub B, uint32_t p, int op,
                 void* workspace, int* status, cudaStream_t s);

@@ -264,11 +264,12 @@ extern "C" int64_t fm_gf2_workspace_size(int64_t M, int64_t N, int64_t K)
 {
     if (M < 0 || N < 0 || K < 0) return FM_EINVAL;
     FmLimbPlan q;
-    FM_TRY(fm_gf2_plan(M, N, K, &q));
+    FM_TRY(fm_gf2_plan(M, N, K, false, &q));
     return (int64_t)(q.a_plane_bytes + q.b_plane_bytes);
 }
 
-extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, fm_stream stream)
+extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, const fm_opts* opts,
+                           fm_stream stream)
 {
     if (op < FM_OP_SET || op > FM_OP_SUB) return FM_EINVAL;
     FM_TRY(check_gf2_matrix(C.m));
@@ -286,7 +287,7 @@ extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op,
         return FM_OK;
     }
     FmLimbPlan q;
-    FM_TRY(fm_gf2_plan(M, N, K, &q));
+    FM_TRY(fm_gf2_plan(M, N, K, opts && opts->cta_pair == 1, &q));
     uint8_t* Ap = static_cast<uint8_t*>(fm_workspace(0, q.a_plane_bytes + q.b_plane_bytes));
     if (!Ap) return FM_ENOMEM;
     uint8_t* Bp = Ap + q.a_plane_bytes;

@@ -557,6 +557,7 @@ constexpr int kPairStages = 6;
 constexpr uint32_t kPairStageBytes = 2 * kATileBytes;  // A half + B half, 16 KB each
 constexpr size_t kPairSmem = (size_t)kPairStages * kPairStageBytes + 1024;
 
+template <int KIND>
 __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const LimbGemmArgs args)
 {
     constexpr int BN = 256;
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                     for (int kb = kb0; kb < kb1; ++kb, ++g) {
                         const int s = g % S;
                         const uint32_t ph = (g / S) & 1;
-                        if (!fm_mbar_wait_cluster(&full_bar[s], ph, args.status, &s_abort)) {
+                        if (!fm_mbar_wait(&full_bar[s], ph, args.status, &s_abort)) {
                             ok = false;
                             break;
                         }
@@ -687,7 +688,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                             const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
                             const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
                             const uint32_t acc = (t >= 2 || !first || k > 0) ? 1u : 0u;
-                            fm_mma_f16_pair(d_tmem, ad, bd, idesc, acc);
+                            if (KIND == kE4M3Gf2)
+                                fm_mma_e4m3_pair(d_tmem, ad, bd, idesc, acc);
+                            else
+                                fm_mma_f16_pair(d_tmem, ad, bd, idesc, acc);
                         }
                         fm_mma_commit_pair(&empty_bar[s], 0x3);  // stage free in both CTAs
                         first = false;
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                             ok = false;
                             break;
                         }
-                        fm_mbar_arrive_cluster(leader_full + (uint32_t)(s * sizeof(uint64_t)));
+                        fm_mbar_arrive_remote(leader_full + (uint32_t)(s * sizeof(uint64_t)));
                     }
                 }
             }
@@ -807,7 +811,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + (uint32_t)(by * BN) + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < args.M) write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                if (gi < args.M) {
+                    if (KIND == kE4M3Gf2)
+                        write_gf2_run(args, gi, (int64_t)nb * BN + col, sres);
+                    else
+                        write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                }
             }
             fm_tc_fence_before();
             __syncwarp();
@@ -870,12 +879,13 @@ int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
 
 // Clusters of two CTAs, one per pair tile up to the number of pairs that fit
 // on the device at once (the kernel walks further tiles itself).
+template <int KIND>
 int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
 {
     static int max_pairs[64] = {0};
     int dev = 0;
     FM_CUDA_TRY(cudaGetDevice(&dev));
-    auto k = limb_gemm_pair_kernel;
+    auto k = limb_gemm_pair_kernel<KIND>;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -992,7 +1002,7 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     return FM_OK;
 }
 
-int fm_gf2_plan(int64_t M, int64_t N, int64_t K, FmLimbPlan* plan)
+int fm_gf2_plan(int64_t M, int64_t N, int64_t K, bool pair, FmLimbPlan* plan)
 {
     FmLimbPlan q;
     q.M = M;
@@ -1006,6 +1016,7 @@ int fm_gf2_plan(int64_t M, int64_t N, int64_t K, FmLimbPlan* plan)
     q.block_n = 256;
     q.fold = 1;
     q.gf2 = 1;
+    q.pair = pair ? 1 : 0;
     q.MB = (int)((M + kBM - 1) / kBM);
     q.MB += q.MB & 1;
     q.NB = (int)((N + 255) / 256);
@@ -1071,8 +1082,11 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.M = q.M;
     a.N = q.N;
     a.status = status;
-    if (q.gf2) return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
-    if (q.pair) return launch_gemm_pair(a, q.MB / 2 * q.NB, s);
+    if (q.gf2) {
+        if (q.pair) return launch_gemm_pair<kE4M3Gf2>(a, q.MB / 2 * q.NB, s);
+        return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
+    }
+    if (q.pair) return launch_gemm_pair<kF16Res>(a, q.MB / 2 * q.NB, s);
     const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);

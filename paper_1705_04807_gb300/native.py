@@ -124,7 +124,8 @@ def lib():
         "fm_pluq": ([fm_matrix, I64, I64, U32, P, P, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
         "fm_gf2_pack": ([P, I64, I64, I64, fm_gf2_matrix, P], ctypes.c_int),
         "fm_gf2_unpack": ([fm_gf2_matrix, I64, I64, P, I64, P], ctypes.c_int),
-        "fm_gf2_gemm": ([fm_gf2_sub, fm_gf2_sub, fm_gf2_sub, I32, P], ctypes.c_int),
+        "fm_gf2_gemm": ([fm_gf2_sub, fm_gf2_sub, fm_gf2_sub, I32, ctypes.POINTER(fm_opts), P],
+                        ctypes.c_int),
         "fm_gf2_workspace_size": ([I64, I64, I64], I64),
     }
     for name, (args, res) in sig.items():
@@ -367,8 +368,10 @@ def fm_gf2_unpack(src: fm_gf2_matrix, rows, cols, dst, ld, stream=None):
                   "fm_gf2_unpack")
 
 
-def fm_gf2_gemm(C: fm_gf2_sub, A: fm_gf2_sub, B: fm_gf2_sub, op: int = FM_OP_SET, stream=None):
-    return _check(lib().fm_gf2_gemm(C, A, B, int(op), _stream(stream)), "fm_gf2_gemm")
+def fm_gf2_gemm(C: fm_gf2_sub, A: fm_gf2_sub, B: fm_gf2_sub, op: int = FM_OP_SET, options=None,
+                stream=None):
+    o = ctypes.byref(options) if options is not None else None
+    return _check(lib().fm_gf2_gemm(C, A, B, int(op), o, _stream(stream)), "fm_gf2_gemm")
 
 
 def fm_gf2_workspace_size(M: int, N: int, K: int) -> int:

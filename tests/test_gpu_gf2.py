@@ -61,7 +61,7 @@ def test_pack_unpack_against_oracle(env, orc, rows, cols, lg, ld_pad):
     assert np.all(got[:, cols:] == 7)
 
 
-def gf2_case(env, orc, M, N, K, offs, lgs, op, seed):
+def gf2_case(env, orc, M, N, K, offs, lgs, op, seed, options=None):
     fm, dev = env
     rC, cC, rA, cA, rB, cB = offs
     lC, lA, lB = lgs
@@ -71,7 +71,7 @@ def gf2_case(env, orc, M, N, K, offs, lgs, op, seed):
     GC = Gf2Matrix(fm, dev, lC, orc.gf2_pack(Cf, lC))
     GA = Gf2Matrix(fm, dev, lA, orc.gf2_pack(Af, lA))
     GB = Gf2Matrix(fm, dev, lB, orc.gf2_pack(Bf, lB))
-    fm.fm_gf2_gemm(GC.sub(rC, cC, M, N), GA.sub(rA, cA, M, K), GB.sub(rB, cB, K, N), op)
+    fm.fm_gf2_gemm(GC.sub(rC, cC, M, N), GA.sub(rA, cA, M, K), GB.sub(rB, cB, K, N), op, options)
     assert fm.fm_get_last_device_status() == 0
     got = orc.gf2_unpack(GC.words(), lC, GC.n, GC.n)
     want = Cf.copy()
@@ -94,12 +94,15 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_gf2_gemm_parity(env, orc, case):
+@pytest.mark.parametrize("pair", [0, 1])
+def test_gf2_gemm_parity(env, orc, case, pair):
     # full compare of C: the sub-matrix and every bit around it, including the
-    # bits that share a word with its first and last columns
+    # bits that share a word with its first and last columns; single CTAs on
+    # 128 x 256 tiles and CTA pairs on 256 x 256 tiles
     M, N, K, offs, lgs = case
+    options = env[0].opts(cta_pair=pair)
     for op in (0, 1, 2):
-        got, want = gf2_case(env, orc, M, N, K, offs, lgs, op, seed=M + N + K + op)
+        got, want = gf2_case(env, orc, M, N, K, offs, lgs, op, seed=M + N + K + op, options=options)
         assert np.array_equal(got, want), op
 
 
@@ -187,10 +190,12 @@ def test_gf2_8192(env, orc):
     C = fm_inputs.uniform_residues(31, (n, n), 2, 3)
     GA = Gf2Matrix(fm, dev, lg, orc.gf2_pack(A, lg))
     GB = Gf2Matrix(fm, dev, lg, orc.gf2_pack(B, lg))
-    GC = Gf2Matrix(fm, dev, lg, orc.gf2_pack(C, lg))
-    fm.fm_gf2_gemm(GC.sub(0, 0, n, n), GA.sub(0, 0, n, n), GB.sub(0, 0, n, n), 1)
-    assert fm.fm_get_last_device_status() == 0
-    got = orc.gf2_unpack(GC.words(), lg, n, n)
     ij = np.stack([fm_inputs.integers(7, 3000, 0, n - 1, 1), fm_inputs.integers(7, 3000, 0, n - 1, 2)], 1)
-    assert np.array_equal(got[ij[:, 0], ij[:, 1]], orc.gemm_modp_entries(C, A, B, 2, 1, ij))
-    assert orc.freivalds(got, C, A, B, 2, 1, trials=24, seed=3)
+    want = orc.gemm_modp_entries(C, A, B, 2, 1, ij)
+    for pair in (0, 1):
+        GC = Gf2Matrix(fm, dev, lg, orc.gf2_pack(C, lg))
+        fm.fm_gf2_gemm(GC.sub(0, 0, n, n), GA.sub(0, 0, n, n), GB.sub(0, 0, n, n), 1, fm.opts(cta_pair=pair))
+        assert fm.fm_get_last_device_status() == 0
+        got = orc.gf2_unpack(GC.words(), lg, n, n)
+        assert np.array_equal(got[ij[:, 0], ij[:, 1]], want), pair
+        assert orc.freivalds(got, C, A, B, 2, 1, trials=24, seed=3 + pair), pair
