@@ -292,6 +292,25 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
     torch.cuda.synchronize()
     same = bool(torch.equal(tC, per_call_result))
     del per_call_result
+    # the same batch in the tensor-core limb form: 3 launches for all calls
+    plain_result = tC.clone()
+    lplan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC)
+    tC.copy_(snap)
+    lplan.run(stream)
+    torch.cuda.synchronize()
+    limb_same = bool(torch.equal(tC, plain_result))
+    del plain_result
+    for _ in range(2):
+        lplan.run(stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        lplan.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    limb_ms = e0.elapsed_time(e1) / reps
+    limb_tiles = lplan.work_items
+    lplan.close()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(reps):
@@ -307,7 +326,12 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
             "value": ops / (batched_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": batched_ms,
             "per_call_ms": per_call_ms, "per_call_value": ops / (per_call_ms / 1e3) / 1e9,
             "speedup_vs_per_call": per_call_ms / batched_ms, "work_items": items,
-            "launches": 1, "per_call_launches": count, "bit_identical_to_per_call": same}
+            "launches": 1, "per_call_launches": count, "bit_identical_to_per_call": same,
+            "limb": {"workload": "the same calls as one tensor-core limb plan (T' of the operands, "
+                                 "planes of every call in one workspace)",
+                     "value": ops / (limb_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": limb_ms,
+                     "launches": 3, "output_tiles": limb_tiles, "speedup_vs_plain_batched": batched_ms / limb_ms,
+                     "bit_identical_to_plain": limb_same}}
 
 
 def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
@@ -431,7 +455,9 @@ def run_gf2(fm, torch, dev, stream, n=8192, paper_n=2048, paper_calls=468, seed=
     ms_pack = e0.elapsed_time(e1) / 10
     status = fm.fm_get_last_device_status(stream)
     del tA, tB, tC, sA, sB, sC
-    # the experiments' workload: random sub-matrix products in paper_n x paper_n matrices
+    # the experiments' workload: random sub-matrix products in paper_n x paper_n
+    # matrices; every product is its own experiment, so each writes its own C
+    # matrix (random C rectangles of one matrix would overlap)
     plg = 0
     while (32 << plg) < paper_n:
         plg += 1
@@ -444,27 +470,58 @@ def run_gf2(fm, torch, dev, stream, n=8192, paper_n=2048, paper_calls=468, seed=
         fm.fm_gf2_pack(src, paper_n, paper_n, paper_n, fm.gf2_matrix(t, plg), stream)
         pm.append((t, fm.gf2_matrix(t, plg)))
     rects = fm_inputs.sub_rectangles(seed, paper_calls, paper_n)
-    calls = [(fm.gf2_sub(pm[0][1], int(r[3]), int(r[4]), int(r[0]), int(r[1])),
+    cs = pm[0][0].repeat(paper_calls)  # paper_calls copies of the first matrix
+    cmats = [fm.gf2_matrix(cs[c * pw:(c + 1) * pw], plg) for c in range(paper_calls)]
+    calls = [(fm.gf2_sub(cmats[c], int(r[3]), int(r[4]), int(r[0]), int(r[1])),
               fm.gf2_sub(pm[1][1], int(r[5]), int(r[6]), int(r[0]), int(r[2])),
-              fm.gf2_sub(pm[2][1], int(r[7]), int(r[8]), int(r[2]), int(r[1]))) for r in rects]
+              fm.gf2_sub(pm[2][1], int(r[7]), int(r[8]), int(r[2]), int(r[1]))) for c, r in enumerate(rects)]
     ops = float(sum(2.0 * int(r[0]) * int(r[1]) * int(r[2]) for r in rects))
+    snap = cs.clone()
     for c in calls:
         fm.fm_gf2_gemm(*c, fm.FM_OP_ADD, None, stream)
     torch.cuda.synchronize()
+    per_call_result = cs.clone()
     e0.record(stream)
     for c in calls:
         fm.fm_gf2_gemm(*c, fm.FM_OP_ADD, None, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     pms = e0.elapsed_time(e1)
-    del pm
+    # the same products as one plan: three launches for the whole batch
+    gcalls = []
+    for c in calls:
+        g = fm.fm_gf2_call()
+        g.C, g.A, g.B = c
+        g.op = fm.FM_OP_ADD
+        gcalls.append(g)
+    plan = fm.fm_gf2_plan_create(gcalls)
+    cs.copy_(snap)
+    plan.run(stream)
+    torch.cuda.synchronize()
+    plan_same = bool(torch.equal(cs, per_call_result))
+    for _ in range(2):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        plan.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan_ms = e0.elapsed_time(e1) / 5
+    plan.close()
+    del pm, cs, snap, per_call_result
     return {"workload": f"C += A*B over GF(2), n={n}, bit-packed Morton-hybrid T'=32, E4M3 tensor cores",
             "value": 2.0 * n ** 3 / (ms / 1e3) / 1e9, "unit": "Gop/s", "ms": ms, "pack_ms": ms_pack,
             "bit_identical_to_limb_p2": identical, "status": status,
             "paper_workload": {"workload": f"{paper_calls} products of random sub-matrices of "
-                                           f"{paper_n}x{paper_n} bit-packed Morton-hybrid matrices, T'=32",
+                                           f"{paper_n}x{paper_n} bit-packed Morton-hybrid matrices, T'=32 "
+                                           f"(one C matrix per product)",
                                "ms": pms, "value": ops / (pms / 1e3) / 1e9, "unit": "Gop/s",
-                               "mean_call_us": pms * 1e3 / paper_calls}}
+                               "mean_call_us": pms * 1e3 / paper_calls,
+                               "plan": {"ms": plan_ms, "value": ops / (plan_ms / 1e3) / 1e9,
+                                        "unit": "Gop/s", "launches": 3,
+                                        "speedup_vs_per_call": pms / plan_ms,
+                                        "bit_identical_to_per_call": plan_same}}}
 
 
 def run_fm(args, world, rank, local):

@@ -240,19 +240,28 @@ typedef struct fm_gemm_call {
 
 typedef struct fm_plan fm_plan;
 
-/* Plans a batch of n calls (host array calls[0..n-1]) for one modulus p:
- * decomposes every call into contained tile products (Sec. 2.2), packs them
- * into one work list and uploads it. Calls of one batch must write disjoint
- * C regions. The plan owns its device workspace until fm_plan_destroy. */
+/* Plans a batch of n calls (host array calls[0..n-1]) for one modulus p.
+ * Calls of one batch must write disjoint C regions. The plan owns its device
+ * workspace until fm_plan_destroy.
+ *   FM_ALGO_AUTO / FM_ALGO_PLAIN / FM_ALGO_DFMA: decomposes every call into
+ *     contained tile products (Sec. 2.2; all matrices with T' = 32 or 64), packs
+ *     them into one work list and uploads it.
+ *   FM_ALGO_LIMB_TC: the tensor-core limb form for the whole batch (any T'):
+ *     limb planes for every call's operands in one workspace (cached in the
+ *     plan); opts as for fm_gemm_modp except cta_pair (FM_EUNSUPPORTED). */
 int fm_plan_create(fm_plan** plan, const fm_gemm_call* calls, int64_t n, uint32_t p,
                    int32_t algo, const fm_opts* opts);
 
-/* Runs every call of the plan in ONE persistent kernel launch on stream (its
- * CTAs pull work items from a device queue). May be captured in a CUDA graph;
- * the plan must outlive the graph. */
+/* Runs every call of the plan on stream. Decomposed forms: ONE persistent
+ * kernel launch whose CTAs pull work items from a device queue. Limb form:
+ * three launches for the whole batch (limb split of every A, of every B, and
+ * one persistent GEMM over the output tiles of every call, longest first),
+ * plus one small launch per call with K = 0 under FM_OP_SET. May be captured
+ * in a CUDA graph; the plan must outlive the graph. */
 int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream);
 
-/* Number of work items / base-case tile products in the plan (host). */
+/* Work items (decomposed forms: base-case tile products; limb form: output
+ * tiles) of the plan (host). */
 int64_t fm_plan_work_items(const fm_plan* plan);
 
 int fm_plan_destroy(fm_plan* plan);
@@ -346,6 +355,23 @@ int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, const fm_o
 
 /* Device workspace bytes of fm_gf2_gemm for an M x N x K product. */
 int64_t fm_gf2_workspace_size(int64_t M, int64_t N, int64_t K);
+
+/* One call of a GF(2) batch: C <- A*B (FM_OP_SET) or C + A*B (FM_OP_ADD /
+ * FM_OP_SUB) on bit-packed sub-matrices (fields as in fm_gf2_gemm). */
+typedef struct fm_gf2_call {
+    fm_gf2_sub C, A, B;
+    int32_t op;
+    int32_t reserved;
+} fm_gf2_call;
+
+/* Plans a batch of n GF(2) calls (the experiments' workload of Sec. 2.2 is such
+ * a batch of independent sub-matrix products). Calls of one batch must write
+ * disjoint C regions (they may share words). Run it with fm_gemm_modp_batched (three
+ * launches: the E4M3 split of every A, of every B, one persistent GEMM over
+ * the output tiles of every call; plus one launch per call with K = 0 under
+ * FM_OP_SET) and free it with fm_plan_destroy. opts may be NULL (cta_pair is
+ * not supported: FM_EUNSUPPORTED). */
+int fm_gf2_plan_create(fm_plan** plan, const fm_gf2_call* calls, int64_t n, const fm_opts* opts);
 
 /* ---- status ------------------------------------------------------------- */
 

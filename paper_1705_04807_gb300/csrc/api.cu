@@ -302,6 +302,7 @@ struct fm_plan {
     FmLPiece* d_lps = nullptr;
     int* d_queue = nullptr;
     int grid = 0;
+    FmLimbBatch* limb = nullptr;  // FM_ALGO_LIMB_TC: the batched tensor-core form
 };
 
 extern "C" int fm_plan_create(fm_plan** out, const fm_gemm_call* calls, int64_t n, uint32_t p,
@@ -311,6 +312,24 @@ extern "C" int fm_plan_create(fm_plan** out, const fm_gemm_call* calls, int64_t 
     if (!out || (n > 0 && !calls) || n < 0) return FM_EINVAL;
     *out = nullptr;
     if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
+    if (algo == FM_ALGO_LIMB_TC) {
+        for (int64_t c = 0; c < n; ++c) {
+            const fm_gemm_call& g = calls[c];
+            if (g.op < FM_OP_SET || g.op > FM_OP_SUB) return FM_EINVAL;
+            FM_TRY(fm_check_product(g.C, g.A, g.B, false));
+        }
+        fm_plan* pl = new fm_plan();
+        pl->device = current_device();
+        pl->p = p;
+        const int rc = fm_limb_batch_create(calls, n, p, opts, &pl->limb);
+        if (rc != FM_OK) {
+            delete pl;
+            return rc;
+        }
+        pl->n_items = fm_limb_batch_tiles(pl->limb);
+        *out = pl;
+        return FM_OK;
+    }
     if (algo != FM_ALGO_AUTO && algo != FM_ALGO_PLAIN && algo != FM_ALGO_DFMA) return FM_EUNSUPPORTED;
     int lt = -1;
     int64_t kmax = 0;
@@ -367,9 +386,34 @@ extern "C" int fm_plan_create(fm_plan** out, const fm_gemm_call* calls, int64_t 
     return FM_OK;
 }
 
+extern "C" int fm_gf2_plan_create(fm_plan** out, const fm_gf2_call* calls, int64_t n, const fm_opts* opts)
+{
+    if (!out || (n > 0 && !calls) || n < 0) return FM_EINVAL;
+    *out = nullptr;
+    for (int64_t c = 0; c < n; ++c) FM_TRY(fm_gf2_check_call(calls[c]));
+    fm_plan* pl = new fm_plan();
+    pl->device = current_device();
+    pl->p = 2;
+    const int rc = fm_gf2_batch_create(calls, n, opts, &pl->limb);
+    if (rc != FM_OK) {
+        delete pl;
+        return rc;
+    }
+    pl->n_items = fm_limb_batch_tiles(pl->limb);
+    *out = pl;
+    return FM_OK;
+}
+
 extern "C" int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream)
 {
     if (!plan) return FM_EINVAL;
+    if (plan->limb) {
+        for (const fm_gemm_call& g : fm_limb_batch_zero_calls(plan->limb))
+            if (g.op == FM_OP_SET) FM_TRY(fm_gemm_modp(g.C, g.A, g.B, plan->p, g.op, FM_ALGO_LIMB_TC, nullptr, stream));
+        int* status = fm_device_status();
+        if (!status) return FM_ECUDA;
+        return fm_limb_batch_run(plan->limb, status, (cudaStream_t)stream);
+    }
     if (plan->n_items == 0) return FM_OK;
     int* status = fm_device_status();
     if (!status) return FM_ECUDA;
@@ -392,6 +436,7 @@ extern "C" int fm_plan_destroy(fm_plan* plan)
     cudaFree(plan->d_items);
     cudaFree(plan->d_lps);
     cudaFree(plan->d_queue);
+    fm_limb_batch_destroy(plan->limb);
     delete plan;
     return FM_OK;
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fm_sched.h"
 
 enum { kArithNarrow = 0, kArithWide = 1, kArithDfma = 2 };
@@ -46,8 +48,41 @@ int fm_limb_run(const FmLimbPlan& plan, fm_sub C, fm_sub A, fm_sub B, uint32_t p
                 void* workspace, int* status, cudaStream_t s);
 int fm_limb_split_run(const FmLimbPlan& plan, fm_sub X, int role, uint32_t p, void* planes,
                       cudaStream_t s);
+// One operand of a batched split: X (rows x cols as used: M x K for A, K x N
+// for B) -> its limb planes at out.
+struct FmSplitDesc {
+    const uint32_t* src;
+    int lt;
+    int KB;
+    int64_t row0, col0, rows, cols;
+    uint8_t* out;
+    size_t plane_bytes;
+};
+// Splits tile jobs[b].y of operand descs[jobs[b].x], b < n_jobs, in one launch;
+// q supplies the limb parameters (w, planes, block_n) shared by all operands.
+int fm_limb_split_batch_run(const FmLimbPlan& q, int role, const FmSplitDesc* d_descs,
+                            const int2* d_jobs, int64_t n_jobs, uint32_t p, cudaStream_t s);
 int fm_limb_gemm_run(const FmLimbPlan& plan, fm_sub C, const void* a_planes,
                      const void* b_planes, uint32_t p, int op, int* status, cudaStream_t s);
+
+// Batched limb form (limb_gemm.cu): every call's limb planes in one workspace;
+// a run is two split launches and one persistent GEMM launch over the output
+// tiles of every call. Calls with K = 0 are set aside (zero_calls): the caller
+// runs them (only FM_OP_SET changes C).
+struct FmLimbBatch;
+int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const fm_opts* opts,
+                         FmLimbBatch** out);
+int fm_limb_batch_run(FmLimbBatch* b, int* status, cudaStream_t s);
+int64_t fm_limb_batch_tiles(const FmLimbBatch* b);
+const std::vector<fm_gemm_call>& fm_limb_batch_zero_calls(const FmLimbBatch* b);
+void fm_limb_batch_destroy(FmLimbBatch* b);
+// GF(2) batches (gf2.cu splits; limb_gemm.cu plans and multiplies): the same
+// three launches on bit-packed operands (FmSplitDesc.lt carries log2_grid).
+int fm_gf2_batch_create(const fm_gf2_call* calls, int64_t n, const fm_opts* opts, FmLimbBatch** out);
+int fm_gf2_split_batch_run(int role, const FmSplitDesc* d_descs, const int2* d_jobs, int64_t n_jobs,
+                           cudaStream_t s);
+int fm_gf2_zero_sub(const fm_gf2_sub& C, cudaStream_t s);
+int fm_gf2_check_call(const fm_gf2_call& g);  // argument checks of fm_gf2_gemm
 
 // Remembered autotune choice for a problem class (autotune.cu).
 bool fm_tuned_choice(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result* out);

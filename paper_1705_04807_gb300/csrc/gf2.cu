@@ -129,12 +129,12 @@ __global__ void gf2_unpack_kernel(const uint32_t* __restrict__ src, int lg, int6
 
 // A (M x K sub-matrix) -> plane of [MB][KB] tiles, 128 rows x 128 k bytes.
 // Thread item (r, q): row r of the tile, k bits [32 q, 32 q + 32) -> chunks 2q, 2q+1.
-__global__ void __launch_bounds__(kGf2Threads) gf2_split_a_kernel(
-    const uint32_t* __restrict__ base, int lg, int64_t row0, int64_t col0, int64_t M, int64_t K,
-    int KB, uint8_t* __restrict__ out)
+__device__ __forceinline__ void gf2_split_a_tile(const uint32_t* __restrict__ base, int lg, int64_t row0,
+                                                 int64_t col0, int64_t M, int64_t K, int KB, int t,
+                                                 uint8_t* __restrict__ out)
 {
-    const int mb = blockIdx.x / KB, kb = blockIdx.x % KB;
-    uint8_t* tile = out + (size_t)blockIdx.x * kATileBytes;
+    const int mb = t / KB, kb = t % KB;
+    uint8_t* tile = out + (size_t)t * kATileBytes;
     const uint64_t words = (uint64_t)1 << lg;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(kGf2Threads) gf2_split_a_kernel(
 // (B transposed). A warp takes 32 x 32 blocks: lane i reads 32 column bits of
 // B row l0 + i, and 32 ballots turn them into lane j's 32 row bits of column
 // n0 + j.
-__global__ void __launch_bounds__(kGf2Threads) gf2_split_b_kernel(
-    const uint32_t* __restrict__ base, int lg, int64_t row0, int64_t col0, int64_t K, int64_t N,
-    int KB, uint8_t* __restrict__ out)
+__device__ __forceinline__ void gf2_split_b_tile(const uint32_t* __restrict__ base, int lg, int64_t row0,
+                                                 int64_t col0, int64_t K, int64_t N, int KB, int t,
+                                                 uint8_t* __restrict__ out)
 {
-    const int nb = blockIdx.x / KB, kb = blockIdx.x % KB;
-    uint8_t* tile = out + (size_t)blockIdx.x * (256 * 128);
+    const int nb = t / KB, kb = t % KB;
+    uint8_t* tile = out + (size_t)t * (256 * 128);
     const uint64_t words = (uint64_t)1 << lg;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
@@ -180,6 +180,38 @@ __global__ void __launch_bounds__(kGf2Threads) gf2_split_b_kernel(
         *tile_chunk(tile, r, 2 * lb) = expand16(col & 0xFFFFu);
         *tile_chunk(tile, r, 2 * lb + 1) = expand16(col >> 16);
     }
+}
+
+__global__ void __launch_bounds__(kGf2Threads) gf2_split_a_kernel(
+    const uint32_t* __restrict__ base, int lg, int64_t row0, int64_t col0, int64_t M, int64_t K,
+    int KB, uint8_t* __restrict__ out)
+{
+    gf2_split_a_tile(base, lg, row0, col0, M, K, KB, blockIdx.x, out);
+}
+
+__global__ void __launch_bounds__(kGf2Threads) gf2_split_b_kernel(
+    const uint32_t* __restrict__ base, int lg, int64_t row0, int64_t col0, int64_t K, int64_t N,
+    int KB, uint8_t* __restrict__ out)
+{
+    gf2_split_b_tile(base, lg, row0, col0, K, N, KB, blockIdx.x, out);
+}
+
+// Batched: CTA b splits tile jobs[b].y of operand jobs[b].x (lt carries the
+// operand's log2_grid).
+__global__ void __launch_bounds__(kGf2Threads) gf2_split_a_batch_kernel(const FmSplitDesc* __restrict__ d,
+                                                                        const int2* __restrict__ jobs)
+{
+    const int2 j = jobs[blockIdx.x];
+    const FmSplitDesc x = d[j.x];
+    gf2_split_a_tile(x.src, x.lt, x.row0, x.col0, x.rows, x.cols, x.KB, j.y, x.out);
+}
+
+__global__ void __launch_bounds__(kGf2Threads) gf2_split_b_batch_kernel(const FmSplitDesc* __restrict__ d,
+                                                                        const int2* __restrict__ jobs)
+{
+    const int2 j = jobs[blockIdx.x];
+    const FmSplitDesc x = d[j.x];
+    gf2_split_b_tile(x.src, x.lt, x.row0, x.col0, x.rows, x.cols, x.KB, j.y, x.out);
 }
 
 // C <- 0 on a sub-matrix (the product with K = 0 under FM_OP_SET).
@@ -229,6 +261,27 @@ fm_sub as_sub(const fm_gf2_sub& s)
 
 }  // namespace
 
+int fm_gf2_split_batch_run(int role, const FmSplitDesc* d_descs, const int2* d_jobs, int64_t n_jobs,
+                           cudaStream_t s)
+{
+    if (n_jobs == 0) return FM_OK;
+    if (n_jobs > 0x7fffffff) return FM_EINVAL;
+    if (role == FM_LIMB_A)
+        gf2_split_a_batch_kernel<<<(unsigned)n_jobs, kGf2Threads, 0, s>>>(d_descs, d_jobs);
+    else
+        gf2_split_b_batch_kernel<<<(unsigned)n_jobs, kGf2Threads, 0, s>>>(d_descs, d_jobs);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+int fm_gf2_zero_sub(const fm_gf2_sub& C, cudaStream_t s)
+{
+    if (C.rows == 0 || C.cols == 0) return FM_OK;
+    gf2_zero_kernel<<<fm_sm_count() * 4, 256, 0, s>>>(C.m.base, C.row0, C.col0, C.rows, C.cols);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
 extern "C" int fm_gf2_pack(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
                            fm_gf2_matrix dst, fm_stream stream)
 {
@@ -268,15 +321,26 @@ extern "C" int64_t fm_gf2_workspace_size(int64_t M, int64_t N, int64_t K)
     return (int64_t)(q.a_plane_bytes + q.b_plane_bytes);
 }
 
+int fm_gf2_check_call(const fm_gf2_call& g)
+{
+    if (g.op < FM_OP_SET || g.op > FM_OP_SUB) return FM_EINVAL;
+    FM_TRY(check_gf2_matrix(g.C.m));
+    FM_TRY(check_gf2_matrix(g.A.m));
+    FM_TRY(check_gf2_matrix(g.B.m));
+    return fm_check_product(as_sub(g.C), as_sub(g.A), as_sub(g.B), false);
+}
+
 extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, const fm_opts* opts,
                            fm_stream stream)
 {
-    if (op < FM_OP_SET || op > FM_OP_SUB) return FM_EINVAL;
-    FM_TRY(check_gf2_matrix(C.m));
-    FM_TRY(check_gf2_matrix(A.m));
-    FM_TRY(check_gf2_matrix(B.m));
-    const fm_sub Cs = as_sub(C), As = as_sub(A), Bs = as_sub(B);
-    FM_TRY(fm_check_product(Cs, As, Bs, false));
+    fm_gf2_call g;
+    g.C = C;
+    g.A = A;
+    g.B = B;
+    g.op = op;
+    g.reserved = 0;
+    FM_TRY(fm_gf2_check_call(g));
+    const fm_sub Cs = as_sub(C);
     const int64_t M = C.rows, N = C.cols, K = A.cols;
     if (M == 0 || N == 0) return FM_OK;
     cudaStream_t s = (cudaStream_t)stream;

@@ -24,6 +24,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "fm_internal.cuh"
 #include "fm_kernels.h"
@@ -62,23 +64,33 @@ __device__ __forceinline__ uint32_t op_combine(uint32_t c, uint32_t s, uint32_t 
     return cc >= s ? cc - s : cc + (p - s);
 }
 
-struct LimbGemmArgs {
+// Per-call part of a limb GEMM: its limb planes, K stages and jobs, and its C
+// sub-matrix.
+struct LimbCall {
     const uint8_t* Ap;
     const uint8_t* Bp;
     uint64_t a_plane_bytes, b_plane_bytes;
-    int MB, NB, KB, n_products;
+    int MB, NB, KB, njobs;
+    int first[17];  // first job of product k; first[n_products] = njobs
+    uint32_t* C;
+    int c_lt, op;
+    int64_t c_row0, c_col0, M, N;
+};
+
+struct LimbGemmArgs {
+    LimbCall call;          // one call (the batched kernel reads calls[] instead)
+    const LimbCall* calls;  // batched: call table
+    const int4* tiles;      // batched: (call, mb, nb) per output tile, longest first
+    int n_tiles;            // batched: number of output tiles
+    int n_products;
     int pa[16], pb[16];  // planes of A and B of product k
     int cs[16];          // 64-wide K stages per chunk of product k
-    int first[17];       // first job of product k; first[n_products] = number of jobs
     uint32_t p, mu32;
     uint64_t mu64;
     uint32_t wt[16];  // weight of product k mod p
     uint32_t cn[16];  // fold form: cn[k * 4 + k2] = wt[k] * wt[k2]^-1 mod p
     float invp, pf;   // fold form: 1/p and p as float
     uint64_t offs64;  // residue form: multiple of p >= 2^31 (makes an int32 sum non-negative)
-    uint32_t* C;
-    int c_lt, op;
-    int64_t c_row0, c_col0, M, N;
     int* status;
 };
 
@@ -125,28 +137,27 @@ __device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool t
 // C(gi, j0 .. j0+W-1) <- C op sres (mod p), in the Morton-hybrid layout. Loads
 // are issued before stores; a run inside one tile row moves as 16-byte vectors.
 template <int W>
-__device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi, int64_t j0,
+__device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, int64_t gi, int64_t j0,
                                             uint64_t cmask, const uint32_t (&sres)[W])
 {
-    const uint32_t p = args.p;
-    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
-    const uint64_t cj0 = (uint64_t)(args.c_col0 + j0);
-    const uint64_t base = fm_encode(ci, cj0, args.c_lt);
-    const bool run = j0 + W <= args.N && (cj0 & cmask) + W <= cmask + 1 && (base & 3) == 0;
+    const uint64_t ci = (uint64_t)(c.c_row0 + gi);
+    const uint64_t cj0 = (uint64_t)(c.c_col0 + j0);
+    const uint64_t base = fm_encode(ci, cj0, c.c_lt);
+    const bool run = j0 + W <= c.N && (cj0 & cmask) + W <= cmask + 1 && (base & 3) == 0;
     if (run) {
-        uint4* dst = reinterpret_cast<uint4*>(args.C + base);
+        uint4* dst = reinterpret_cast<uint4*>(c.C + base);
         uint4 old[W / 4];
-        if (args.op != FM_OP_SET) {
+        if (c.op != FM_OP_SET) {
 #pragma unroll
             for (int q = 0; q < W / 4; ++q) old[q] = dst[q];
         }
 #pragma unroll
         for (int q = 0; q < W / 4; ++q) {
-            uint4 o = args.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
-            o.x = op_combine(o.x, sres[4 * q + 0], p, args.op);
-            o.y = op_combine(o.y, sres[4 * q + 1], p, args.op);
-            o.z = op_combine(o.z, sres[4 * q + 2], p, args.op);
-            o.w = op_combine(o.w, sres[4 * q + 3], p, args.op);
+            uint4 o = c.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
+            o.x = op_combine(o.x, sres[4 * q + 0], p, c.op);
+            o.y = op_combine(o.y, sres[4 * q + 1], p, c.op);
+            o.z = op_combine(o.z, sres[4 * q + 2], p, c.op);
+            o.w = op_combine(o.w, sres[4 * q + 3], p, c.op);
             dst[q] = o;
         }
         return;
@@ -160,12 +171,12 @@ __device__ __forceinline__ void write_c_run(const LimbGemmArgs& args, int64_t gi
         uint64_t a[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            a[e] = fm_encode(ci, cj0 + g + e, args.c_lt);
-            old[e] = (args.op != FM_OP_SET && j0 + g + e < args.N) ? args.C[a[e]] : 0u;
+            a[e] = fm_encode(ci, cj0 + g + e, c.c_lt);
+            old[e] = (c.op != FM_OP_SET && j0 + g + e < c.N) ? c.C[a[e]] : 0u;
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-            if (j0 + g + e < args.N) args.C[a[e]] = op_combine(old[e], sres[g + e], p, args.op);
+            if (j0 + g + e < c.N) c.C[a[e]] = op_combine(old[e], sres[g + e], p, c.op);
     }
 }
 
@@ -193,23 +204,23 @@ __device__ __forceinline__ void gf2_apply(uint32_t* w, uint32_t m, uint32_t x, i
     }
 }
 
-__device__ __forceinline__ void write_gf2_run(const LimbGemmArgs& args, int64_t gi, int64_t j0,
+__device__ __forceinline__ void write_gf2_run(const LimbCall& c, int64_t gi, int64_t j0,
                                               const uint32_t (&r)[32])
 {
-    const int64_t nvalid = args.N - j0;
+    const int64_t nvalid = c.N - j0;
     if (nvalid <= 0) return;
     uint32_t bits = 0;
 #pragma unroll
     for (int e = 0; e < 32; ++e) bits |= (r[e] & 1u) << e;
     const uint32_t vmask = nvalid >= 32 ? ~0u : ((1u << nvalid) - 1u);
     bits &= vmask;
-    const uint64_t ci = (uint64_t)(args.c_row0 + gi);
-    const uint64_t cj = (uint64_t)(args.c_col0 + j0);
+    const uint64_t ci = (uint64_t)(c.c_row0 + gi);
+    const uint64_t cj = (uint64_t)(c.c_col0 + j0);
     const uint32_t b = (uint32_t)(cj & 31);
-    gf2_apply(args.C + (fm_encode(ci, cj, 5) >> 5), vmask << b, bits << b, args.op);
+    gf2_apply(c.C + (fm_encode(ci, cj, 5) >> 5), vmask << b, bits << b, c.op);
     if (b != 0) {
         const uint32_t m1 = vmask >> (32 - b);
-        if (m1) gf2_apply(args.C + (fm_encode(ci, cj + (32 - b), 5) >> 5), m1, bits >> (32 - b), args.op);
+        if (m1) gf2_apply(c.C + (fm_encode(ci, cj + (32 - b), 5) >> 5), m1, bits >> (32 - b), c.op);
     }
 }
 
@@ -229,8 +240,9 @@ struct GemmCfg {
 // kE4M3Gf2 = E4M3 0/1 planes (GF(2)), parity bits written to a bit-packed C.
 enum { kF16Res = 0, kE4M3Gf2 = 1 };
 
-template <int BN, bool FOLD, int KIND>
-__global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGemmArgs args)
+template <int BN, bool FOLD, int KIND, bool BATCH>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    limb_gemm_kernel(const __grid_constant__ LimbGemmArgs args)
 {
     using Cfg = GemmCfg<BN>;
     constexpr int S = Cfg::kStages;
@@ -247,18 +259,35 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
     __shared__ uint32_t s_issued, s_consumed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_tiles = args.MB * args.NB;
-    const int njobs = args.first[args.n_products];  // jobs per tile
+    // row blocks holding rows of C (the A planes may carry one more, zero)
+    const int mb_rows = (int)((args.call.M + kBM - 1) / kBM);
+    const int n_tiles = BATCH ? args.n_tiles : mb_rows * args.call.NB;
 
-    // tile -> (mb, nb): grouped raster (groups of 8 row blocks) for L2 reuse
-    auto coords = [&](int tile, int& mb, int& nb) {
+    // tile -> its call and (mb, nb). One call: grouped raster (groups of 8 row
+    // blocks) for L2 reuse; batched: the plan's tile list.
+    auto tile_call = [&](int tile, int& mb, int& nb) -> const LimbCall& {
+        if (BATCH) {
+            const int4 e = args.tiles[tile];
+            mb = e.y;
+            nb = e.z;
+            return args.calls[e.x];
+        }
         const int GROUP = 8;
-        const int per_group = GROUP * args.NB;
+        const int per_group = GROUP * args.call.NB;
         const int first_mb = (tile / per_group) * GROUP;
-        const int gsz = min(args.MB - first_mb, GROUP);
+        const int gsz = min(mb_rows - first_mb, GROUP);
         const int inner = tile % per_group;
         mb = first_mb + inner % gsz;
         nb = inner / gsz;
+        return args.call;
+    };
+    // rows and columns of the tile inside C; the MMA runs on the valid columns
+    // rounded up to 16 (its N granularity) and loads only the rows it needs
+    auto tile_rows = [&](const LimbCall& cl, int mb) {
+        return (int)min((int64_t)kBM, cl.M - (int64_t)mb * kBM);
+    };
+    auto tile_cols = [&](const LimbCall& cl, int nb) {
+        return (int)min((int64_t)BN, cl.N - (int64_t)nb * BN);
     };
 
     if (tid == 0) {
@@ -292,16 +321,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 int mb, nb;
-                coords(tile, mb, nb);
+                const LimbCall& cl = tile_call(tile, mb, nb);
+                const int njobs = cl.njobs;
+                const uint32_t a_bytes = (uint32_t)tile_rows(cl, mb) * 128u;
+                const uint32_t b_bytes = (uint32_t)((tile_cols(cl, nb) + 15) & ~15) * 128u;
                 int idx = 0;
                 for (int t = 0; t < njobs && ok; ++t) {
-                    while (t >= args.first[idx + 1]) ++idx;
-                    const int c = t - args.first[idx];
-                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
-                    const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
-                                           ((size_t)mb * args.KB) * kATileBytes;
-                    const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
-                                           ((size_t)nb * args.KB) * Cfg::kBTileBytes;
+                    while (t >= cl.first[idx + 1]) ++idx;
+                    const int c = t - cl.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(cl.KB, kb0 + args.cs[idx]);
+                    const uint8_t* a_src = cl.Ap + (size_t)args.pa[idx] * cl.a_plane_bytes +
+                                           ((size_t)mb * cl.KB) * kATileBytes;
+                    const uint8_t* b_src = cl.Bp + (size_t)args.pb[idx] * cl.b_plane_bytes +
+                                           ((size_t)nb * cl.KB) * Cfg::kBTileBytes;
                     for (int kb = kb0; kb < kb1; ++kb, ++g) {
                         const int s = g % S;
                         const uint32_t ph = (g / S) & 1;
@@ -310,10 +342,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                             break;
                         }
                         uint8_t* sa = smem + (size_t)s * Cfg::kStageBytes;
-                        fm_mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
-                        fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
-                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * Cfg::kBTileBytes,
-                                    Cfg::kBTileBytes, &full_bar[s]);
+                        fm_mbar_arrive_expect_tx(&full_bar[s], a_bytes + b_bytes);
+                        fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, a_bytes, &full_bar[s]);
+                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * Cfg::kBTileBytes, b_bytes,
+                                    &full_bar[s]);
                     }
                 }
             }
@@ -322,16 +354,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            const uint32_t idesc = fm_idesc_f16_f32(kBM, BN);
             uint32_t g = 0, T = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int mb, nb;
+                const LimbCall& cl = tile_call(tile, mb, nb);
+                const int njobs = cl.njobs;
+                const uint32_t idesc = fm_idesc_f16_f32(kBM, (tile_cols(cl, nb) + 15) & ~15);
                 int idx = 0;
                 for (int t = 0; t < njobs && ok; ++t, ++T) {
                     const int b = T & 1;
-                    while (t >= args.first[idx + 1]) ++idx;
-                    const int c = t - args.first[idx];
-                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    while (t >= cl.first[idx + 1]) ++idx;
+                    const int c = t - cl.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(cl.KB, kb0 + args.cs[idx]);
                     if (T >= 2 &&
                         !fm_mbar_wait(&acce_bar[b], ((T >> 1) - 1) & 1, args.status, &s_abort)) {
                         ok = false;
@@ -386,12 +421,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const uint32_t col0 = (uint32_t)(half * kCols);
         const uint32_t p = args.p;
-        const uint64_t cmask = (1ull << args.c_lt) - 1;
+        
         uint32_t T = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             int mb, nb;
-            coords(tile, mb, nb);
+            const LimbCall& cl = tile_call(tile, mb, nb);
+            const int njobs = cl.njobs;
+            // 32-column chunks of this warp inside C (none when its lane
+            // quarter lies below the last row): the rest is never written
+            const int live_cols = quarter * 32 < tile_rows(cl, mb) ? tile_cols(cl, nb) - (int)col0 : 0;
+            const int n32 = max(0, min(kCols / 32, (live_cols + 31) / 32));
             int idx = 0;
             for (int t = 0; t < njobs; ++t, ++T) {
                 const int b = T & 1;
@@ -400,21 +440,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                     break;
                 }
                 fm_tc_fence_after();
-                while (t >= args.first[idx + 1]) ++idx;
-                const int c = t - args.first[idx];
-                const int n_chunks = args.first[idx + 1] - args.first[idx];
+                while (t >= cl.first[idx + 1]) ++idx;
+                const int c = t - cl.first[idx];
+                const int n_chunks = cl.first[idx + 1] - cl.first[idx];
                 const bool last_on_buffer = (t + 2 >= njobs);
                 // fold form: the job two steps later on this buffer continues the
                 // same limb product (same weight) unless a product boundary lies between
                 int idx2 = idx;
                 if (!last_on_buffer)
-                    while (t + 2 >= args.first[idx2 + 1]) ++idx2;
+                    while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
                 const bool same_next = !last_on_buffer && idx2 == idx;
                 const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
                 if (FOLD) {
                     const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
-                    for (int g = 0; g < kCols / 64; ++g) {  // two 32-column chunks in flight
+                    for (int g = 0; g < (n32 + 1) / 2; ++g) {  // two 32-column chunks in flight
                         uint32_t v0[32], v1[32];
                         fm_tmem_ld32(dbase + g * 64, v0);
                         fm_tmem_ld32(dbase + g * 64 + 32, v1);
@@ -438,7 +478,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                     const uint32_t sbase = tmem + lane_base + (uint32_t)(3 * BN) + col0;
                     const uint32_t rbase = tmem + lane_base + (uint32_t)(2 * BN) + col0;
 #pragma unroll 1
-                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                    for (int cc = 0; cc < n32; ++cc) {
                         uint32_t v[32], sv[32];
                         fm_tmem_ld32(dbase + cc * 32, v);
                         if (!s_fresh) fm_tmem_ld32(sbase + cc * 32, sv);
@@ -489,7 +529,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                     const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
                     const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
 #pragma unroll 1
-                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                    for (int cc = 0; cc < n32; ++cc) {
                         uint32_t xv[32], yv[32];
                         fm_tmem_ld32(xb + cc * 32, xv);
                         fm_tmem_ld32(yb + cc * 32, yv);
@@ -510,16 +550,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_kernel(const LimbGe
                 rsrc = (uint32_t)(2 * BN);
             }
 #pragma unroll 1
-            for (int cc = 0; cc < kCols / 32; ++cc) {
+            for (int cc = 0; cc < n32; ++cc) {
                 uint32_t sres[32];
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < args.M) {
+                if (gi < cl.M) {
                     if (KIND == kE4M3Gf2)
-                        write_gf2_run(args, gi, (int64_t)nb * BN + col, sres);
+                        write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
                     else
-                        write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                        write_c_run<32>(cl, p, gi, (int64_t)nb * BN + col, (1ull << cl.c_lt) - 1, sres);
                 }
             }
             if (FOLD) {
@@ -558,7 +598,7 @@ constexpr uint32_t kPairStageBytes = 2 * kATileBytes;  // A half + B half, 16 KB
 constexpr size_t kPairSmem = (size_t)kPairStages * kPairStageBytes + 1024;
 
 template <int KIND>
-__global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const LimbGemmArgs args)
+__global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const __grid_constant__ LimbGemmArgs args)
 {
     constexpr int BN = 256;
     constexpr int S = kPairStages;
@@ -578,13 +618,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
     const uint32_t rank = fm_cluster_ctarank();
     const bool leader = rank == 0;
     const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-    const int MB2 = args.MB >> 1;  // A planes are padded to an even number of row blocks
-    const int n_tiles = MB2 * args.NB;
-    const int njobs = args.first[args.n_products];
+    const LimbCall& cl = args.call;
+    const int MB2 = cl.MB >> 1;  // A planes are padded to an even number of row blocks
+    const int n_tiles = MB2 * cl.NB;
+    const int njobs = cl.njobs;
 
     auto coords = [&](int tile, int& mb2, int& nb) {
         const int GROUP = 4;
-        const int per_group = GROUP * args.NB;
+        const int per_group = GROUP * cl.NB;
         const int first = (tile / per_group) * GROUP;
         const int gsz = min(MB2 - first, GROUP);
         const int inner = tile % per_group;
@@ -627,13 +668,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                 coords(tile, mb2, nb);
                 int idx = 0;
                 for (int t = 0; t < njobs && ok; ++t) {
-                    while (t >= args.first[idx + 1]) ++idx;
-                    const int c = t - args.first[idx];
-                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
-                    const uint8_t* a_src = args.Ap + (size_t)args.pa[idx] * args.a_plane_bytes +
-                                           ((size_t)(2 * mb2 + rank) * args.KB) * kATileBytes;
-                    const uint8_t* b_src = args.Bp + (size_t)args.pb[idx] * args.b_plane_bytes +
-                                           ((size_t)nb * args.KB) * (2 * kATileBytes) +
+                    while (t >= cl.first[idx + 1]) ++idx;
+                    const int c = t - cl.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(cl.KB, kb0 + args.cs[idx]);
+                    const uint8_t* a_src = cl.Ap + (size_t)args.pa[idx] * cl.a_plane_bytes +
+                                           ((size_t)(2 * mb2 + rank) * cl.KB) * kATileBytes;
+                    const uint8_t* b_src = cl.Bp + (size_t)args.pb[idx] * cl.b_plane_bytes +
+                                           ((size_t)nb * cl.KB) * (2 * kATileBytes) +
                                            (size_t)rank * kATileBytes;
                     for (int kb = kb0; kb < kb1; ++kb, ++g) {
                         const int s = g % S;
@@ -662,9 +703,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                 int idx = 0;
                 for (int t = 0; t < njobs && ok; ++t, ++T) {
                     const int b = T & 1;
-                    while (t >= args.first[idx + 1]) ++idx;
-                    const int c = t - args.first[idx];
-                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    while (t >= cl.first[idx + 1]) ++idx;
+                    const int c = t - cl.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(cl.KB, kb0 + args.cs[idx]);
                     if (T >= 2 &&
                         !fm_mbar_wait(&acce_bar[b], ((T >> 1) - 1) & 1, args.status, &s_abort)) {
                         ok = false;
@@ -711,9 +752,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
             for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
                 int idx = 0;
                 for (int t = 0; t < njobs && ok; ++t) {
-                    while (t >= args.first[idx + 1]) ++idx;
-                    const int c = t - args.first[idx];
-                    const int kb0 = c * args.cs[idx], kb1 = min(args.KB, kb0 + args.cs[idx]);
+                    while (t >= cl.first[idx + 1]) ++idx;
+                    const int c = t - cl.first[idx];
+                    const int kb0 = c * args.cs[idx], kb1 = min(cl.KB, kb0 + args.cs[idx]);
                     for (int kb = kb0; kb < kb1; ++kb, ++g) {
                         const int s = g % S;
                         if (!fm_mbar_wait(&full_bar[s], (g / S) & 1, args.status, &s_abort)) {
@@ -735,7 +776,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const uint32_t col0 = (uint32_t)(half * kCols);
         const uint32_t p = args.p;
-        const uint64_t cmask = (1ull << args.c_lt) - 1;
+        const uint64_t cmask = (1ull << cl.c_lt) - 1;
         const uint32_t acce_leader = fm_mapa(fm_smem_u32(&acce_bar[0]), 0);
         uint32_t T = 0;
         bool ok = true;
@@ -750,11 +791,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                     break;
                 }
                 fm_tc_fence_after();
-                while (t >= args.first[idx + 1]) ++idx;
+                while (t >= cl.first[idx + 1]) ++idx;
                 const bool last_on_buffer = (t + 2 >= njobs);
                 int idx2 = idx;
                 if (!last_on_buffer)
-                    while (t + 2 >= args.first[idx2 + 1]) ++idx2;
+                    while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
                 const bool same_next = !last_on_buffer && idx2 == idx;
                 const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
                 const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
@@ -811,11 +852,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const L
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + (uint32_t)(by * BN) + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < args.M) {
+                if (gi < cl.M) {
                     if (KIND == kE4M3Gf2)
-                        write_gf2_run(args, gi, (int64_t)nb * BN + col, sres);
+                        write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
                     else
-                        write_c_run<32>(args, gi, (int64_t)nb * BN + col, cmask, sres);
+                        write_c_run<32>(cl, p, gi, (int64_t)nb * BN + col, cmask, sres);
                 }
             }
             fm_tc_fence_before();
@@ -866,10 +907,10 @@ uint32_t invmod(uint32_t a, uint32_t m)
     return (uint32_t)(t % m);
 }
 
-template <int BN, bool FOLD, int KIND = kF16Res>
+template <int BN, bool FOLD, int KIND = kF16Res, bool BATCH = false>
 int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
 {
-    auto k = limb_gemm_kernel<BN, FOLD, KIND>;
+    auto k = limb_gemm_kernel<BN, FOLD, KIND, BATCH>;
     const size_t smem = GemmCfg<BN>::kSmem;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, kGemmThreads, smem, s>>>(a);
@@ -1035,35 +1076,22 @@ size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
     return (size_t)q.n_planes * (q.a_plane_bytes + q.b_plane_bytes);
 }
 
-int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const void* b_planes,
-                     uint32_t p, int op, int* status, cudaStream_t s)
+namespace {
+
+// Fields shared by every call of a launch: the limb products and the modulus.
+void fill_common(const FmLimbPlan& q, uint32_t p, int* status, LimbGemmArgs& a)
 {
-    if (q.M == 0 || q.N == 0 || q.K == 0) return FM_OK;
-    LimbGemmArgs a;
-    a.Ap = static_cast<const uint8_t*>(a_planes);
-    a.Bp = static_cast<const uint8_t*>(b_planes);
-    a.a_plane_bytes = q.a_plane_bytes;
-    a.b_plane_bytes = q.b_plane_bytes;
-    a.MB = q.MB;
-    a.NB = q.NB;
-    a.KB = q.KB;
+    std::memset(&a, 0, sizeof(a));
     a.n_products = q.n_products;
     a.p = p;
     a.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
     a.mu64 = ~0ull / p;
-    for (int k = 0; k < 16; ++k) {
-        a.pa[k] = a.pb[k] = a.cs[k] = 0;
-        a.wt[k] = a.cn[k] = 0;
-    }
-    a.first[0] = 0;
     for (int k = 0; k < q.n_products; ++k) {
         a.pa[k] = q.prod_a[k];
         a.pb[k] = q.prod_b[k];
         a.cs[k] = q.prod_cs[k];
         a.wt[k] = q.prod_w[k];
-        a.first[k + 1] = a.first[k] + (q.KB + q.prod_cs[k] - 1) / q.prod_cs[k];
     }
-    for (int k = q.n_products + 1; k <= 16; ++k) a.first[k] = a.first[q.n_products];
     if (q.fold) {
         for (int k = 0; k < q.n_products; ++k)
             for (int k2 = 0; k2 < q.n_products; ++k2) {
@@ -1074,14 +1102,46 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.invp = 1.0f / (float)p;
     a.pf = (float)p;
     a.offs64 = ((((uint64_t)1 << 31) + p - 1) / p) * (uint64_t)p;
-    a.C = C.m.base;
-    a.c_lt = C.m.log2_T;
-    a.op = op;
-    a.c_row0 = C.row0;
-    a.c_col0 = C.col0;
-    a.M = q.M;
-    a.N = q.N;
     a.status = status;
+}
+
+// One call: its planes, tile counts, jobs (chunks of every product) and C.
+void fill_call(const FmLimbPlan& q, int MB, int NB, int KB, uint64_t a_plane_bytes,
+               uint64_t b_plane_bytes, fm_sub C, const void* a_planes, const void* b_planes, int op,
+               LimbCall& c)
+{
+    std::memset(&c, 0, sizeof(c));
+    c.Ap = static_cast<const uint8_t*>(a_planes);
+    c.Bp = static_cast<const uint8_t*>(b_planes);
+    c.a_plane_bytes = a_plane_bytes;
+    c.b_plane_bytes = b_plane_bytes;
+    c.MB = MB;
+    c.NB = NB;
+    c.KB = KB;
+    c.first[0] = 0;
+    for (int k = 0; k < q.n_products; ++k) c.first[k + 1] = c.first[k] + (KB + q.prod_cs[k] - 1) / q.prod_cs[k];
+    for (int k = q.n_products + 1; k <= 16; ++k) c.first[k] = c.first[q.n_products];
+    c.njobs = c.first[q.n_products];
+    c.C = C.m.base;
+    c.c_lt = C.m.log2_T;
+    c.op = op;
+    c.c_row0 = C.row0;
+    c.c_col0 = C.col0;
+    c.M = C.rows;
+    c.N = C.cols;
+}
+
+}  // namespace
+
+int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const void* b_planes,
+                     uint32_t p, int op, int* status, cudaStream_t s)
+{
+    if (q.M == 0 || q.N == 0 || q.K == 0) return FM_OK;
+    LimbGemmArgs a;
+    fill_common(q, p, status, a);
+    fill_call(q, q.MB, q.NB, q.KB, q.a_plane_bytes, q.b_plane_bytes, C, a_planes, b_planes, op, a.call);
+    a.call.M = q.M;
+    a.call.N = q.N;
     if (q.gf2) {
         if (q.pair) return launch_gemm_pair<kE4M3Gf2>(a, q.MB / 2 * q.NB, s);
         return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
@@ -1104,6 +1164,259 @@ int fm_limb_run(const FmLimbPlan& q, fm_sub C, fm_sub A, fm_sub B, uint32_t p, i
     FM_TRY(fm_limb_split_run(q, A, FM_LIMB_A, p, Ap, s));
     FM_TRY(fm_limb_split_run(q, B, FM_LIMB_B, p, Bp, s));
     return fm_limb_gemm_run(q, C, Ap, Bp, p, op, status, s);
+}
+
+// ---- batched limb form ------------------------------------------------------
+// Every call of a batch gets its own limb planes in one workspace. Three
+// launches run the whole batch: the A splits of every call, the B splits of
+// every call, and one persistent GEMM over the output tiles of every call
+// (longest first; each CTA walks tiles blockIdx.x, + gridDim.x, ...).
+struct FmLimbBatch {
+    FmLimbPlan q;  // limb parameters shared by every call (products, chunks, BN)
+    uint32_t p = 0;
+    void* ws = nullptr;
+    FmSplitDesc* d_adesc = nullptr;
+    FmSplitDesc* d_bdesc = nullptr;
+    int2* d_ajobs = nullptr;
+    int2* d_bjobs = nullptr;
+    int64_t n_ajobs = 0, n_bjobs = 0;
+    LimbCall* d_calls = nullptr;
+    int4* d_tiles = nullptr;
+    int n_tiles = 0;
+    bool gf2 = false;                      // bit-packed GF(2) operands
+    std::vector<fm_gemm_call> zero_calls;  // K = 0: only FM_OP_SET changes C
+    std::vector<fm_gf2_sub> zero_subs;     // GF(2), K = 0 under FM_OP_SET
+};
+
+namespace {
+template <typename T>
+int upload_vec(const std::vector<T>& v, T** out)
+{
+    *out = nullptr;
+    if (v.empty()) return FM_OK;
+    if (cudaMalloc(reinterpret_cast<void**>(out), v.size() * sizeof(T)) != cudaSuccess) return FM_ENOMEM;
+    if (cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FM_ECUDA;
+    return FM_OK;
+}
+}  // namespace
+
+void fm_limb_batch_destroy(FmLimbBatch* b)
+{
+    if (!b) return;
+    cudaFree(b->ws);
+    cudaFree(b->d_adesc);
+    cudaFree(b->d_bdesc);
+    cudaFree(b->d_ajobs);
+    cudaFree(b->d_bjobs);
+    cudaFree(b->d_calls);
+    cudaFree(b->d_tiles);
+    delete b;
+}
+
+namespace {
+
+// One call of a batch before its planes are placed: shapes, the two operands
+// (src, lt, row0, col0, rows, cols of its FmSplitDesc) and C.
+struct BatchCall {
+    int64_t M, N, K;
+    FmSplitDesc a, b;
+    fm_sub C;
+    int op;
+};
+
+// Places every call's planes in one workspace (K tiles of kt elements, output
+// tiles of 128 x bn) and uploads the split jobs, the call table and the tile
+// list (longest first).
+int build_batch(const std::vector<BatchCall>& in, int bn, int kt, FmLimbBatch* b)
+{
+    const FmLimbPlan& q = b->q;
+    const uint64_t b_tile = (uint64_t)bn * 128;
+    std::vector<uint64_t> a_off(in.size()), b_off(in.size());
+    uint64_t total = 0;
+    for (size_t c = 0; c < in.size(); ++c) {
+        const int MB = (int)((in[c].M + kBM - 1) / kBM), NB = (int)((in[c].N + bn - 1) / bn);
+        const int KB = (int)((in[c].K + kt - 1) / kt);
+        a_off[c] = total;
+        total += ((q.n_planes * (uint64_t)MB * KB * kATileBytes + 1023) / 1024) * 1024;
+        b_off[c] = total;
+        total += ((q.n_planes * (uint64_t)NB * KB * b_tile + 1023) / 1024) * 1024;
+    }
+    if (total > 0 && cudaMalloc(&b->ws, total) != cudaSuccess) return FM_ENOMEM;
+    uint8_t* ws = static_cast<uint8_t*>(b->ws);
+    std::vector<FmSplitDesc> ad, bd;
+    std::vector<int2> aj, bj;
+    std::vector<LimbCall> lc;
+    std::vector<int4> tiles;
+    std::vector<int64_t> cost;
+    for (size_t c = 0; c < in.size(); ++c) {
+        const BatchCall& g = in[c];
+        const int MB = (int)((g.M + kBM - 1) / kBM), NB = (int)((g.N + bn - 1) / bn);
+        const int KB = (int)((g.K + kt - 1) / kt);
+        const uint64_t ab = (uint64_t)MB * KB * kATileBytes, bb = (uint64_t)NB * KB * b_tile;
+        const int di = (int)ad.size();
+        FmSplitDesc da = g.a, db = g.b;
+        da.KB = db.KB = KB;
+        da.out = ws + a_off[c];
+        db.out = ws + b_off[c];
+        da.plane_bytes = (size_t)ab;
+        db.plane_bytes = (size_t)bb;
+        ad.push_back(da);
+        bd.push_back(db);
+        for (int t = 0; t < MB * KB; ++t) aj.push_back(make_int2(di, t));
+        for (int t = 0; t < NB * KB; ++t) bj.push_back(make_int2(di, t));
+        LimbCall call;
+        fill_call(q, MB, NB, KB, ab, bb, g.C, ws + a_off[c], ws + b_off[c], g.op, call);
+        const int ci = (int)lc.size();
+        lc.push_back(call);
+        for (int mb = 0; mb < MB; ++mb)
+            for (int nb = 0; nb < NB; ++nb) {
+                tiles.push_back(make_int4(ci, mb, nb, 0));
+                const int64_t rows = std::min<int64_t>(kBM, g.M - (int64_t)mb * kBM);
+                const int64_t cols = std::min<int64_t>(bn, g.N - (int64_t)nb * bn);
+                cost.push_back((int64_t)call.njobs * 4096 + (int64_t)KB * 64 + (rows * cols >> 10));
+            }
+    }
+    // longest tiles first, so that the static walk of the persistent grid balances
+    std::vector<size_t> order(tiles.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<int4> sorted(tiles.size());
+    for (size_t t = 0; t < order.size(); ++t) sorted[t] = tiles[order[t]];
+    if (sorted.size() > 0x7fffffff || aj.size() > 0x7fffffff || bj.size() > 0x7fffffff) return FM_EINVAL;
+    FM_TRY(upload_vec(ad, &b->d_adesc));
+    FM_TRY(upload_vec(bd, &b->d_bdesc));
+    FM_TRY(upload_vec(aj, &b->d_ajobs));
+    FM_TRY(upload_vec(bj, &b->d_bjobs));
+    FM_TRY(upload_vec(lc, &b->d_calls));
+    FM_TRY(upload_vec(sorted, &b->d_tiles));
+    b->n_ajobs = (int64_t)aj.size();
+    b->n_bjobs = (int64_t)bj.size();
+    b->n_tiles = (int)sorted.size();
+    return FM_OK;
+}
+
+}  // namespace
+
+int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const fm_opts* opts,
+                         FmLimbBatch** out)
+{
+    *out = nullptr;
+    if (opts && opts->cta_pair) return FM_EUNSUPPORTED;
+    // batches of small products waste less on 128-wide output tiles
+    fm_opts o = opts ? *opts : fm_opts{};
+    if (o.block_n == 0) o.block_n = 128;
+    FmLimbPlan q;
+    FM_TRY(fm_limb_plan(1, 1, 1, p, &o, &q));
+    FmLimbBatch* b = new FmLimbBatch();
+    b->q = q;
+    b->p = p;
+    std::vector<BatchCall> in;
+    for (int64_t c = 0; c < n; ++c) {
+        const fm_gemm_call& g = calls[c];
+        if (g.C.rows == 0 || g.C.cols == 0) continue;
+        if (g.A.cols == 0) {
+            b->zero_calls.push_back(g);
+            continue;
+        }
+        BatchCall bc;
+        bc.M = g.C.rows;
+        bc.N = g.C.cols;
+        bc.K = g.A.cols;
+        bc.a = FmSplitDesc{g.A.m.base, g.A.m.log2_T, 0, g.A.row0, g.A.col0, bc.M, bc.K, nullptr, 0};
+        bc.b = FmSplitDesc{g.B.m.base, g.B.m.log2_T, 0, g.B.row0, g.B.col0, bc.K, bc.N, nullptr, 0};
+        bc.C = g.C;
+        bc.op = g.op;
+        in.push_back(bc);
+    }
+    const int rc = build_batch(in, q.block_n, kBK, b);
+    if (rc != FM_OK) {
+        fm_limb_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FM_OK;
+}
+
+int fm_gf2_batch_create(const fm_gf2_call* calls, int64_t n, const fm_opts* opts, FmLimbBatch** out)
+{
+    *out = nullptr;
+    if (opts && opts->cta_pair) return FM_EUNSUPPORTED;
+    FmLimbPlan q;
+    FM_TRY(fm_gf2_plan(1, 1, 1, false, &q));
+    q.prod_cs[0] = (int)((((int64_t)1 << 24) - 2) / 128);  // one accumulation for any K < 2^24
+    FmLimbBatch* b = new FmLimbBatch();
+    b->q = q;
+    b->p = 2;
+    b->gf2 = true;
+    std::vector<BatchCall> in;
+    for (int64_t c = 0; c < n; ++c) {
+        const fm_gf2_call& g = calls[c];
+        if (g.C.rows == 0 || g.C.cols == 0) continue;
+        if (g.A.cols == 0) {
+            if (g.op == FM_OP_SET) b->zero_subs.push_back(g.C);
+            continue;
+        }
+        BatchCall bc;
+        bc.M = g.C.rows;
+        bc.N = g.C.cols;
+        bc.K = g.A.cols;
+        bc.a = FmSplitDesc{g.A.m.base, g.A.m.log2_grid, 0, g.A.row0, g.A.col0, bc.M, bc.K, nullptr, 0};
+        bc.b = FmSplitDesc{g.B.m.base, g.B.m.log2_grid, 0, g.B.row0, g.B.col0, bc.K, bc.N, nullptr, 0};
+        fm_sub cs;
+        cs.m.base = g.C.m.base;
+        cs.m.log2_grid = g.C.m.log2_grid;
+        cs.m.log2_T = 5;
+        cs.row0 = g.C.row0;
+        cs.col0 = g.C.col0;
+        cs.rows = g.C.rows;
+        cs.cols = g.C.cols;
+        bc.C = cs;
+        bc.op = g.op;
+        in.push_back(bc);
+    }
+    const int rc = build_batch(in, 256, 128, b);
+    if (rc != FM_OK) {
+        fm_limb_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FM_OK;
+}
+
+int64_t fm_limb_batch_tiles(const FmLimbBatch* b)
+{
+    return b ? b->n_tiles : 0;
+}
+
+const std::vector<fm_gemm_call>& fm_limb_batch_zero_calls(const FmLimbBatch* b)
+{
+    return b->zero_calls;
+}
+
+int fm_limb_batch_run(FmLimbBatch* b, int* status, cudaStream_t s)
+{
+    for (const fm_gf2_sub& z : b->zero_subs) FM_TRY(fm_gf2_zero_sub(z, s));
+    if (b->n_tiles == 0) return FM_OK;
+    if (b->gf2) {
+        FM_TRY(fm_gf2_split_batch_run(FM_LIMB_A, b->d_adesc, b->d_ajobs, b->n_ajobs, s));
+        FM_TRY(fm_gf2_split_batch_run(FM_LIMB_B, b->d_bdesc, b->d_bjobs, b->n_bjobs, s));
+    } else {
+        FM_TRY(fm_limb_split_batch_run(b->q, FM_LIMB_A, b->d_adesc, b->d_ajobs, b->n_ajobs, b->p, s));
+        FM_TRY(fm_limb_split_batch_run(b->q, FM_LIMB_B, b->d_bdesc, b->d_bjobs, b->n_bjobs, b->p, s));
+    }
+    LimbGemmArgs a;
+    fill_common(b->q, b->p, status, a);
+    a.calls = b->d_calls;
+    a.tiles = b->d_tiles;
+    a.n_tiles = b->n_tiles;
+    const int grid = std::min(b->n_tiles, fm_sm_count());
+    if (b->gf2) return launch_gemm<256, true, kE4M3Gf2, true>(a, grid, s);
+    if (b->q.fold) {
+        if (b->q.block_n == 256) return launch_gemm<256, true, kF16Res, true>(a, grid, s);
+        return launch_gemm<128, true, kF16Res, true>(a, grid, s);
+    }
+    return launch_gemm<128, false, kF16Res, true>(a, grid, s);
 }
 
 // ---- C entry points of the step-by-step limb form --------------------------

@@ -90,12 +90,12 @@ __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, 
 }
 
 // A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
-__global__ void __launch_bounds__(kSplitThreads)
-    split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
-                   int64_t K, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
+// One CTA writes tile (mb, kb) of every plane.
+__device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int lt, int64_t row0,
+                                             int64_t col0, int64_t M, int64_t K, int KB, int tile, int w,
+                                             int n_planes, uint32_t p, int32_t hi,
+                                             uint8_t* __restrict__ planes, size_t plane_bytes)
 {
-    const int tile = blockIdx.x;
     const int mb = tile / KB, kb = tile % KB;
     uint8_t* out = planes + (size_t)tile * kATileBytes;
     constexpr int kIters = kBM * 8 / kSplitThreads;  // 16-byte chunks per thread
@@ -136,18 +136,17 @@ __global__ void __launch_bounds__(kSplitThreads)
 // B (K x N) -> w planes of [NB][KB] tiles, each BN rows (n) x 64 k f16 (B
 // transposed to K-major), swizzled. Staged through shared memory so that both
 // the Morton reads (along n, 16-byte vectors) and the tile writes (along k)
-// are coalesced.
+// are coalesced. One CTA writes tile (nb, kb) of every plane.
 template <int BN>
-__global__ void __launch_bounds__(kSplitThreads)
-    split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
-                   int64_t N, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
+__device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int lt, int64_t row0,
+                                             int64_t col0, int64_t K, int64_t N, int KB, int tile, int w,
+                                             int n_planes, uint32_t p, int32_t hi,
+                                             uint8_t* __restrict__ planes, size_t plane_bytes,
+                                             uint32_t* sb)
 {
-    // [kBK][BN] staging; column n of row kk lives at n ^ ((kk / 8) * 4), which
-    // keeps 4-aligned runs contiguous and makes the column reads below hit 32
-    // distinct banks
-    extern __shared__ __align__(16) uint32_t sb[];
-    const int tile = blockIdx.x;
+    // sb: [kBK][BN] staging; column n of row kk lives at n ^ ((kk / 8) * 4),
+    // which keeps 4-aligned runs contiguous and makes the column reads below
+    // hit 32 distinct banks
     const int nb = tile / KB, kb = tile % KB;
     const uint64_t mask = (1ull << lt) - 1;
     constexpr int kIters = kBK * BN / 4 / kSplitThreads;  // 16-byte loads per thread
@@ -210,6 +209,48 @@ __global__ void __launch_bounds__(kSplitThreads)
     }
 }
 
+__global__ void __launch_bounds__(kSplitThreads)
+    split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
+                   int64_t K, int KB, int w, int n_planes, uint32_t p, int32_t hi,
+                   uint8_t* __restrict__ planes, size_t plane_bytes)
+{
+    split_a_tile(A, lt, row0, col0, M, K, KB, blockIdx.x, w, n_planes, p, hi, planes, plane_bytes);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
+                   int64_t N, int KB, int w, int n_planes, uint32_t p, int32_t hi,
+                   uint8_t* __restrict__ planes, size_t plane_bytes)
+{
+    extern __shared__ __align__(16) uint32_t sb[];
+    split_b_tile<BN>(B, lt, row0, col0, K, N, KB, blockIdx.x, w, n_planes, p, hi, planes, plane_bytes, sb);
+}
+
+// Batched: CTA b splits tile jobs[b].y of operand jobs[b].x (one launch for the
+// A (or B) operands of every call of a plan).
+__global__ void __launch_bounds__(kSplitThreads)
+    split_a_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, int w,
+                         int n_planes, uint32_t p, int32_t hi)
+{
+    const int2 j = jobs[blockIdx.x];
+    const FmSplitDesc d = descs[j.x];
+    split_a_tile(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, w, n_planes, p, hi, d.out,
+                 d.plane_bytes);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_b_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, int w,
+                         int n_planes, uint32_t p, int32_t hi)
+{
+    extern __shared__ __align__(16) uint32_t sb[];
+    const int2 j = jobs[blockIdx.x];
+    const FmSplitDesc d = descs[j.x];
+    split_b_tile<BN>(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, w, n_planes, p, hi, d.out,
+                     d.plane_bytes, sb);
+}
+
 }  // namespace
 
 namespace {
@@ -239,6 +280,24 @@ int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void*
         k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N,
                                                       q.KB, q.w, q.n_planes, p, hi, out,
                                                       q.b_plane_bytes);
+    }
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+int fm_limb_split_batch_run(const FmLimbPlan& q, int role, const FmSplitDesc* d_descs,
+                            const int2* d_jobs, int64_t n_jobs, uint32_t p, cudaStream_t s)
+{
+    if (n_jobs == 0) return FM_OK;
+    if (n_jobs > 0x7fffffff) return FM_EINVAL;
+    const int32_t hi = limb_hi(q.w);
+    if (role == FM_LIMB_A) {
+        split_a_batch_kernel<<<(unsigned)n_jobs, kSplitThreads, 0, s>>>(d_descs, d_jobs, q.w, q.n_planes, p, hi);
+    } else {
+        const size_t sb_smem = (size_t)kBK * q.block_n * 4;
+        auto k = q.block_n == 256 ? split_b_batch_kernel<256> : split_b_batch_kernel<128>;
+        FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
+        k<<<(unsigned)n_jobs, kSplitThreads, sb_smem, s>>>(d_descs, d_jobs, q.w, q.n_planes, p, hi);
     }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;

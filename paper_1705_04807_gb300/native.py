@@ -31,6 +31,7 @@ EXPORTS = (
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
     "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
     "fm_pluq", "fm_gf2_pack", "fm_gf2_unpack", "fm_gf2_gemm", "fm_gf2_workspace_size",
+    "fm_gf2_plan_create",
 )
 
 
@@ -77,6 +78,11 @@ FM_TUNE_NO_LIMB, FM_TUNE_NO_PLAIN = 1, 2
 
 class fm_gemm_call(ctypes.Structure):
     _fields_ = [("C", fm_sub), ("A", fm_sub), ("B", fm_sub), ("op", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class fm_gf2_call(ctypes.Structure):
+    _fields_ = [("C", fm_gf2_sub), ("A", fm_gf2_sub), ("B", fm_gf2_sub), ("op", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -127,6 +133,8 @@ def lib():
         "fm_gf2_gemm": ([fm_gf2_sub, fm_gf2_sub, fm_gf2_sub, I32, ctypes.POINTER(fm_opts), P],
                         ctypes.c_int),
         "fm_gf2_workspace_size": ([I64, I64, I64], I64),
+        "fm_gf2_plan_create": ([ctypes.POINTER(P), ctypes.POINTER(fm_gf2_call), I64,
+                                ctypes.POINTER(fm_opts)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -248,12 +256,17 @@ def fm_gemm_modp_workspace_size(C: fm_sub, A: fm_sub, B: fm_sub, p: int,
 class Plan:
     """Owns an fm_plan (fm_plan_create / fm_plan_destroy)."""
 
-    def __init__(self, calls, p: int, algo: int = FM_ALGO_AUTO, options: fm_opts | None = None):
-        arr = (fm_gemm_call * len(calls))(*calls)
+    def __init__(self, calls, p: int, algo: int = FM_ALGO_AUTO, options: fm_opts | None = None,
+                 gf2: bool = False):
         h = ctypes.c_void_p()
         o = ctypes.byref(options) if options is not None else None
-        _check(lib().fm_plan_create(ctypes.byref(h), arr, len(calls), int(p), int(algo), o),
-               "fm_plan_create")
+        if gf2:
+            arr = (fm_gf2_call * len(calls))(*calls)
+            _check(lib().fm_gf2_plan_create(ctypes.byref(h), arr, len(calls), o), "fm_gf2_plan_create")
+        else:
+            arr = (fm_gemm_call * len(calls))(*calls)
+            _check(lib().fm_plan_create(ctypes.byref(h), arr, len(calls), int(p), int(algo), o),
+                   "fm_plan_create")
         self.handle = h
 
     def run(self, stream=None):
@@ -277,6 +290,11 @@ class Plan:
 
 def fm_plan_create(calls, p: int, algo: int = FM_ALGO_AUTO, options=None) -> Plan:
     return Plan(calls, p, algo, options)
+
+
+def fm_gf2_plan_create(calls, options=None) -> Plan:
+    """A plan for a batch of GF(2) calls (fm_gf2_call); run it with fm_gemm_modp_batched."""
+    return Plan(calls, 2, options=options, gf2=True)
 
 
 def fm_gemm_modp_batched(plan: Plan, stream=None):

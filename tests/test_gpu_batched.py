@@ -50,12 +50,12 @@ def make_batch(fm, dev, count, seed, lt=6, lo=32, hi=512, block=512, big=4096):
     return MC, MA, MB, Cf, Af, Bf, calls, meta
 
 
-def expected(orc, Cf, Af, Bf, meta, times=1):
+def expected(orc, Cf, Af, Bf, meta, times=1, p=P16):
     want = Cf.copy()
     for (M, N, K, cr, cc, ar, ac, br, bc, op) in meta:
         blk = want[cr:cr + M, cc:cc + N]
         for _ in range(times):
-            blk = orc.gemm_modp(blk, Af[ar:ar + M, ac:ac + K], Bf[br:br + K, bc:bc + N], P16, op)
+            blk = orc.gemm_modp(blk, Af[ar:ar + M, ac:ac + K], Bf[br:br + K, bc:bc + N], p, op)
         want[cr:cr + M, cc:cc + N] = blk
     return want
 
@@ -109,3 +109,86 @@ def test_empty_plan_and_errors(env):
     call.C, call.A, call.B = M.sub(0, 0, 8, 8), M.sub(8, 8, 8, 8), M.sub(4, 4, 8, 8)  # overlap
     with pytest.raises(fm.FmError):
         fm.fm_plan_create([call], P16)
+
+
+P31 = 2147483647
+
+
+@pytest.mark.parametrize("p,opt", [(P16, {}), (P16, {"block_n": 128}), (P16, {"no_karatsuba": 1}),
+                                   (P31, {}), (257, {})])
+@pytest.mark.parametrize("lt", [6, 7])
+def test_limb_batched_matches_oracle_and_per_call(env, orc, p, opt, lt):
+    # the tensor-core form for a whole batch (2 split launches + 1 GEMM launch)
+    # against the oracle and against one fm_gemm_modp call per product (inputs
+    # reduced mod p when p < 65521)
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 40, seed=lt + p % 7, lt=lt)
+    if p < P16:  # inputs must be residues mod p
+        Cf, Af, Bf = Cf % p, Af % p, Bf % p
+        MC.load(Cf)
+        MA.load(Af)
+        MB.load(Bf)
+    o = fm.opts(**opt)
+    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC, o)
+    assert plan.work_items > 0
+    saved = MC.t.clone()
+    plan.run()
+    got = MC.read()
+    assert fm.fm_get_last_device_status() == 0
+    assert np.array_equal(got, expected(orc, Cf, Af, Bf, meta, p=p))
+    MC.t.copy_(saved)
+    for call in calls:
+        fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_LIMB_TC, o)
+    assert np.array_equal(MC.read(), got)
+    plan.close()
+
+
+def test_limb_batched_with_empty_and_k0_calls(env, orc):
+    # calls with K = 0 (SET zeroes C, ADD/SUB leave it) and with M or N = 0
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 12, seed=3, lt=6)
+    extra_meta = []
+    for c, (M, N, K, op) in enumerate([(40, 50, 0, 0), (30, 20, 0, 1), (0, 10, 5, 0), (10, 0, 5, 2)]):
+        call = fm.fm_gemm_call()
+        r0 = 3800 + 60 * c  # a free corner of C (make_batch uses cells < 12 of the 8 x 8 grid)
+        call.C, call.A, call.B = MC.sub(r0, 3900, M, N), MA.sub(7, 9, M, K), MB.sub(11, 13, K, N)
+        call.op = op
+        calls.append(call)
+        extra_meta.append((M, N, K, r0, 3900, 7, 9, 11, 13, op))
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC)
+    plan.run()
+    want = expected(orc, Cf, Af, Bf, meta + extra_meta)
+    assert np.array_equal(MC.read(), want)
+    plan.close()
+
+
+def test_limb_batched_graph_capture_and_replay(env, orc):
+    import torch
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 24, seed=11, lt=7)
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC)
+    fm.fm_get_last_device_status()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    torch.cuda.synchronize()
+    assert np.array_equal(MC.read(), Cf)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(MC.read(), expected(orc, Cf, Af, Bf, meta, times=2))
+    plan.close()
+
+
+def test_limb_batched_rejects_pairs_and_overlap(env):
+    fm, dev = env
+    M = MortonMatrix(fm, dev, 1, 6)
+    N = MortonMatrix(fm, dev, 1, 6)
+    call = fm.fm_gemm_call()
+    call.C, call.A, call.B = M.sub(0, 0, 8, 8), N.sub(8, 8, 8, 8), N.sub(4, 4, 8, 8)
+    with pytest.raises(fm.FmError):
+        fm.fm_plan_create([call], P16, fm.FM_ALGO_LIMB_TC, fm.opts(cta_pair=1))
+    call.A = M.sub(4, 4, 8, 8)  # overlaps C
+    with pytest.raises(fm.FmError):
+        fm.fm_plan_create([call], P16, fm.FM_ALGO_LIMB_TC)

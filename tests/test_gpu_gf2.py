@@ -199,3 +199,97 @@ def test_gf2_8192(env, orc):
         got = orc.gf2_unpack(GC.words(), lg, n, n)
         assert np.array_equal(got[ij[:, 0], ij[:, 1]], want), pair
         assert orc.freivalds(got, C, A, B, 2, 1, trials=24, seed=3 + pair), pair
+
+
+def _gf2_call(fm, C, A, B, op):
+    call = fm.fm_gf2_call()
+    call.C, call.A, call.B = C, A, B
+    call.op = op
+    return call
+
+
+def test_gf2_plan_matches_per_call_and_oracle(env, orc):
+    # a batch of random sub-matrix products (the experiments' workload) as one
+    # plan; C regions of different calls are disjoint rows but share words
+    fm, dev = env
+    lg, n = 5, 1024
+    Cf = fm_inputs.uniform_residues(41, (n, n), 2, 1)
+    Af = fm_inputs.uniform_residues(41, (n, n), 2, 2)
+    Bf = fm_inputs.uniform_residues(41, (n, n), 2, 3)
+    GA = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Af, lg))
+    GB = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Bf, lg))
+    GC = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Cf, lg))
+    rects = fm_inputs.sub_rectangles(77, 30, 300)
+    calls, meta = [], []
+    for t, r in enumerate(rects):
+        M, N, K, _, cC, rA, cA, rB, cB = (int(x) for x in r)
+        M = min(M, 30)           # 30 bands of 30 rows: disjoint C regions
+        rC = 32 * t + 1          # ... starting at odd rows, columns anywhere
+        op = t % 3
+        calls.append(_gf2_call(fm, GC.sub(rC, cC, M, N), GA.sub(rA, cA, M, K), GB.sub(rB, cB, K, N), op))
+        meta.append((M, N, K, rC, cC, rA, cA, rB, cB, op))
+    calls.append(_gf2_call(fm, GC.sub(980, 3, 20, 50), GA.sub(0, 0, 20, 0), GB.sub(0, 0, 0, 50), 0))  # K = 0
+    meta.append((20, 50, 0, 980, 3, 0, 0, 0, 0, 0))
+    plan = fm.fm_gf2_plan_create(calls)
+    assert plan.work_items > 0
+    plan.run()
+    assert fm.fm_get_last_device_status() == 0
+    got = orc.gf2_unpack(GC.words(), lg, n, n)
+    want = Cf.copy()
+    for (M, N, K, rC, cC, rA, cA, rB, cB, op) in meta:
+        want[rC:rC + M, cC:cC + N] = orc.gemm_modp(want[rC:rC + M, cC:cC + N], Af[rA:rA + M, cA:cA + K],
+                                                   Bf[rB:rB + K, cB:cB + N], 2, op)
+    assert np.array_equal(got, want)
+    # one fm_gf2_gemm per call from the same start: the same bits
+    GC2 = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Cf, lg))
+    for c in calls:
+        C = c.C
+        fm.fm_gf2_gemm(GC2.sub(C.row0, C.col0, C.rows, C.cols), c.A, c.B, c.op)
+    assert np.array_equal(GC2.words(), GC.words())
+    plan.close()
+
+
+def test_gf2_plan_graph_replay(env, orc):
+    import torch
+    fm, dev = env
+    lg, n = 4, 512
+    Cf = fm_inputs.uniform_residues(43, (n, n), 2, 1)
+    Af = fm_inputs.uniform_residues(43, (n, n), 2, 2)
+    GA = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Af, lg))
+    GC = Gf2Matrix(fm, dev, lg, orc.gf2_pack(Cf, lg))
+    calls = [_gf2_call(fm, GC.sub(100 * t, 7 * t, 90, 200), GA.sub(3 * t, 5, 90, 300),
+                       GA.sub(11, 13 * t, 300, 200), 1) for t in range(5)]
+    plan = fm.fm_gf2_plan_create(calls)
+    fm.fm_get_last_device_status()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    torch.cuda.synchronize()
+    g.replay()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    want = Cf.copy()
+    for t in range(5):   # three additions of the same product: C + A B over GF(2)
+        blk = want[100 * t:100 * t + 90, 7 * t:7 * t + 200]
+        want[100 * t:100 * t + 90, 7 * t:7 * t + 200] = orc.gemm_modp(
+            blk, Af[3 * t:3 * t + 90, 5:305], Af[11:311, 13 * t:13 * t + 200], 2, 1)
+    assert np.array_equal(orc.gf2_unpack(GC.words(), lg, n, n), want)
+    plan.close()
+
+
+def test_gf2_plan_errors(env):
+    fm, dev = env
+    G = Gf2Matrix(fm, dev, 2)
+    H = Gf2Matrix(fm, dev, 2)
+    bad = _gf2_call(fm, G.sub(0, 0, 40, 40), G.sub(30, 30, 40, 10), H.sub(0, 0, 10, 40), 0)
+    with pytest.raises(fm.FmError):
+        fm.fm_gf2_plan_create([bad])
+    ok = _gf2_call(fm, G.sub(0, 0, 40, 40), H.sub(0, 0, 40, 10), H.sub(0, 0, 10, 40), 0)
+    with pytest.raises(fm.FmError):
+        fm.fm_gf2_plan_create([ok], fm.opts(cta_pair=1))
+    empty = fm.fm_gf2_plan_create([])
+    assert empty.work_items == 0
+    empty.run()
+    empty.close()
