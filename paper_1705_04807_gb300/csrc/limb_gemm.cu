@@ -53,10 +53,10 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t t, uint32_t p, uint64_t m
     return (uint32_t)r;
 }
 
-__device__ __forceinline__ uint32_t op_combine(uint32_t c, uint32_t s, uint32_t p, int op)
+__device__ __forceinline__ uint32_t op_combine(uint32_t c, uint32_t s, uint32_t p, uint32_t mu32, int op)
 {
     if (op == FM_OP_SET) return s;
-    const uint32_t cc = c % p;
+    const uint32_t cc = barrett32(c, p, mu32);  // C holds residues; any 32-bit value is reduced
     if (op == FM_OP_ADD) {
         const uint32_t r = cc + s;
         return r >= p ? r - p : r;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool t
 // C(gi, j0 .. j0+W-1) <- C op sres (mod p), in the Morton-hybrid layout. Loads
 // are issued before stores; a run inside one tile row moves as 16-byte vectors.
 template <int W>
-__device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, int64_t gi, int64_t j0,
+__device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, uint32_t mu32, int64_t gi, int64_t j0,
                                             uint64_t cmask, const uint32_t (&sres)[W])
 {
     const uint64_t ci = (uint64_t)(c.c_row0 + gi);
@@ -154,10 +154,10 @@ __device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, int64
 #pragma unroll
         for (int q = 0; q < W / 4; ++q) {
             uint4 o = c.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
-            o.x = op_combine(o.x, sres[4 * q + 0], p, c.op);
-            o.y = op_combine(o.y, sres[4 * q + 1], p, c.op);
-            o.z = op_combine(o.z, sres[4 * q + 2], p, c.op);
-            o.w = op_combine(o.w, sres[4 * q + 3], p, c.op);
+            o.x = op_combine(o.x, sres[4 * q + 0], p, mu32, c.op);
+            o.y = op_combine(o.y, sres[4 * q + 1], p, mu32, c.op);
+            o.z = op_combine(o.z, sres[4 * q + 2], p, mu32, c.op);
+            o.w = op_combine(o.w, sres[4 * q + 3], p, mu32, c.op);
             dst[q] = o;
         }
         return;
@@ -176,7 +176,7 @@ __device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, int64
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-            if (j0 + g + e < c.N) c.C[a[e]] = op_combine(old[e], sres[g + e], p, c.op);
+            if (j0 + g + e < c.N) c.C[a[e]] = op_combine(old[e], sres[g + e], p, mu32, c.op);
     }
 }
 
@@ -221,6 +221,25 @@ __device__ __forceinline__ void write_gf2_run(const LimbCall& c, int64_t gi, int
     if (b != 0) {
         const uint32_t m1 = vmask >> (32 - b);
         if (m1) gf2_apply(c.C + (fm_encode(ci, cj + (32 - b), 5) >> 5), m1, bits >> (32 - b), c.op);
+    }
+}
+
+// Prefetch into L2 the C entries of row gi, columns j0 .. j0+n-1 (n > 0): one
+// request per 128-byte line of each run that is contiguous in the
+// Morton-hybrid layout (a tile row).
+__device__ __forceinline__ void prefetch_c_row(const LimbCall& c, int64_t gi, int64_t j0, int64_t n)
+{
+    const int lt = c.c_lt;
+    const int64_t T = (int64_t)1 << lt;
+    const uint64_t ci = (uint64_t)(c.c_row0 + gi);
+    int64_t j = c.c_col0 + j0;
+    const int64_t end = j + n;
+    while (j < end) {
+        const int64_t run = min(end, (j | (T - 1)) + 1) - j;
+        const uint32_t* a = c.C + fm_encode(ci, (uint64_t)j, lt);
+        const uintptr_t lo = (uintptr_t)a & ~(uintptr_t)127, hi = (uintptr_t)(a + run);
+        for (uintptr_t q = lo; q < hi; q += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+        j += run;
     }
 }
 
@@ -432,6 +451,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // quarter lies below the last row): the rest is never written
             const int live_cols = quarter * 32 < tile_rows(cl, mb) ? tile_cols(cl, nb) - (int)col0 : 0;
             const int n32 = max(0, min(kCols / 32, (live_cols + 31) / 32));
+            // C of this tile is read at its end: start moving it into L2 now
+            if (KIND != kE4M3Gf2 && cl.op != FM_OP_SET && live_cols > 0 &&
+                (int64_t)mb * kBM + quarter * 32 + lane < cl.M)
+                prefetch_c_row(cl, (int64_t)mb * kBM + quarter * 32 + lane, (int64_t)nb * BN + col0,
+                               min(live_cols, kCols));
             int idx = 0;
             for (int t = 0; t < njobs; ++t, ++T) {
                 const int b = T & 1;
@@ -559,7 +583,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     if (KIND == kE4M3Gf2)
                         write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
                     else
-                        write_c_run<32>(cl, p, gi, (int64_t)nb * BN + col, (1ull << cl.c_lt) - 1, sres);
+                        write_c_run<32>(cl, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cl.c_lt) - 1,
+                                        sres);
                 }
             }
             if (FOLD) {
@@ -856,7 +881,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                     if (KIND == kE4M3Gf2)
                         write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
                     else
-                        write_c_run<32>(cl, p, gi, (int64_t)nb * BN + col, cmask, sres);
+                        write_c_run<32>(cl, p, args.mu32, gi, (int64_t)nb * BN + col, cmask, sres);
                 }
             }
             fm_tc_fence_before();
