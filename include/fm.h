@@ -373,6 +373,21 @@ typedef struct fm_gf2_call {
  * not supported: FM_EUNSUPPORTED). */
 int fm_gf2_plan_create(fm_plan** plan, const fm_gf2_call* calls, int64_t n, const fm_opts* opts);
 
+/* ---- failure detection (the paper has no counterpart) ---------------------
+ * Every device-side wait of the library is bounded: after 2 s it raises
+ * FM_ETIMEOUT in the device status word and the kernel winds down, leaving the
+ * context usable. This hook launches a kernel whose wait cannot complete so
+ * that tests can watch that happen: which = 0, an mbarrier phase that nothing
+ * completes; which = 1, a grid barrier that one CTA of the grid never reaches.
+ * Returns launch errors only; the outcome is read with
+ * fm_get_last_device_status. Nothing faults or hangs.
+ *
+ * Tracing: with the environment variable FM_TRACE set (to "1" for stderr, or
+ * to a file path), every fm_gemm_modp, fm_gemm_modp_batched, fm_gf2_gemm and
+ * fm_pluq call appends one line with its shapes and work (products, tiles,
+ * plane bytes). The public entry points are also NVTX ranges. */
+int fm_debug_expire_wait(int32_t which, fm_stream stream);
+
 /* ---- status ------------------------------------------------------------- */
 
 /* Synchronises stream, returns and clears the device status word that

@@ -1,6 +1,11 @@
 // api.cu -- C entry points of libfm: validation, algorithm dispatch, cached
 // workspace, device status word, and the batched plan.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <mutex>
@@ -212,9 +217,38 @@ int fm_sm_count()
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Tracing (FM_TRACE) and NVTX ranges.
+bool fm_trace_on()
+{
+    const char* v = std::getenv("FM_TRACE");
+    return v && *v && std::strcmp(v, "0") != 0;
+}
+
+void fm_trace(const char* fmt, ...)
+{
+    if (!fm_trace_on()) return;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    const char* v = std::getenv("FM_TRACE");
+    FILE* f = std::strcmp(v, "1") == 0 ? stderr : std::fopen(v, "a");
+    if (!f) return;
+    va_list ap;
+    va_start(ap, fmt);
+    std::fprintf(f, "fm: ");
+    std::vfprintf(f, fmt, ap);
+    std::fprintf(f, "\n");
+    va_end(ap);
+    if (f != stderr) std::fclose(f);
+}
+
+FmRange::FmRange(const char* name) { nvtxRangePushA(name); }
+FmRange::~FmRange() { nvtxRangePop(); }
+
 extern "C" int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, int32_t algo,
                             const fm_opts* opts, fm_stream stream)
 {
+    FmRange range("fm_gemm_modp");
     if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
     if (op < FM_OP_SET || op > FM_OP_SUB) return FM_EINVAL;
     if (algo < FM_ALGO_AUTO || algo > FM_ALGO_DFMA) return FM_EINVAL;
@@ -255,6 +289,10 @@ extern "C" int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op
         FM_TRY(fm_limb_plan(M, N, K, p, opts, &plan));
         void* ws = fm_workspace(0, fm_limb_workspace_bytes(plan));
         if (!ws) return FM_ENOMEM;
+        fm_trace("gemm_modp limb M=%lld N=%lld K=%lld p=%u op=%d products=%d tiles=%d jobs/tile=%d planes=%zu B",
+                 (long long)M, (long long)N, (long long)K, p, op, plan.n_products, plan.MB * plan.NB,
+                 plan.n_products ? (plan.KB + plan.prod_cs[0] - 1) / plan.prod_cs[0] : 0,
+                 fm_limb_workspace_bytes(plan));
         return fm_limb_run(plan, C, A, B, p, op, ws, status, s);
     }
     // decomposed paths (Sec. 2.2): equal T', T' in {32, 64}
@@ -270,6 +308,9 @@ extern "C" int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op
     }
     ListEntry* e = nullptr;
     FM_TRY(get_lists(C, A, B, op, &e));
+    fm_trace("gemm_modp %s T'=%d M=%lld N=%lld K=%lld p=%u op=%d base-case products=%lld",
+             algo == FM_ALGO_DFMA ? "dfma" : "plain", 1 << lt, (long long)M, (long long)N, (long long)K, p,
+             op, (long long)e->n_items);
     return fm_plain_launch(lt, arith, e->d_calls, e->d_items, e->d_lps, e->n_items, p, nullptr,
                            (int)e->n_items, status, s);
 }
@@ -406,7 +447,10 @@ extern "C" int fm_gf2_plan_create(fm_plan** out, const fm_gf2_call* calls, int64
 
 extern "C" int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream)
 {
+    FmRange range("fm_gemm_modp_batched");
     if (!plan) return FM_EINVAL;
+    fm_trace("gemm_modp_batched %s work items=%lld", plan->limb ? "tensor-core" : "decomposed",
+             (long long)plan->n_items);
     if (plan->limb) {
         for (const fm_gemm_call& g : fm_limb_batch_zero_calls(plan->limb))
             if (g.op == FM_OP_SET) FM_TRY(fm_gemm_modp(g.C, g.A, g.B, plan->p, g.op, FM_ALGO_LIMB_TC, nullptr, stream));

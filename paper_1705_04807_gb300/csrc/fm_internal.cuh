@@ -99,6 +99,17 @@ void* fm_workspace(int slot, size_t bytes);
 void* fm_host_staging(int slot, size_t bytes);
 int fm_sm_count();
 
+// FM_TRACE: when the environment variable is set, every public call appends one
+// line (call, shapes, work) to stderr, or to the file it names if it is not "1".
+bool fm_trace_on();
+void fm_trace(const char* fmt, ...);
+
+// NVTX range around a public entry point (visible in Nsight timelines).
+struct FmRange {
+    explicit FmRange(const char* name);
+    ~FmRange();
+};
+
 // ---------------------------------------------------------------------------
 // Device-side: bounded waits and status.
 // ---------------------------------------------------------------------------
@@ -118,6 +129,37 @@ __device__ __forceinline__ uint64_t fm_globaltimer()
 __device__ __forceinline__ void fm_raise(int* status, int code)
 {
     if (status) atomicCAS(status, 0, code);
+}
+
+// Grid-wide barrier of a cooperative launch (bar[0] = arrivals, bar[1] =
+// generation, zeroed before the launch). A wait that expires raises FM_ETIMEOUT
+// and sets *s_abort (shared), after which every later barrier of the CTA
+// returns false at once.
+__device__ __forceinline__ bool fm_grid_barrier(unsigned* bar, int* status, volatile int* s_abort)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*s_abort) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = fm_globaltimer();
+            while (*gen == g) {
+                if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
+                    fm_raise(status, FM_ETIMEOUT);
+                    *s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !*s_abort;
 }
 
 __device__ __forceinline__ uint32_t fm_smem_u32(const void* p)

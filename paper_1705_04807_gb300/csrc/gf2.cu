@@ -333,6 +333,7 @@ int fm_gf2_check_call(const fm_gf2_call& g)
 extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op, const fm_opts* opts,
                            fm_stream stream)
 {
+    FmRange range("fm_gf2_gemm");
     fm_gf2_call g;
     g.C = C;
     g.A = A;
@@ -363,5 +364,7 @@ extern "C" int fm_gf2_gemm(fm_gf2_sub C, fm_gf2_sub A, fm_gf2_sub B, int32_t op,
     gf2_split_b_kernel<<<q.NB * q.KB, kGf2Threads, 0, s>>>(B.m.base, B.m.log2_grid, B.row0, B.col0, K, N,
                                                            q.KB, Bp);
     FM_CUDA_TRY(cudaGetLastError());
+    fm_trace("gf2_gemm M=%lld N=%lld K=%lld op=%d tiles=%d planes=%llu B", (long long)M, (long long)N,
+             (long long)K, op, q.MB * q.NB, (unsigned long long)(q.a_plane_bytes + q.b_plane_bytes));
     return fm_limb_gemm_run(q, Cs, Ap, Bp, 2u, op, status, s);
 }

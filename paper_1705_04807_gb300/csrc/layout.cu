@@ -228,6 +228,7 @@ int to_morton_impl(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
 extern "C" int fm_layout_to_morton(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
                                    fm_matrix dst, fm_stream stream)
 {
+    FmRange range("fm_layout_to_morton");
     return to_morton_impl(src, rows, cols, ld, nullptr, nullptr, dst, stream);
 }
 
@@ -236,12 +237,14 @@ extern "C" int fm_layout_to_morton_permuted(const uint32_t* src, int64_t rows, i
                                             const int32_t* col_perm, fm_matrix dst,
                                             fm_stream stream)
 {
+    FmRange range("fm_layout_to_morton_permuted");
     return to_morton_impl(src, rows, cols, ld, row_perm, col_perm, dst, stream);
 }
 
 extern "C" int fm_layout_from_morton(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst,
                                      int64_t ld, fm_stream stream)
 {
+    FmRange range("fm_layout_from_morton");
     FM_TRY(fm_check_matrix(src));
     const int64_t n = fm_side(src);
     if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
@@ -259,6 +262,7 @@ extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, 
                                     const int32_t* row_perm, const int32_t* col_perm,
                                     fm_stream stream)
 {
+    FmRange range("fm_permute_rows_cols");
     FM_TRY(fm_check_matrix(src));
     FM_TRY(fm_check_matrix(dst));
     const int64_t ns = fm_side(src), nd = fm_side(dst);

@@ -80,34 +80,6 @@ struct PanelArgs {
     int* status;
 };
 
-// Bounded grid-wide barrier (all CTAs co-resident: cooperative launch).
-__device__ bool grid_barrier(unsigned* bar, int* status, volatile int* s_abort)
-{
-    __syncthreads();
-    if (threadIdx.x == 0 && !*s_abort) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const uint64_t t0 = fm_globaltimer();
-            while (*gen == g) {
-                if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
-                    fm_raise(status, FM_ETIMEOUT);
-                    *s_abort = 1;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return !*s_abort;
-}
-
 __device__ __forceinline__ uint32_t* elem(const PanelArgs& a, int64_t i, int64_t j)
 {
     return a.A + fm_encode((uint64_t)i, (uint64_t)j, a.lt);
@@ -127,7 +99,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
     int found = 0;
     for (int t = 0; t < a.w; ++t) {
         const int64_t j = a.c0 + t;
-        if (!grid_barrier(a.bar, a.status, &s_abort)) return;  // updates of column t-1 done
+        if (!fm_grid_barrier(a.bar, a.status, &s_abort)) return;  // updates of column t-1 done
         if (r >= a.m) {
             if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = -1;
             continue;
@@ -146,7 +118,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
                     break;
                 }
             }
-            if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+            if (!fm_grid_barrier(a.bar, a.status, &s_abort)) return;
             piv = *(volatile int*)&a.piv_slot[t];
             if (piv == INT_MAX) {  // no nonzero below row r: a non-pivot column
                 if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = -1;
@@ -161,7 +133,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
                     *y = tmp;
                 }
             }
-            if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+            if (!fm_grid_barrier(a.bar, a.status, &s_abort)) return;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) a.piv_row[t] = piv;
         // pivot row to shared memory
@@ -342,7 +314,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
             if (tid == 0) atomicMin(&a.slot[t], (int)(row0 + li));
         }
         // 2. one barrier: every candidate is published
-        if (!grid_barrier(a.bar, a.status, &s_abort)) return;
+        if (!fm_grid_barrier(a.bar, a.status, &s_abort)) return;
         const int piv = *(volatile int*)&a.slot[t];
         if (piv == INT_MAX) {  // no nonzero left in this column: a non-pivot column
             if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = -1;
@@ -456,6 +428,7 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(uint32_t* A, int lt,
 extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* row_perm,
                        int32_t* col_perm, int64_t* rank, fm_stream stream)
 {
+    FmRange range("fm_pluq");
     if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
     FM_TRY(fm_check_matrix(Am));
     if (m < 0 || n < 0 || m > fm_side(Am) || n > fm_side(Am) || !rank) return FM_EINVAL;
@@ -667,5 +640,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     }
     FM_CUDA_TRY(cudaStreamSynchronize(s));
     *rank = r;
+    fm_trace("pluq m=%lld n=%lld p=%u rank=%lld panels of %d columns", (long long)m, (long long)n, p,
+             (long long)r, kNb);
     return FM_OK;
 }

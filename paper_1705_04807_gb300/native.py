@@ -31,7 +31,7 @@ EXPORTS = (
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
     "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
     "fm_pluq", "fm_gf2_pack", "fm_gf2_unpack", "fm_gf2_gemm", "fm_gf2_workspace_size",
-    "fm_gf2_plan_create",
+    "fm_gf2_plan_create", "fm_debug_expire_wait",
 )
 
 
@@ -135,6 +135,7 @@ def lib():
         "fm_gf2_workspace_size": ([I64, I64, I64], I64),
         "fm_gf2_plan_create": ([ctypes.POINTER(P), ctypes.POINTER(fm_gf2_call), I64,
                                 ctypes.POINTER(fm_opts)], ctypes.c_int),
+        "fm_debug_expire_wait": ([I32, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -397,6 +398,10 @@ def fm_gf2_workspace_size(M: int, N: int, K: int) -> int:
     if r < 0:
         raise FmError(int(r), "fm_gf2_workspace_size")
     return int(r)
+
+
+def fm_debug_expire_wait(which: int, stream=None):
+    return _check(lib().fm_debug_expire_wait(int(which), _stream(stream)), "fm_debug_expire_wait")
 
 
 def fm_get_last_device_status(stream=None) -> int:
