@@ -282,8 +282,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int mb_rows = (int)((args.call.M + kBM - 1) / kBM);
     const int n_tiles = BATCH ? args.n_tiles : mb_rows * args.call.NB;
 
-    // tile -> its call and (mb, nb). One call: grouped raster (groups of 8 row
-    // blocks) for L2 reuse; batched: the plan's tile list.
+    // tile -> its call and (mb, nb). One call: grouped raster for L2 reuse (a
+    // wave of 152 tiles covers GROUP row blocks; 16 for 256-wide tiles, whose B
+    // panels are twice as wide, makes the wave's panel bytes near minimal);
+    // batched: the plan's tile list.
     auto tile_call = [&](int tile, int& mb, int& nb) -> const LimbCall& {
         if (BATCH) {
             const int4 e = args.tiles[tile];
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             nb = e.z;
             return args.calls[e.x];
         }
-        const int GROUP = 8;
+        const int GROUP = BN == 256 ? 16 : 8;
         const int per_group = GROUP * args.call.NB;
         const int first_mb = (tile / per_group) * GROUP;
         const int gsz = min(mb_rows - first_mb, GROUP);
