@@ -112,10 +112,25 @@ __device__ __forceinline__ float fold_round(float f, float invp, float pf)
     return __fmaf_rn(-q, pf, f);
 }
 
+// The same-product drain is the drain that runs most often (the Karatsuba
+// middle product's 256-deep chunks): it uses Blackwell's packed FP32 arithmetic,
+// two accumulator values per instruction (each lane rounded exactly as the
+// scalar fold_round does), halving its instruction issue.
 __device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
 {
+    const uint64_t ip = (uint64_t)__float_as_uint(invp) * 0x100000001ull;
+    const uint64_t bs = (uint64_t)__float_as_uint(kRoundBias) * 0x100000001ull;
+    const uint64_t np = (uint64_t)__float_as_uint(-pf) * 0x100000001ull;
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = __float_as_uint(fold_round(__uint_as_float(v[e]), invp, pf));
+    for (int e = 0; e < 32; e += 2)
+        asm("{\n\t.reg .b64 x, t, q;\n\t"
+            "mov.b64 x, {%0, %1};\n\t"
+            "fma.rn.f32x2 t, x, %2, %3;\n\t"   // v / p + 1.5 * 2^23
+            "sub.rn.f32x2 q, t, %3;\n\t"       // round(v / p)
+            "fma.rn.f32x2 x, q, %4, x;\n\t"    // v - round(v / p) p
+            "mov.b64 {%0, %1}, x;\n\t}"
+            : "+r"(v[e]), "+r"(v[e + 1])
+            : "l"(ip), "l"(bs), "l"(np));
 }
 
 __device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
