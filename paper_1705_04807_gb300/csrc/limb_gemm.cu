@@ -100,7 +100,8 @@ struct LimbGemmArgs {
 // round-to-nearest of v / p is one FMA with the constant 1.5 * 2^23 (the sum
 // lands where the float spacing is 1) and one subtraction, both on the FMA
 // pipe; conversions between small integers and floats use the same bias.
-// fold_fp: v - round(v/p) p, exact, a carried value of magnitude <= p/2 + 1.
+// fold_fp: v - q p with q = the rounded quotient (within 3/4 of v / p, as 1/p
+// is rounded), exact, a carried value of magnitude <= 3p/4 < p.
 // fold_int: that value times mul mod p, as a float to carry on (to_float) or
 // as the final residue in [0, p).
 constexpr float kRoundBias = 12582912.0f;  // 1.5 * 2^23
@@ -133,19 +134,66 @@ __device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
             : "l"(ip), "l"(bs), "l"(np));
 }
 
-__device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
-                                         uint32_t mu32, float invp, float pf)
+// Packed FP32 helpers: two lanes per instruction, each rounded as the scalar op.
+__device__ __forceinline__ uint64_t f2_fold(uint64_t x, uint64_t ip, uint64_t bs, uint64_t np)
 {
+    uint64_t r;
+    asm("{\n\t.reg .b64 t, q;\n\t"
+        "fma.rn.f32x2 t, %1, %2, %3;\n\t"
+        "sub.rn.f32x2 q, t, %3;\n\t"
+        "fma.rn.f32x2 %0, q, %4, %1;\n\t}"
+        : "=l"(r)
+        : "l"(x), "l"(ip), "l"(bs), "l"(np));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t f2_splat(float f)
+{
+    return (uint64_t)__float_as_uint(f) * 0x100000001ull;
+}
+
+// Product-boundary and final drains: x = v folded (|x| <= 3p/4, since the
+// rounded quotient is off by at most 3/4), then x * mul mod p in exact FP32
+// steps with mul = 256 c1 + c0 (c0, c1 < 256): x c0 and x c1 are below 2^24 in
+// magnitude and are folded, and r0 + 256 r1 (at most 257 * 3p/4 < 2^24) is
+// folded once more. The result, a value in (-p, p), is carried on as a float
+// (to_float) or converted to the residue in [0, p) through the same bias.
+__device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
+                                         float invp, float pf)
+{
+    const uint64_t ip = f2_splat(invp), bs = f2_splat(kRoundBias), np = f2_splat(-pf);
+    const uint64_t c0 = f2_splat((float)(mul & 255u)), c1 = f2_splat((float)(mul >> 8));
+    const uint64_t k256 = f2_splat(256.0f);
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const float r = fold_round(__uint_as_float(v[e]), invp, pf);
-        int32_t x = (int32_t)(__float_as_uint(__fadd_rn(r, kRoundBias)) - kRoundBiasBits);
-        x += x < 0 ? (int32_t)p : 0;
-        x -= x >= (int32_t)p ? (int32_t)p : 0;
-        const uint32_t y = barrett32(mul * (uint32_t)x, p, mu32);  // mul, x < p < 2^16
-        // y < 2^16: its float is 2^23 + y with the low mantissa bits = y, minus 2^23
-        v[e] = to_float ? __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | y), 8388608.0f))
-                        : y;
+    for (int e = 0; e < 32; e += 2) {
+        uint64_t x = ((uint64_t)v[e + 1] << 32) | v[e];
+        x = f2_fold(x, ip, bs, np);
+        const uint64_t r0 = f2_fold(f2_mul(x, c0), ip, bs, np);
+        const uint64_t r1 = f2_fold(f2_mul(x, c1), ip, bs, np);
+        const uint64_t y = f2_fold(f2_fma(r1, k256, r0), ip, bs, np);
+        uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+        if (!to_float) {
+            int32_t a = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(y0), kRoundBias)) - kRoundBiasBits);
+            int32_t b = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(y1), kRoundBias)) - kRoundBiasBits);
+            y0 = (uint32_t)(a + (a < 0 ? (int32_t)p : 0));
+            y1 = (uint32_t)(b + (b < 0 ? (int32_t)p : 0));
+        }
+        v[e] = y0;
+        v[e + 1] = y1;
     }
 }
 
@@ -504,8 +552,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                             fold_fp(v0, args.invp, args.pf);
                             fold_fp(v1, args.invp, args.pf);
                         } else {
-                            fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
-                            fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
+                            fold_int(v0, mul, !last_on_buffer, p, args.invp, args.pf);
+                            fold_int(v1, mul, !last_on_buffer, p, args.invp, args.pf);
                         }
                         fm_tmem_st32(dbase + g * 64, v0);
                         fm_tmem_st32(dbase + g * 64 + 32, v1);
@@ -851,8 +899,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                         fold_fp(v0, args.invp, args.pf);
                         fold_fp(v1, args.invp, args.pf);
                     } else {
-                        fold_int(v0, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
-                        fold_int(v1, mul, !last_on_buffer, p, args.mu32, args.invp, args.pf);
+                        fold_int(v0, mul, !last_on_buffer, p, args.invp, args.pf);
+                        fold_int(v1, mul, !last_on_buffer, p, args.invp, args.pf);
                     }
                     fm_tmem_st32(dbase + g * 64, v0);
                     fm_tmem_st32(dbase + g * 64 + 32, v1);
