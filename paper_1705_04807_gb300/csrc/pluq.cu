@@ -12,7 +12,8 @@
 //        nonzero below row r is skipped (it belongs to the non-pivot columns);
 //     2. move the panel's pivot columns in front of its skipped ones;
 //     3. apply the panel's row swaps to the rest of the matrix;
-//     4. U12 <- L11^-1 A12 (unit lower triangular solve);
+//     4. U12 <- L11^-1 A12: the inverse of the unit lower triangle L11 (one
+//        CTA), then one limb product X * A12 written over A12;
 //     5. A22 <- A22 - L21 U12 mod p: one fm_gemm_modp call on three disjoint
 //        sub-matrices of the Morton-hybrid matrix -- the MM call the paper's
 //        decomposition issues (Sec. 2: S_A = S_B * S_C on sub-matrices).
@@ -375,52 +376,46 @@ __global__ void swap_pairs_kernel(uint32_t* A, int lt, int64_t n, const int* __r
     }
 }
 
-// U12 <- L11^-1 A12 on rows [r0, r0+k) x columns [cl, n), L11 the unit lower
-// triangle of rows [r0, r0+k) x columns [c0, c0+k). Each CTA stages L11 and a
-// block of 32 columns in shared memory and runs the forward substitution row by
-// row, 8 threads sharing each column's dot product.
-constexpr int kTrsmCols = 32;
-constexpr int kTrsmThreads = 256;
-__global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(uint32_t* A, int lt, int64_t r0, int64_t c0,
-                                                            int k, int64_t cl, int64_t n, uint32_t p,
-                                                            uint64_t mu)
+// X <- L11^-1 (k x k, k <= 128), L11 the unit lower triangle of rows
+// [r0, r0+k) x columns [c0, c0+k); X is written to the Morton-hybrid matrix Xm
+// (zero above the diagonal, ones on it). Row i of X follows from the rows above
+// it, X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j); four lanes share each
+// column's sum (64-bit accumulation: raw products below p^2 < 2^32 when
+// p < 2^16, products reduced mod p otherwise).
+constexpr int kInvThreads = 512;
+
+__global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
+                                                              int k, uint32_t* X, int xlt, uint32_t p,
+                                                              uint64_t mu)
 {
     extern __shared__ uint32_t smx[];
-    uint32_t* L = smx;                    // [k][k]
-    uint32_t* X = smx + (size_t)k * k;    // [k][kTrsmCols]
+    uint32_t* L = smx;                  // [k][k], strictly lower part
+    uint32_t* Xs = smx + (size_t)k * k;  // [k][k]
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int i = e / k, t = e % k;
         L[e] = t < i ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
+        Xs[e] = i == t ? 1u : 0u;
     }
-    const int c = threadIdx.x >> 3, sub = threadIdx.x & 7;  // column in block, share of the sum
-    for (int64_t jb = cl + (int64_t)blockIdx.x * kTrsmCols; jb < n; jb += (int64_t)gridDim.x * kTrsmCols) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < k * kTrsmCols; e += blockDim.x) {
-            const int i = e / kTrsmCols, cc = e % kTrsmCols;
-            X[e] = jb + cc < n ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(jb + cc), lt)] : 0u;
+    __syncthreads();
+    const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
+    for (int i = 1; i < k; ++i) {
+        uint64_t acc = 0;
+        if (j < i) {
+            if (p < 65536u)
+                for (int t = j + q; t < i; t += 4) acc += (uint64_t)L[i * k + t] * Xs[t * k + j];
+            else
+                for (int t = j + q; t < i; t += 4) acc += mulmod(L[i * k + t], Xs[t * k + j], p, mu);
+        }
+        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+        if (j < i && q == 0) {
+            const uint32_t r = (uint32_t)(acc % p);
+            Xs[i * k + j] = r == 0 ? 0u : p - r;
         }
         __syncthreads();
-        for (int i = 1; i < k; ++i) {
-            // x_i -= sum_{t<i} L[i][t] x_t; partial sums reduced mod p before combining
-            uint64_t acc = 0;
-            for (int t = sub; t < i; t += 8) {
-                acc += (uint64_t)mulmod(L[i * k + t], X[t * kTrsmCols + c], p, mu);
-            }
-            uint32_t part = (uint32_t)(acc % p);
-#pragma unroll
-            for (int o = 4; o >= 1; o >>= 1) {
-                const uint32_t other = __shfl_xor_sync(0xffffffffu, part, o);
-                const uint32_t sum = part + other;
-                part = sum >= p ? sum - p : sum;
-            }
-            if (sub == 0) X[i * kTrsmCols + c] = submod(X[i * kTrsmCols + c], part, p);
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < k * kTrsmCols; e += blockDim.x) {
-            const int i = e / kTrsmCols, cc = e % kTrsmCols;
-            if (jb + cc < n) A[fm_encode((uint64_t)(r0 + i), (uint64_t)(jb + cc), lt)] = X[e];
-        }
     }
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x)
+        X[fm_encode((uint64_t)(e / k), (uint64_t)(e % k), xlt)] = Xs[e];
 }
 
 }  // namespace
@@ -601,12 +596,23 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             const int64_t cl = c0 + w;
             if (cl < n) {
                 const int64_t cols = n - cl;
-                const size_t tsmem = ((size_t)k * k + (size_t)k * kTrsmCols) * 4;
-                FM_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)tsmem));
-                trsm_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((cols + kTrsmCols - 1) / kTrsmCols, 4096)),
-                              kTrsmThreads, tsmem, s>>>(Am.base, Am.log2_T, r, c0, k, cl, n, p, mu);
+                // U12 <- L11^-1 A12 as a product (Sec. 2: S_A = S_B * S_C): X = L11^-1
+                // in one CTA, then the limb product into A12 itself (it multiplies
+                // limb planes split from A12 before A12 is written)
+                uint32_t* xs = static_cast<uint32_t*>(fm_workspace(4, (size_t)kNb * kNb * 4));
+                if (!xs) return FM_ENOMEM;
+                const size_t ismem = (size_t)2 * k * k * 4;
+                FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)ismem));
+                tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
                 FM_CUDA_TRY(cudaGetLastError());
+                const fm_matrix Xm{xs, 0, 7};
+                const fm_sub A12{Am, r, cl, k, cols};
+                FmLimbPlan lq;
+                FM_TRY(fm_limb_plan(k, cols, k, p, nullptr, &lq));
+                void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
+                if (!lws) return FM_ENOMEM;
+                FM_TRY(fm_limb_run(lq, A12, fm_sub{Xm, 0, 0, k, k}, A12, p, FM_OP_SET, lws, status, s));
                 if (r + k < m) {
                     const fm_sub C{Am, r + k, cl, m - r - k, cols};
                     const fm_sub L21{Am, r + k, c0, m - r - k, k};
