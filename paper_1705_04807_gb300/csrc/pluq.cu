@@ -262,27 +262,63 @@ struct SmemPanelArgs {
     int rows_per_cta;  // R: CTA b owns rows [r0 + b R, r0 + (b+1) R) of the panel
     uint32_t p;
     uint64_t mu;
-    int* slot;         // [w] smallest candidate row per column (INT_MAX before)
-    uint32_t* cand;    // [2][gridDim.x][w + 2]: candidate row values, inverse, row
+    int* stat;         // [w][gridDim.x], zeroed: 0 = not yet published, 1 = no
+                       // candidate, 2 + i = candidate is this CTA's row i
+    uint32_t* cand;    // [w][gridDim.x][w + 2]: candidate row values, inverse, row
     int* piv_row;      // out [w]: pivot row of column t (original index) or -1
     int* n_piv;        // out
     unsigned* bar;
     int* status;
 };
 
-// Panel factorisation with the panel rows resident in shared memory: per column
-// each CTA offers its first non-pivot row with a nonzero entry, one grid
-// barrier picks the smallest row index, every CTA reads that row and updates
-// its own non-pivot rows. Rows are not moved; the pivot order is returned.
+// a * b mod p for a, b < p: one 32-bit Barrett step when p < 2^16 (the product
+// fits 32 bits), the 64-bit one otherwise (mu32 = 2^32 / p, mu = 2^64 / p).
+__device__ __forceinline__ uint32_t mul_p(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32, uint64_t mu)
+{
+    if (p < 65536u) {
+        const uint32_t x = a * b;
+        uint32_t r = x - __umulhi(x, mu32) * p;
+        return r >= p ? r - p : r;
+    }
+    return mulmod(a, b, p, mu);
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Panel factorisation with the panel rows resident in shared memory. CTA b owns
+// rows [r0 + b R, r0 + (b+1) R). The pivot of column t is the first row (in row
+// order) that is not yet a pivot and has a nonzero in column t, so it belongs to
+// the lowest-numbered CTA that has such a row. Per column every CTA publishes
+// its candidate (row values, inverse, index) in a slot of its own and then a
+// status word (release); it reads the status words of CTAs 0, 1, ... (acquire)
+// only up to the first one that has a candidate, takes that row and updates its
+// own non-pivot rows. The CTA that owns the pivot reads only lower-numbered
+// CTAs' status words (already published: they have no candidate) and uses its
+// own row, so it runs at its own pace; there is no grid-wide barrier per
+// column. A CTA publishes column t before it reads anything of column t, so the
+// waits form no cycle. Rows are not moved; the pivot order is returned. Every
+// wait is bounded.
 __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const SmemPanelArgs a)
 {
     extern __shared__ uint32_t sm[];
-    const int R = a.rows_per_cta, w = a.w;
+    const int R = a.rows_per_cta, w = a.w, P = gridDim.x;
     uint32_t* rows = sm;                                   // [R][w]
     uint32_t* prow = rows + (size_t)R * w;                 // [w]
     int* piv_flag = reinterpret_cast<int*>(prow + kNb);    // [R]
-    __shared__ int s_abort, s_first;
-    __shared__ uint32_t s_inv;
+    uint32_t* lbuf = reinterpret_cast<uint32_t*>(piv_flag + R);  // [R] multipliers
+    const uint32_t mu32 = (uint32_t)(0x100000000ull / a.p);
+    __shared__ int s_abort, s_first, s_owner, s_code;
+    __shared__ uint32_t s_inv, s_myinv;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = a.r0 + (int64_t)blockIdx.x * R;
     const int64_t left = a.m - row0;
@@ -296,7 +332,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
     __syncthreads();
     int found = 0;
     for (int t = 0; t < w; ++t) {
-        uint32_t* cbuf = a.cand + ((size_t)(t & 1) * gridDim.x + blockIdx.x) * (w + 2);
         // 1. this CTA's candidate: first non-pivot row with a nonzero in column t
         if (tid == 0) s_first = INT_MAX;
         __syncthreads();
@@ -304,44 +339,89 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
             if (!piv_flag[i] && rows[(size_t)i * w + t] != 0) atomicMin(&s_first, i);
         __syncthreads();
         const int li = s_first;
-        if (li != INT_MAX) {
-            for (int c = tid; c < w; c += kPanelThreads) cbuf[c] = rows[(size_t)li * w + c];
-            if (tid == 0) {
-                cbuf[w] = inv_euclid(rows[(size_t)li * w + t], a.p);
-                cbuf[w + 1] = (uint32_t)(row0 + li);
+        const int mycode = li != INT_MAX ? 2 + li : 1;
+        // warp 0 publishes: the candidate row, then (ordered after the warp's
+        // writes by __syncwarp, and cumulative) one release store of the status
+        if (warp == 0) {
+            if (li != INT_MAX) {
+                uint32_t* cbuf = a.cand + ((size_t)t * P + blockIdx.x) * (w + 2);
+                for (int c = lane; c < w; c += 32) cbuf[c] = rows[(size_t)li * w + c];
+                if (lane == 0) {
+                    s_myinv = inv_euclid(rows[(size_t)li * w + t], a.p);
+                    cbuf[w] = s_myinv;
+                    cbuf[w + 1] = (uint32_t)(row0 + li);
+                }
             }
-            __threadfence();  // every writer: the candidate is visible before its index
-            __syncthreads();
-            if (tid == 0) atomicMin(&a.slot[t], (int)(row0 + li));
+            __syncwarp();
+            if (lane == 0) {
+                st_release_gpu(&a.stat[(size_t)t * P + blockIdx.x], mycode);
+                s_owner = INT_MAX;
+            }
         }
-        // 2. one barrier: every candidate is published
-        if (!fm_grid_barrier(a.bar, a.status, &s_abort)) return;
-        const int piv = *(volatile int*)&a.slot[t];
-        if (piv == INT_MAX) {  // no nonzero left in this column: a non-pivot column
+        __syncthreads();
+        // 2. find the first CTA with a candidate: thread b reads CTA b's status
+        // word, all at once (only lower CTAs when this one has a candidate); a
+        // thread stops as soon as a lower CTA is known to have one, so only CTAs
+        // up to the owner are waited for
+        const int limit = mycode >= 2 ? (int)blockIdx.x + 1 : P;
+        for (int b = tid; b < limit; b += kPanelThreads) {
+            int code = b == (int)blockIdx.x ? mycode : 0;
+            if (code == 0) {
+                const int* sp = &a.stat[(size_t)t * P + b];
+                const uint64_t t0 = fm_globaltimer();
+                while ((code = ld_acquire_gpu(sp)) == 0) {
+                    if (*(volatile int*)&s_owner < b || s_abort) break;
+                    if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
+                        fm_raise(a.status, FM_ETIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+            }
+            if (code >= 2) atomicMin(&s_owner, b);
+        }
+        __syncthreads();
+        if (s_abort) return;
+        if (tid == 0) {
+            const int o = s_owner;
+            s_code = o == INT_MAX ? 0 : (o == (int)blockIdx.x ? mycode : __ldcg(&a.stat[(size_t)t * P + o]));
+            if (o == INT_MAX) s_owner = -1;
+        }
+        __syncthreads();
+        const int owner = s_owner;
+        if (owner < 0) {  // no nonzero left in this column: a non-pivot column
             if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = -1;
             continue;
         }
-        // 3. the pivot row from its owner's candidate slot
-        const int owner = (int)((piv - a.r0) / R);
-        const volatile uint32_t* ob =
-            a.cand + ((size_t)(t & 1) * gridDim.x + owner) * (w + 2);
-        for (int c = tid; c < w; c += kPanelThreads) prow[c] = ob[c];
-        if (tid == 0) s_inv = ob[w];
-        if (owner == (int)blockIdx.x && tid == 0) piv_flag[piv - row0] = 1;
-        if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = piv;
+        // 3. the pivot row: this CTA's own row, or the owner's published copy
+        if (owner == (int)blockIdx.x) {
+            for (int c = tid; c < w; c += kPanelThreads) prow[c] = rows[(size_t)li * w + c];
+            if (tid == 0) {
+                s_inv = s_myinv;
+                piv_flag[li] = 1;
+            }
+        } else {
+            const uint32_t* ob = a.cand + ((size_t)t * P + owner) * (w + 2);
+            for (int c = tid; c < w; c += kPanelThreads) prow[c] = __ldcg(ob + c);
+            if (tid == 0) s_inv = __ldcg(ob + w);
+        }
+        if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = (int)(a.r0 + (int64_t)owner * R + (s_code - 2));
         __syncthreads();
         const uint32_t inv = s_inv;
-        // 4. update the non-pivot rows: a_i <- a_i - l_i * pivot row (columns > t), l_i in column t
+        // 4. the multipliers l_i (column t) of all non-pivot rows at once, then
+        // a_i <- a_i - l_i * pivot row on columns > t (warps over rows, lanes
+        // over columns); l_i is kept in column t
+        for (int i = tid; i < nrows; i += kPanelThreads)
+            lbuf[i] = piv_flag[i] ? 0u : mul_p(rows[(size_t)i * w + t], inv, a.p, mu32, a.mu);
+        __syncthreads();
         for (int i = warp; i < nrows; i += kPanelThreads / 32) {
-            if (piv_flag[i]) continue;
+            const uint32_t l = lbuf[i];
+            if (l == 0) continue;
             uint32_t* ri = rows + (size_t)i * w;
-            const uint32_t l = mulmod(ri[t], inv, a.p, a.mu);
-            if (l != 0)
-                for (int c = t + 1 + lane; c < w; c += 32)
-                    ri[c] = submod(ri[c], mulmod(l, prow[c], a.p, a.mu), a.p);
-            __syncwarp();
-            if (lane == 0) ri[t] = l;
+            for (int c = t + 1 + lane; c < w; c += 32) ri[c] = submod(ri[c], mul_p(l, prow[c], a.p, mu32, a.mu), a.p);
         }
+        for (int i = tid; i < nrows; i += kPanelThreads)
+            if (!piv_flag[i]) rows[(size_t)i * w + t] = lbuf[i];
         __syncthreads();
         ++found;
     }
@@ -379,10 +459,10 @@ __global__ void swap_pairs_kernel(uint32_t* A, int lt, int64_t n, const int* __r
 // X <- L11^-1 (k x k, k <= 128), L11 the unit lower triangle of rows
 // [r0, r0+k) x columns [c0, c0+k); X is written to the Morton-hybrid matrix Xm
 // (zero above the diagonal, ones on it). Row i of X follows from the rows above
-// it, X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j); four lanes share each
+// it, X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j); eight lanes share each
 // column's sum (64-bit accumulation: raw products below p^2 < 2^32 when
 // p < 2^16, products reduced mod p otherwise).
-constexpr int kInvThreads = 512;
+constexpr int kInvThreads = 1024;
 
 __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                               int k, uint32_t* X, int xlt, uint32_t p,
@@ -397,17 +477,18 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A,
         Xs[e] = i == t ? 1u : 0u;
     }
     __syncthreads();
-    const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int j = threadIdx.x >> 3, q = threadIdx.x & 7;
     for (int i = 1; i < k; ++i) {
         uint64_t acc = 0;
         if (j < i) {
             if (p < 65536u)
-                for (int t = j + q; t < i; t += 4) acc += (uint64_t)L[i * k + t] * Xs[t * k + j];
+                for (int t = j + q; t < i; t += 8) acc += (uint64_t)L[i * k + t] * Xs[t * k + j];
             else
-                for (int t = j + q; t < i; t += 4) acc += mulmod(L[i * k + t], Xs[t * k + j], p, mu);
+                for (int t = j + q; t < i; t += 8) acc += mulmod(L[i * k + t], Xs[t * k + j], p, mu);
         }
         acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
         acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
         if (j < i && q == 0) {
             const uint32_t r = (uint32_t)(acc % p);
             Xs[i * k + j] = r == 0 ? 0u : p - r;
@@ -442,14 +523,14 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         FM_CUDA_TRY(cudaStreamSynchronize(s));
     }
     // device workspace: piv_slot[kNb], piv_row[kNb], order[kNb], n_piv, barrier[2],
-    // swap pairs[2 kNb], candidate rows [2][grid][kNb + 2]
+    // swap pairs[2 kNb], candidate rows [kNb][grid][kNb + 2], status words [kNb][grid]
     int dev = 0, coop = 0, per_sm = 0, max_smem = 0;
     FM_CUDA_TRY(cudaGetDevice(&dev));
     FM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     FM_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (!coop) return FM_EUNSUPPORTED;
     const int sms = fm_sm_count();
-    const size_t ws_ints = 3 * kNb + 4 + 2 * kNb + 2 * (size_t)sms * (kNb + 2);
+    const size_t ws_ints = 3 * kNb + 4 + 2 * kNb + (size_t)kNb * sms * (kNb + 2) + (size_t)kNb * sms;
     int* ws = static_cast<int*>(fm_workspace(1, sizeof(int) * ws_ints));
     if (!ws) return FM_ENOMEM;
     int* d_slot = ws;
@@ -459,6 +540,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     unsigned* d_bar = reinterpret_cast<unsigned*>(ws + 3 * kNb + 2);
     int* d_pairs = ws + 3 * kNb + 4;
     uint32_t* d_cand = reinterpret_cast<uint32_t*>(ws + 5 * kNb + 4);
+    int* d_stat = ws + 5 * kNb + 4 + (size_t)kNb * sms * (kNb + 2);
     FM_CUDA_TRY(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
 
     FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, kPanelThreads, 0));
@@ -480,7 +562,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         FM_CUDA_TRY(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int) * kNb, cudaMemcpyHostToDevice, s));
         // panel rows resident in shared memory when a CTA's share fits
         const int R = (int)((m - r + sms - 1) / sms);
-        const size_t psmem = ((size_t)R * w + kNb + R) * 4;
+        const size_t psmem = ((size_t)R * w + kNb + 2 * (size_t)R) * 4;
         const bool smem_path = psmem <= (size_t)max_smem;
         if (smem_path) {
             SmemPanelArgs pa;
@@ -493,8 +575,9 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             pa.rows_per_cta = R;
             pa.p = p;
             pa.mu = mu;
-            pa.slot = d_slot;
+            pa.stat = d_stat;
             pa.cand = d_cand;
+            FM_CUDA_TRY(cudaMemsetAsync(d_stat, 0, sizeof(int) * (size_t)w * sms, s));
             pa.piv_row = d_piv;
             pa.n_piv = d_npiv;
             pa.bar = d_bar;
