@@ -458,45 +458,75 @@ __global__ void swap_pairs_kernel(uint32_t* A, int lt, int64_t n, const int* __r
 
 // X <- L11^-1 (k x k, k <= 128), L11 the unit lower triangle of rows
 // [r0, r0+k) x columns [c0, c0+k); X is written to the Morton-hybrid matrix Xm
-// (zero above the diagonal, ones on it). Row i of X follows from the rows above
-// it, X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j); eight lanes share each
-// column's sum (64-bit accumulation: raw products below p^2 < 2^32 when
-// p < 2^16, products reduced mod p otherwise).
+// (zero above the diagonal, ones on it). Blocked in 32 x 32 blocks (the
+// identity pads k to a multiple of 32): one warp inverts each diagonal block
+// row by row (X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j)); then block row bi
+// follows from the rows above it, X(bi, bj) = -X(bi, bi) sum_{bj <= m < bi}
+// L(bi, m) X(m, bj), for all bj at once. Sums accumulate in 64 bits: raw
+// products below p^2 < 2^32 when p < 2^16, products reduced mod p otherwise.
 constexpr int kInvThreads = 1024;
+
+__device__ __forceinline__ uint64_t mac_p(uint64_t acc, uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
+{
+    return acc + (p < 65536u ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
+}
+
+__device__ __forceinline__ uint32_t neg_mod(uint64_t acc, uint32_t p)
+{
+    const uint32_t r = (uint32_t)(acc % p);
+    return r == 0 ? 0u : p - r;
+}
 
 __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                               int k, uint32_t* X, int xlt, uint32_t p,
                                                               uint64_t mu)
 {
     extern __shared__ uint32_t smx[];
-    uint32_t* L = smx;                  // [k][k], strictly lower part
-    uint32_t* Xs = smx + (size_t)k * k;  // [k][k]
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        const int i = e / k, t = e % k;
-        L[e] = t < i ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
+    constexpr int K = kNb;                 // padded size, 4 blocks of 32
+    uint32_t* L = smx;                     // [K][K], strictly lower part
+    uint32_t* Xs = smx + (size_t)K * K;    // [K][K]
+    uint32_t* T = Xs + (size_t)K * K;      // [3][32][32]
+    const int nb = (k + 31) / 32;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int i = e / K, t = e % K;
+        L[e] = (t < i && i < k) ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
         Xs[e] = i == t ? 1u : 0u;
     }
     __syncthreads();
-    const int j = threadIdx.x >> 3, q = threadIdx.x & 7;
-    for (int i = 1; i < k; ++i) {
-        uint64_t acc = 0;
-        if (j < i) {
-            if (p < 65536u)
-                for (int t = j + q; t < i; t += 8) acc += (uint64_t)L[i * k + t] * Xs[t * k + j];
-            else
-                for (int t = j + q; t < i; t += 8) acc += mulmod(L[i * k + t], Xs[t * k + j], p, mu);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // 1. the diagonal blocks, one warp each
+    if (warp < nb) {
+        const int base = 32 * warp, j = base + lane;
+        for (int r = 1; r < 32; ++r) {
+            const int i = base + r;
+            if (lane < r) {
+                uint64_t acc = 0;
+                for (int t = j; t < i; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + j], p, mu);
+                Xs[i * K + j] = neg_mod(acc, p);
+            }
+            __syncwarp();
         }
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
-        if (j < i && q == 0) {
-            const uint32_t r = (uint32_t)(acc % p);
-            Xs[i * k + j] = r == 0 ? 0u : p - r;
+    }
+    __syncthreads();
+    // 2. block rows below the first: thread (r, c) = (warp, lane) of each 32 x 32 block
+    for (int bi = 1; bi < nb; ++bi) {
+        const int i = 32 * bi + warp;
+        for (int bj = 0; bj < bi; ++bj) {
+            uint64_t acc = 0;
+            for (int t = 32 * bj; t < 32 * bi; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + 32 * bj + lane], p, mu);
+            T[(bj * 32 + warp) * 32 + lane] = (uint32_t)(acc % p);
+        }
+        __syncthreads();
+        for (int bj = 0; bj < bi; ++bj) {
+            uint64_t acc = 0;
+            for (int s2 = 0; s2 < 32; ++s2)
+                acc = mac_p(acc, Xs[i * K + 32 * bi + s2], T[(bj * 32 + s2) * 32 + lane], p, mu);
+            Xs[i * K + 32 * bj + lane] = neg_mod(acc, p);
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < k * k; e += blockDim.x)
-        X[fm_encode((uint64_t)(e / k), (uint64_t)(e % k), xlt)] = Xs[e];
+        X[fm_encode((uint64_t)(e / k), (uint64_t)(e % k), xlt)] = Xs[(e / k) * K + (e % k)];
 }
 
 }  // namespace
@@ -684,7 +714,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 // limb planes split from A12 before A12 is written)
                 uint32_t* xs = static_cast<uint32_t*>(fm_workspace(4, (size_t)kNb * kNb * 4));
                 if (!xs) return FM_ENOMEM;
-                const size_t ismem = (size_t)2 * k * k * 4;
+                const size_t ismem = ((size_t)2 * kNb * kNb + 3 * 32 * 32) * 4;
                 FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)ismem));
                 tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
