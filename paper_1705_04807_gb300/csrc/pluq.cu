@@ -26,6 +26,7 @@
 // is bounded: a wait that expires raises FM_ETIMEOUT and every CTA leaves the
 // kernel.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <unordered_map>
 #include <vector>
@@ -262,9 +263,11 @@ struct SmemPanelArgs {
     int rows_per_cta;  // R: CTA b owns rows [r0 + b R, r0 + (b+1) R) of the panel
     uint32_t p;
     uint64_t mu;
-    int* stat;         // [w][gridDim.x], zeroed: 0 = not yet published, 1 = no
-                       // candidate, 2 + i = candidate is this CTA's row i
-    uint32_t* cand;    // [w][gridDim.x][w + 2]: candidate row values, inverse, row
+    uint2* stat;       // [w][gridDim.x] (code, tag): code 1 = no candidate,
+                       // 2 + i = candidate is this CTA's row i
+    uint2* cand;       // [w][gridDim.x][w + 2] (value, tag): candidate row values,
+                       // inverse, global row index
+    uint32_t tag0;     // tags of this launch: tag0 + t for column t (never reused)
     int* piv_row;      // out [w]: pivot row of column t (original index) or -1
     int* n_piv;        // out
     unsigned* bar;
@@ -283,16 +286,45 @@ __device__ __forceinline__ uint32_t mul_p(uint32_t a, uint32_t b, uint32_t p, ui
     return mulmod(a, b, p, mu);
 }
 
-__device__ __forceinline__ void st_release_gpu(int* p, int v)
+// Published words are (value, tag) pairs written by one aligned 64-bit store and
+// read by one 64-bit load (single-copy atomic), so a reader that sees the tag it
+// expects also sees the value: no fences, no clearing between launches.
+__device__ __forceinline__ void put_tagged(uint2* p, uint32_t v, uint32_t tag)
 {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v), "r"(tag) : "memory");
 }
 
-__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+__device__ __forceinline__ uint2 get_tagged(const uint2* p)
 {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+    uint2 r;
+    asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p) : "memory");
+    return r;
+}
+
+// Waits (bounded) until *p carries the tag; false if the wait expired or
+// *abort became non-zero.
+__device__ __forceinline__ bool wait_tagged(const uint2* p, uint32_t tag, uint32_t* v, int* status,
+                                            volatile int* abort)
+{
+    uint2 r = get_tagged(p);
+    if (r.y == tag) {
+        *v = r.x;
+        return true;
+    }
+    const uint64_t t0 = fm_globaltimer();
+    while (true) {
+        r = get_tagged(p);
+        if (r.y == tag) {
+            *v = r.x;
+            return true;
+        }
+        if (*abort) return false;
+        if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
+            fm_raise(status, FM_ETIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
 }
 
 // Panel factorisation with the panel rows resident in shared memory. CTA b owns
@@ -305,9 +337,10 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p)
 // own non-pivot rows. The CTA that owns the pivot reads only lower-numbered
 // CTAs' status words (already published: they have no candidate) and uses its
 // own row, so it runs at its own pace; there is no grid-wide barrier per
-// column. A CTA publishes column t before it reads anything of column t, so the
-// waits form no cycle. Rows are not moved; the pivot order is returned. Every
-// wait is bounded.
+// column. Every published word is tagged with the launch and column, so no
+// fence orders it. A CTA publishes column t before it reads anything of column
+// t, so the waits form no cycle. Rows are not moved; the pivot order is
+// returned. Every wait is bounded.
 __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const SmemPanelArgs a)
 {
     extern __shared__ uint32_t sm[];
@@ -317,8 +350,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
     int* piv_flag = reinterpret_cast<int*>(prow + kNb);    // [R]
     uint32_t* lbuf = reinterpret_cast<uint32_t*>(piv_flag + R);  // [R] multipliers
     const uint32_t mu32 = (uint32_t)(0x100000000ull / a.p);
-    __shared__ int s_abort, s_first, s_owner, s_code;
-    __shared__ uint32_t s_inv, s_myinv;
+    __shared__ int s_abort, s_first, s_owner;
+    __shared__ uint32_t s_myinv;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = a.r0 + (int64_t)blockIdx.x * R;
     const int64_t left = a.m - row0;
@@ -330,46 +363,53 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
     }
     for (int i = tid; i < R; i += kPanelThreads) piv_flag[i] = 0;
     __syncthreads();
+    if (tid == 0) s_first = INT_MAX;
+    __syncthreads();
     int found = 0;
     for (int t = 0; t < w; ++t) {
         // 1. this CTA's candidate: first non-pivot row with a nonzero in column t
-        if (tid == 0) s_first = INT_MAX;
-        __syncthreads();
+        // (s_first was reset after the previous column's publication)
         for (int i = tid; i < nrows; i += kPanelThreads)
             if (!piv_flag[i] && rows[(size_t)i * w + t] != 0) atomicMin(&s_first, i);
         __syncthreads();
         const int li = s_first;
         const int mycode = li != INT_MAX ? 2 + li : 1;
-        // warp 0 publishes: the candidate row, then (ordered after the warp's
-        // writes by __syncwarp, and cumulative) one release store of the status
+        const uint32_t tag = a.tag0 + (uint32_t)t;
+        // warp 0 publishes the candidate row, its inverse and row index, then the
+        // status word, all tagged
         if (warp == 0) {
             if (li != INT_MAX) {
-                uint32_t* cbuf = a.cand + ((size_t)t * P + blockIdx.x) * (w + 2);
-                for (int c = lane; c < w; c += 32) cbuf[c] = rows[(size_t)li * w + c];
+                uint2* cbuf = a.cand + ((size_t)t * P + blockIdx.x) * (w + 2);
+                for (int c = lane; c < w; c += 32) put_tagged(cbuf + c, rows[(size_t)li * w + c], tag);
                 if (lane == 0) {
                     s_myinv = inv_euclid(rows[(size_t)li * w + t], a.p);
-                    cbuf[w] = s_myinv;
-                    cbuf[w + 1] = (uint32_t)(row0 + li);
+                    put_tagged(cbuf + w, s_myinv, tag);
+                    put_tagged(cbuf + w + 1, (uint32_t)(row0 + li), tag);
                 }
             }
-            __syncwarp();
             if (lane == 0) {
-                st_release_gpu(&a.stat[(size_t)t * P + blockIdx.x], mycode);
+                put_tagged(&a.stat[(size_t)t * P + blockIdx.x], (uint32_t)mycode, tag);
                 s_owner = INT_MAX;
             }
         }
         __syncthreads();
+        if (tid == 0) s_first = INT_MAX;  // every thread holds li by now
         // 2. find the first CTA with a candidate: thread b reads CTA b's status
         // word, all at once (only lower CTAs when this one has a candidate); a
         // thread stops as soon as a lower CTA is known to have one, so only CTAs
         // up to the owner are waited for
         const int limit = mycode >= 2 ? (int)blockIdx.x + 1 : P;
         for (int b = tid; b < limit; b += kPanelThreads) {
-            int code = b == (int)blockIdx.x ? mycode : 0;
+            uint32_t code = b == (int)blockIdx.x ? (uint32_t)mycode : 0u;
             if (code == 0) {
-                const int* sp = &a.stat[(size_t)t * P + b];
+                const uint2* sp = &a.stat[(size_t)t * P + b];
                 const uint64_t t0 = fm_globaltimer();
-                while ((code = ld_acquire_gpu(sp)) == 0) {
+                while (true) {
+                    const uint2 r = get_tagged(sp);
+                    if (r.y == tag) {
+                        code = r.x;
+                        break;
+                    }
                     if (*(volatile int*)&s_owner < b || s_abort) break;
                     if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
                         fm_raise(a.status, FM_ETIMEOUT);
@@ -382,38 +422,45 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
         }
         __syncthreads();
         if (s_abort) return;
-        if (tid == 0) {
-            const int o = s_owner;
-            s_code = o == INT_MAX ? 0 : (o == (int)blockIdx.x ? mycode : __ldcg(&a.stat[(size_t)t * P + o]));
-            if (o == INT_MAX) s_owner = -1;
-        }
-        __syncthreads();
-        const int owner = s_owner;
+        const int owner = s_owner == INT_MAX ? -1 : s_owner;
         if (owner < 0) {  // no nonzero left in this column: a non-pivot column
             if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = -1;
             continue;
         }
-        // 3. the pivot row: this CTA's own row, or the owner's published copy
+        // 3. the pivot row (this CTA's own row, or the owner's published copy) and
+        // its inverse; every thread takes the inverse itself
+        uint32_t inv;
         if (owner == (int)blockIdx.x) {
             for (int c = tid; c < w; c += kPanelThreads) prow[c] = rows[(size_t)li * w + c];
+            inv = s_myinv;
             if (tid == 0) {
-                s_inv = s_myinv;
                 piv_flag[li] = 1;
+                if (blockIdx.x == 0) a.piv_row[t] = (int)(row0 + li);
             }
         } else {
-            const uint32_t* ob = a.cand + ((size_t)t * P + owner) * (w + 2);
-            for (int c = tid; c < w; c += kPanelThreads) prow[c] = __ldcg(ob + c);
-            if (tid == 0) s_inv = __ldcg(ob + w);
+            const uint2* ob = a.cand + ((size_t)t * P + owner) * (w + 2);
+            for (int c = tid; c < w; c += kPanelThreads) {
+                uint32_t v = 0;
+                wait_tagged(ob + c, tag, &v, a.status, &s_abort);
+                prow[c] = v;
+            }
+            wait_tagged(ob + w, tag, &inv, a.status, &s_abort);
+            if (blockIdx.x == 0 && tid == 0) {
+                uint32_t g = 0;
+                wait_tagged(ob + w + 1, tag, &g, a.status, &s_abort);
+                a.piv_row[t] = (int)g;
+            }
         }
-        if (blockIdx.x == 0 && tid == 0) a.piv_row[t] = (int)(a.r0 + (int64_t)owner * R + (s_code - 2));
-        __syncthreads();
-        const uint32_t inv = s_inv;
         // 4. the multipliers l_i (column t) of all non-pivot rows at once, then
         // a_i <- a_i - l_i * pivot row on columns > t (warps over rows, lanes
         // over columns); l_i is kept in column t
         for (int i = tid; i < nrows; i += kPanelThreads)
-            lbuf[i] = piv_flag[i] ? 0u : mul_p(rows[(size_t)i * w + t], inv, a.p, mu32, a.mu);
+            if (i != li || owner != (int)blockIdx.x)
+                lbuf[i] = piv_flag[i] ? 0u : mul_p(rows[(size_t)i * w + t], inv, a.p, mu32, a.mu);
+            else
+                lbuf[i] = 0u;
         __syncthreads();
+        if (s_abort) return;
         for (int i = warp; i < nrows; i += kPanelThreads / 32) {
             const uint32_t l = lbuf[i];
             if (l == 0) continue;
@@ -430,6 +477,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) smem_panel_kernel(const Smem
         a.A[fm_encode((uint64_t)(row0 + i), (uint64_t)(a.c0 + c), a.lt)] = rows[e];
     }
     if (blockIdx.x == 0 && tid == 0) *a.n_piv = found;
+}
+
+// Tags of a panel launch: 256 fresh values (one per column), never zero (the
+// slots are cleared at every fm_pluq call; the counter wraps after 2^24 launches).
+uint32_t next_tags()
+{
+    static std::atomic<uint32_t> counter{1};
+    return counter.fetch_add(256u);
 }
 
 // Row swaps (pairs (x, y) in order) on columns [0, n) and on the permutation.
@@ -560,7 +615,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     FM_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (!coop) return FM_EUNSUPPORTED;
     const int sms = fm_sm_count();
-    const size_t ws_ints = 3 * kNb + 4 + 2 * kNb + (size_t)kNb * sms * (kNb + 2) + (size_t)kNb * sms;
+    const size_t ws_ints = 3 * kNb + 4 + 2 * kNb + 2 * ((size_t)kNb * sms * (kNb + 2) + (size_t)kNb * sms);
     int* ws = static_cast<int*>(fm_workspace(1, sizeof(int) * ws_ints));
     if (!ws) return FM_ENOMEM;
     int* d_slot = ws;
@@ -569,8 +624,10 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     int* d_npiv = ws + 3 * kNb;
     unsigned* d_bar = reinterpret_cast<unsigned*>(ws + 3 * kNb + 2);
     int* d_pairs = ws + 3 * kNb + 4;
-    uint32_t* d_cand = reinterpret_cast<uint32_t*>(ws + 5 * kNb + 4);
-    int* d_stat = ws + 5 * kNb + 4 + (size_t)kNb * sms * (kNb + 2);
+    // tagged candidate slots and status words (8-byte aligned: 5 kNb + 4 ints in)
+    uint2* d_cand = reinterpret_cast<uint2*>(ws + 5 * kNb + 4);
+    uint2* d_stat = d_cand + (size_t)kNb * sms * (kNb + 2);
+    FM_CUDA_TRY(cudaMemsetAsync(d_cand, 0, sizeof(uint2) * ((size_t)kNb * sms * (kNb + 2) + (size_t)kNb * sms), s));
     FM_CUDA_TRY(cudaMemsetAsync(d_bar, 0, 2 * sizeof(unsigned), s));
 
     FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, kPanelThreads, 0));
@@ -607,7 +664,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             pa.mu = mu;
             pa.stat = d_stat;
             pa.cand = d_cand;
-            FM_CUDA_TRY(cudaMemsetAsync(d_stat, 0, sizeof(int) * (size_t)w * sms, s));
+            pa.tag0 = next_tags();
             pa.piv_row = d_piv;
             pa.n_piv = d_npiv;
             pa.bar = d_bar;
