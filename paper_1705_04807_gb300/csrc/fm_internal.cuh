@@ -359,49 +359,12 @@ __device__ __forceinline__ uint32_t fm_mapa(uint32_t saddr, uint32_t rank)
     return d;
 }
 
-// Arrive on an mbarrier of any CTA of the cluster (release at cluster scope).
-__device__ __forceinline__ void fm_mbar_arrive_cluster(uint32_t cluster_addr)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-                 : "memory");
-}
-
 // Arrive on an mbarrier of any CTA of the cluster with the default (CTA-scope
 // release) semantics: orders this thread's tcgen05 work fenced before it, not
 // its global stores, so it costs no cluster-wide fence.
 __device__ __forceinline__ void fm_mbar_arrive_remote(uint32_t cluster_addr)
 {
     asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-__device__ __forceinline__ bool fm_mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(fm_smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait with cluster-scope acquire (arrivals may come from the peer CTA).
-__device__ __forceinline__ bool fm_mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* status,
-                                                     volatile int* abort)
-{
-    if (fm_mbar_try_wait_cluster(bar, parity)) return true;
-    const uint64_t t0 = fm_globaltimer();
-    while (true) {
-        if (fm_mbar_try_wait_cluster(bar, parity)) return true;
-        if (abort && *abort) return false;
-        if (fm_globaltimer() - t0 > FM_WAIT_LIMIT_NS) {
-            fm_raise(status, FM_ETIMEOUT);
-            if (abort) *abort = 1;
-            return false;
-        }
-    }
 }
 
 __device__ __forceinline__ void fm_cluster_sync()

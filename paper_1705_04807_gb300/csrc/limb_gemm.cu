@@ -5,22 +5,28 @@
 // over the limb products k: (i, j) with weight 256^(i+j) mod p, or, for two
 // limbs, the three Karatsuba products A0B0, (A0+A1)(B0+B1), A1B1 with weights
 // (1-256), 256, (2^16-256) mod p. Every limb product is an integer GEMM whose
-// entries are at most 2^14 (2^16 for the Karatsuba middle product) in
+// entries are at most 2^14 (255^2 for the Karatsuba middle product) in
 // magnitude. sm_103a's tcgen05 has no integer MMA kind, so the limbs are carried
 // exactly as FP16 values through tcgen05.mma kind::f16 with FP32 accumulation in
 // tensor memory. FP32 holds every integer of magnitude <= 2^24 exactly, so K is
 // cut into chunks small enough that no partial sum can leave that range, and
 // each chunk's accumulator is drained into exact integers.
 //
-// One 128 x BN output tile per CTA: a producer warp (one 1-D bulk copy per
-// operand per 64-wide K stage), an MMA warp (tcgen05.mma into TMEM, two
-// accumulators alternating between jobs = (limb product, K chunk)) and eight
-// epilogue warps that drain each chunk with tcgen05.ld / st. Fold form
-// (p < 2^16): the running residue is folded back into the FP32 accumulator, with
-// an exact FP32 reduction between chunks of one product and a weight change at
-// product boundaries. Residue form (any p < 2^31): an exact int32 sum per
-// product, folded into a residue region of TMEM once per product. The final
-// residue is combined with C (set / add / subtract) in the Morton-hybrid layout.
+// Persistent kernel, one CTA per SM walking 128 x BN output tiles: a producer
+// warp (one 1-D bulk copy per operand per 64-wide K stage, only the rows and
+// columns the tile uses), an MMA warp (tcgen05.mma into TMEM, two accumulators
+// alternating between jobs = (limb product, K chunk), N = the tile's columns
+// rounded to 16) and eight epilogue warps that drain each chunk with
+// tcgen05.ld / st. Fold form (p < 2^16): the running residue is folded back into
+// the FP32 accumulator, with an exact FP32 reduction between chunks of one
+// product and a weight change at product boundaries, in packed FP32. Residue
+// form (any p < 2^31): an exact int32 sum per product, folded into a residue
+// region of TMEM once per product. The final residue is combined with C (set /
+// add / subtract) in the Morton-hybrid layout; C's lines are prefetched into L2
+// when the tile starts. The same kernel runs one call (fields in the kernel
+// arguments) or a batch (a call table and a tile list), on f16 limb planes or on
+// E4M3 0/1 planes for GF(2) (kind::f8f6f4, parity bits written to a bit-packed
+// C). A CTA-pair variant (cta_group::2) computes 256 x 256 tiles.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -107,34 +113,8 @@ struct LimbGemmArgs {
 constexpr float kRoundBias = 12582912.0f;  // 1.5 * 2^23
 constexpr uint32_t kRoundBiasBits = 0x4B400000u;
 
-__device__ __forceinline__ float fold_round(float f, float invp, float pf)
-{
-    const float q = __fsub_rn(__fmaf_rn(f, invp, kRoundBias), kRoundBias);
-    return __fmaf_rn(-q, pf, f);
-}
-
-// The same-product drain is the drain that runs most often (the Karatsuba
-// middle product's 256-deep chunks): it uses Blackwell's packed FP32 arithmetic,
-// two accumulator values per instruction (each lane rounded exactly as the
-// scalar fold_round does), halving its instruction issue.
-__device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
-{
-    const uint64_t ip = (uint64_t)__float_as_uint(invp) * 0x100000001ull;
-    const uint64_t bs = (uint64_t)__float_as_uint(kRoundBias) * 0x100000001ull;
-    const uint64_t np = (uint64_t)__float_as_uint(-pf) * 0x100000001ull;
-#pragma unroll
-    for (int e = 0; e < 32; e += 2)
-        asm("{\n\t.reg .b64 x, t, q;\n\t"
-            "mov.b64 x, {%0, %1};\n\t"
-            "fma.rn.f32x2 t, x, %2, %3;\n\t"   // v / p + 1.5 * 2^23
-            "sub.rn.f32x2 q, t, %3;\n\t"       // round(v / p)
-            "fma.rn.f32x2 x, q, %4, x;\n\t"    // v - round(v / p) p
-            "mov.b64 {%0, %1}, x;\n\t}"
-            : "+r"(v[e]), "+r"(v[e + 1])
-            : "l"(ip), "l"(bs), "l"(np));
-}
-
-// Packed FP32 helpers: two lanes per instruction, each rounded as the scalar op.
+// Packed FP32 helpers (fma/sub/mul .f32x2): two lanes per instruction, each
+// rounded as the scalar FP32 operation. f2_fold: x - round(x / p) p per lane.
 __device__ __forceinline__ uint64_t f2_fold(uint64_t x, uint64_t ip, uint64_t bs, uint64_t np)
 {
     uint64_t r;
@@ -164,6 +144,21 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
 __device__ __forceinline__ uint64_t f2_splat(float f)
 {
     return (uint64_t)__float_as_uint(f) * 0x100000001ull;
+}
+
+// The same-product drain is the drain that runs most often (the Karatsuba
+// middle product's 256-deep chunks): like every drain it uses Blackwell's
+// packed FP32 arithmetic, two accumulator values per instruction, which halves
+// its instruction issue.
+__device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
+{
+    const uint64_t ip = f2_splat(invp), bs = f2_splat(kRoundBias), np = f2_splat(-pf);
+#pragma unroll
+    for (int e = 0; e < 32; e += 2) {
+        const uint64_t x = f2_fold(((uint64_t)v[e + 1] << 32) | v[e], ip, bs, np);
+        v[e] = (uint32_t)x;
+        v[e + 1] = (uint32_t)(x >> 32);
+    }
 }
 
 // Product-boundary and final drains: x = v folded (|x| <= 3p/4, since the
