@@ -233,9 +233,11 @@ def run_reference(args, world, rank):
 def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5):
     """The batching form: count independent calls C_c -= A_c * B_c mod p with
     M, N, K uniform in [lo, hi], each on its own cell of a large Morton C and
-    on random rectangles of shared Morton A and B (T' = 64). One persistent
-    launch (fm_gemm_modp_batched) against one fm_gemm_modp launch per call;
-    both results are checked equal."""
+    on random rectangles of shared Morton A and B (T' = 64). The batch as one
+    tensor-core limb plan (limb planes of every call: 3 launches; and the
+    fused form: 1 launch) and as one decomposed plain plan (1 persistent
+    launch), against one fm_gemm_modp launch per call; every result is checked
+    equal. The roofline is HBM: each call's A, B and C read and C written once."""
     import numpy as np
 
     import fm_inputs
@@ -262,8 +264,10 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
     offs = fm_inputs.raw_u64(seed, 4 * count, 9).reshape(count, 4)
     calls = []
     ops = 0.0
+    algo_bytes = 0.0  # each call reads A, B and C and writes C once (4-byte residues)
     for c in range(count):
         M, N, K = (int(x) for x in shapes[c])
+        algo_bytes += 4.0 * (M * K + K * N + 2 * M * N)
         call = fm.fm_gemm_call()
         call.C = fm.sub(mC, (c // cells) * cell, (c % cells) * cell, M, N)
         call.A = fm.sub(mA, int(offs[c, 0]) % (big - M + 1), int(offs[c, 1]) % (big - K + 1), M, K)
@@ -292,25 +296,31 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
     torch.cuda.synchronize()
     same = bool(torch.equal(tC, per_call_result))
     del per_call_result
-    # the same batch in the tensor-core limb form: 3 launches for all calls
+    # the same batch in the tensor-core limb form: limb planes of every call
+    # (3 launches), and the fused form (1 launch, operands split on the fly)
     plain_result = tC.clone()
-    lplan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC)
-    tC.copy_(snap)
-    lplan.run(stream)
-    torch.cuda.synchronize()
-    limb_same = bool(torch.equal(tC, plain_result))
+
+    def limb_plan(fused):
+        lplan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=fused))
+        tC.copy_(snap)
+        lplan.run(stream)
+        torch.cuda.synchronize()
+        same_ = bool(torch.equal(tC, plain_result))
+        for _ in range(2):
+            lplan.run(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            lplan.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res = (e0.elapsed_time(e1) / reps, lplan.work_items, lplan.launches, same_)
+        lplan.close()
+        return res
+
+    limb_ms, limb_tiles, limb_launches, limb_same = limb_plan(0)
+    fused_ms, fused_tiles, fused_launches, fused_same = limb_plan(1)
     del plain_result
-    for _ in range(2):
-        lplan.run(stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        lplan.run(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    limb_ms = e0.elapsed_time(e1) / reps
-    limb_tiles = lplan.work_items
-    lplan.close()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(reps):
@@ -322,10 +332,20 @@ def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5)
     items = plan.work_items
     plan.close()
     del tA, tB, tC, snap
+    _, _, hbm_peak, peak_src = measured_peaks()
     return {"workload": f"{count} calls C -= A*B mod {p}, M,N,K ~ U[{lo},{hi}], T'=64, "
                         f"one tensor-core limb plan (planes of every call in one workspace)",
-            "value": ops / (limb_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": limb_ms, "launches": 3,
+            "value": ops / (limb_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": limb_ms, "launches": limb_launches,
             "output_tiles": limb_tiles, "bit_identical_to_plain_batched": limb_same,
+            "roofline": {"bound": "hbm", "achieved": algo_bytes / (limb_ms / 1e3) / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": algo_bytes / (limb_ms / 1e3) / 1e9 / hbm_peak,
+                         "per_call_frac": algo_bytes / (per_call_ms / 1e3) / 1e9 / hbm_peak,
+                         "work": "algorithmic bytes: A, B, C read and C written once per call, 4 B each "
+                                 f"({algo_bytes / 1e9:.3f} GB)", "peak_source": f"HBM copy, {peak_src}"},
+            "fused": {"workload": "the same calls as one fused launch (operands split into limbs on the fly)",
+                      "value": ops / (fused_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": fused_ms,
+                      "launches": fused_launches, "output_tiles": fused_tiles,
+                      "bit_identical_to_plain_batched": fused_same},
             "per_call_ms": per_call_ms, "per_call_value": ops / (per_call_ms / 1e3) / 1e9,
             "speedup_vs_per_call": per_call_ms / limb_ms, "per_call_launches": count,
             "plain": {"workload": "the same calls as one decomposed plan (plain form, one persistent launch)",

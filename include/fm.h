@@ -91,7 +91,11 @@ typedef struct fm_opts {
     int32_t cta_pair;       /* limb form, block_n 256, p < 2^16: 1 = a CTA pair
                                (cta_group::2) per 256 x 256 output tile instead
                                of one CTA per 128 x 256 tile                    */
-    int32_t reserved[4];
+    int32_t fused_batch;    /* limb batches: 1 = ONE launch that splits the
+                               operands into limbs on the fly, instead of limb
+                               planes of every call in a workspace and three
+                               launches (Karatsuba form, block_n 128, T' >= 8) */
+    int32_t reserved[3];
 } fm_opts;
 
 /* ---- layout and permutation (Sec. 1; HBM-bound gathers) ---------------- */
@@ -248,21 +252,34 @@ typedef struct fm_plan fm_plan;
  *     them into one work list and uploads it.
  *   FM_ALGO_LIMB_TC: the tensor-core limb form for the whole batch (any T'):
  *     limb planes for every call's operands in one workspace (cached in the
- *     plan); opts as for fm_gemm_modp except cta_pair (FM_EUNSUPPORTED). */
+ *     plan). With opts->fused_batch == 1, the two-limb Karatsuba form (odd
+ *     p < 2^16, block_n 128, the default for batches) and every A and B with
+ *     8 <= T', at most 2^32 entries and a 16-byte aligned base, the batch is
+ *     FUSED instead: one launch that splits the operands into limbs on the
+ *     fly (FM_EUNSUPPORTED when the batch does not qualify). opts as for
+ *     fm_gemm_modp except cta_pair (FM_EUNSUPPORTED). */
 int fm_plan_create(fm_plan** plan, const fm_gemm_call* calls, int64_t n, uint32_t p,
                    int32_t algo, const fm_opts* opts);
 
 /* Runs every call of the plan on stream. Decomposed forms: ONE persistent
- * kernel launch whose CTAs pull work items from a device queue. Limb form:
- * three launches for the whole batch (limb split of every A, of every B, and
- * one persistent GEMM over the output tiles of every call, longest first),
- * plus one small launch per call with K = 0 under FM_OP_SET. May be captured
- * in a CUDA graph; the plan must outlive the graph. */
+ * kernel launch whose CTAs pull work items from a device queue. Fused limb
+ * form: ONE persistent launch over the 128 x 128 output tiles of every call
+ * (longest calls first, a call's tiles adjacent). Limb form with planes: three
+ * launches (limb split of every A, of every B, and one persistent GEMM over
+ * the output tiles of every call, longest first). Limb forms add one small
+ * launch per call with K = 0 under FM_OP_SET. May be captured in a CUDA
+ * graph; the plan must outlive the graph. */
 int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream);
 
 /* Work items (decomposed forms: base-case tile products; limb form: output
  * tiles) of the plan (host). */
 int64_t fm_plan_work_items(const fm_plan* plan);
+
+/* Kernel launches of this library in one fm_gemm_modp_batched run of the plan
+ * (host): 1 for the decomposed forms and for a fused limb batch, 3 for a limb
+ * batch with limb planes in a workspace, plus one per K = 0 call under
+ * FM_OP_SET. */
+int64_t fm_plan_launches(const fm_plan* plan);
 
 int fm_plan_destroy(fm_plan* plan);
 

@@ -449,8 +449,9 @@ extern "C" int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream)
 {
     FmRange range("fm_gemm_modp_batched");
     if (!plan) return FM_EINVAL;
-    fm_trace("gemm_modp_batched %s work items=%lld", plan->limb ? "tensor-core" : "decomposed",
-             (long long)plan->n_items);
+    fm_trace("gemm_modp_batched %s work items=%lld launches=%lld",
+             plan->limb ? "tensor-core" : "decomposed", (long long)plan->n_items,
+             (long long)fm_plan_launches(plan));
     if (plan->limb) {
         for (const fm_gemm_call& g : fm_limb_batch_zero_calls(plan->limb))
             if (g.op == FM_OP_SET) FM_TRY(fm_gemm_modp(g.C, g.A, g.B, plan->p, g.op, FM_ALGO_LIMB_TC, nullptr, stream));
@@ -471,6 +472,17 @@ extern "C" int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream)
 extern "C" int64_t fm_plan_work_items(const fm_plan* plan)
 {
     return plan ? plan->n_items : FM_EINVAL;
+}
+
+extern "C" int64_t fm_plan_launches(const fm_plan* plan)
+{
+    if (!plan) return FM_EINVAL;
+    if (plan->limb) {
+        int64_t n = fm_limb_batch_launches(plan->limb);
+        for (const fm_gemm_call& g : fm_limb_batch_zero_calls(plan->limb)) n += g.op == FM_OP_SET ? 1 : 0;
+        return n;
+    }
+    return plan->n_items > 0 ? 1 : 0;
 }
 
 extern "C" int fm_plan_destroy(fm_plan* plan)

@@ -74,8 +74,19 @@ int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const
                          FmLimbBatch** out);
 int fm_limb_batch_run(FmLimbBatch* b, int* status, cudaStream_t s);
 int64_t fm_limb_batch_tiles(const FmLimbBatch* b);
+int fm_limb_batch_launches(const FmLimbBatch* b);  // per run, excluding zero_calls
 const std::vector<fm_gemm_call>& fm_limb_batch_zero_calls(const FmLimbBatch* b);
 void fm_limb_batch_destroy(FmLimbBatch* b);
+// Fused limb batches (limb_fused.cu): the two-limb Karatsuba fold form (plan q:
+// w = 2, three products, block_n 128) in ONE launch that splits the operands
+// on the fly; FM_EUNSUPPORTED when q or an operand does not allow it (T' < 8,
+// a base not 16-byte aligned). Calls with K = 0 are skipped (the caller's).
+struct FmFusedBatch;
+int fm_fused_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const FmLimbPlan& q,
+                          FmFusedBatch** out);
+int fm_fused_batch_run(FmFusedBatch* b, int* status, cudaStream_t s);
+int64_t fm_fused_batch_tiles(const FmFusedBatch* b);
+void fm_fused_batch_destroy(FmFusedBatch* b);
 // GF(2) batches (gf2.cu splits; limb_gemm.cu plans and multiplies): the same
 // three launches on bit-packed operands (FmSplitDesc.lt carries log2_grid).
 int fm_gf2_batch_create(const fm_gf2_call* calls, int64_t n, const fm_opts* opts, FmLimbBatch** out);

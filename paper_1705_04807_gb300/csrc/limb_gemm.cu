@@ -36,6 +36,7 @@
 #include "fm_internal.cuh"
 #include "fm_kernels.h"
 #include "limb_common.cuh"
+#include "limb_drain.cuh"
 
 namespace {
 
@@ -43,31 +44,12 @@ using namespace fm_limb;
 constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 
-// ---- modular helpers --------------------------------------------------------
-__device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t p, uint32_t mu)
-{
-    const uint32_t q = __umulhi(x, mu);
-    uint32_t r = x - q * p;
-    return r >= p ? r - p : r;
-}
-
 __device__ __forceinline__ uint32_t barrett64(uint64_t t, uint32_t p, uint64_t mu)
 {
     const uint64_t q = __umul64hi(t, mu);
     uint64_t r = t - q * (uint64_t)p;
     while (r >= p) r -= p;
     return (uint32_t)r;
-}
-
-__device__ __forceinline__ uint32_t op_combine(uint32_t c, uint32_t s, uint32_t p, uint32_t mu32, int op)
-{
-    if (op == FM_OP_SET) return s;
-    const uint32_t cc = barrett32(c, p, mu32);  // C holds residues; any 32-bit value is reduced
-    if (op == FM_OP_ADD) {
-        const uint32_t r = cc + s;
-        return r >= p ? r - p : r;
-    }
-    return cc >= s ? cc - s : cc + (p - s);
 }
 
 // Per-call part of a limb GEMM: its limb planes, K stages and jobs, and its C
@@ -100,144 +82,6 @@ struct LimbGemmArgs {
     int* status;
 };
 
-// Fold-form drains. Every accumulator value v is an integer with |v| <= 2^24
-// and |v / p| < 2^22: for p > 4 because |v| <= 2^24, for p <= 4 because the
-// limbs are then below p in magnitude, so |v| <= 960 p^2 + 2p. In that range
-// round-to-nearest of v / p is one FMA with the constant 1.5 * 2^23 (the sum
-// lands where the float spacing is 1) and one subtraction, both on the FMA
-// pipe; conversions between small integers and floats use the same bias.
-// fold_fp: v - q p with q = the rounded quotient (within 3/4 of v / p, as 1/p
-// is rounded), exact, a carried value of magnitude <= 3p/4 < p.
-// fold_int: that value times mul mod p, as a float to carry on (to_float) or
-// as the final residue in [0, p).
-constexpr float kRoundBias = 12582912.0f;  // 1.5 * 2^23
-constexpr uint32_t kRoundBiasBits = 0x4B400000u;
-
-// Packed FP32 helpers (fma/sub/mul .f32x2): two lanes per instruction, each
-// rounded as the scalar FP32 operation. f2_fold: x - round(x / p) p per lane.
-__device__ __forceinline__ uint64_t f2_fold(uint64_t x, uint64_t ip, uint64_t bs, uint64_t np)
-{
-    uint64_t r;
-    asm("{\n\t.reg .b64 t, q;\n\t"
-        "fma.rn.f32x2 t, %1, %2, %3;\n\t"
-        "sub.rn.f32x2 q, t, %3;\n\t"
-        "fma.rn.f32x2 %0, q, %4, %1;\n\t}"
-        : "=l"(r)
-        : "l"(x), "l"(ip), "l"(bs), "l"(np));
-    return r;
-}
-
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-__device__ __forceinline__ uint64_t f2_splat(float f)
-{
-    return (uint64_t)__float_as_uint(f) * 0x100000001ull;
-}
-
-// The same-product drain is the drain that runs most often (the Karatsuba
-// middle product's 256-deep chunks): like every drain it uses Blackwell's
-// packed FP32 arithmetic, two accumulator values per instruction, which halves
-// its instruction issue.
-__device__ __forceinline__ void fold_fp(uint32_t (&v)[32], float invp, float pf)
-{
-    const uint64_t ip = f2_splat(invp), bs = f2_splat(kRoundBias), np = f2_splat(-pf);
-#pragma unroll
-    for (int e = 0; e < 32; e += 2) {
-        const uint64_t x = f2_fold(((uint64_t)v[e + 1] << 32) | v[e], ip, bs, np);
-        v[e] = (uint32_t)x;
-        v[e + 1] = (uint32_t)(x >> 32);
-    }
-}
-
-// Product-boundary and final drains: x = v folded (|x| <= 3p/4, since the
-// rounded quotient is off by at most 3/4), then x * mul mod p in exact FP32
-// steps with mul = 256 c1 + c0 (c0, c1 < 256): x c0 and x c1 are below 2^24 in
-// magnitude and are folded, and r0 + 256 r1 (at most 257 * 3p/4 < 2^24) is
-// folded once more. The result, a value in (-p, p), is carried on as a float
-// (to_float) or converted to the residue in [0, p) through the same bias.
-__device__ __forceinline__ void fold_int(uint32_t (&v)[32], uint32_t mul, bool to_float, uint32_t p,
-                                         float invp, float pf)
-{
-    const uint64_t ip = f2_splat(invp), bs = f2_splat(kRoundBias), np = f2_splat(-pf);
-    const uint64_t c0 = f2_splat((float)(mul & 255u)), c1 = f2_splat((float)(mul >> 8));
-    const uint64_t k256 = f2_splat(256.0f);
-#pragma unroll
-    for (int e = 0; e < 32; e += 2) {
-        uint64_t x = ((uint64_t)v[e + 1] << 32) | v[e];
-        x = f2_fold(x, ip, bs, np);
-        const uint64_t r0 = f2_fold(f2_mul(x, c0), ip, bs, np);
-        const uint64_t r1 = f2_fold(f2_mul(x, c1), ip, bs, np);
-        const uint64_t y = f2_fold(f2_fma(r1, k256, r0), ip, bs, np);
-        uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
-        if (!to_float) {
-            int32_t a = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(y0), kRoundBias)) - kRoundBiasBits);
-            int32_t b = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(y1), kRoundBias)) - kRoundBiasBits);
-            y0 = (uint32_t)(a + (a < 0 ? (int32_t)p : 0));
-            y1 = (uint32_t)(b + (b < 0 ? (int32_t)p : 0));
-        }
-        v[e] = y0;
-        v[e + 1] = y1;
-    }
-}
-
-// C(gi, j0 .. j0+W-1) <- C op sres (mod p), in the Morton-hybrid layout. Loads
-// are issued before stores; a run inside one tile row moves as 16-byte vectors.
-template <int W>
-__device__ __forceinline__ void write_c_run(const LimbCall& c, uint32_t p, uint32_t mu32, int64_t gi, int64_t j0,
-                                            uint64_t cmask, const uint32_t (&sres)[W])
-{
-    const uint64_t ci = (uint64_t)(c.c_row0 + gi);
-    const uint64_t cj0 = (uint64_t)(c.c_col0 + j0);
-    const uint64_t base = fm_encode(ci, cj0, c.c_lt);
-    const bool run = j0 + W <= c.N && (cj0 & cmask) + W <= cmask + 1 && (base & 3) == 0;
-    if (run) {
-        uint4* dst = reinterpret_cast<uint4*>(c.C + base);
-        uint4 old[W / 4];
-        if (c.op != FM_OP_SET) {
-#pragma unroll
-            for (int q = 0; q < W / 4; ++q) old[q] = dst[q];
-        }
-#pragma unroll
-        for (int q = 0; q < W / 4; ++q) {
-            uint4 o = c.op != FM_OP_SET ? old[q] : make_uint4(0, 0, 0, 0);
-            o.x = op_combine(o.x, sres[4 * q + 0], p, mu32, c.op);
-            o.y = op_combine(o.y, sres[4 * q + 1], p, mu32, c.op);
-            o.z = op_combine(o.z, sres[4 * q + 2], p, mu32, c.op);
-            o.w = op_combine(o.w, sres[4 * q + 3], p, mu32, c.op);
-            dst[q] = o;
-        }
-        return;
-    }
-    // ragged edge or a tile boundary inside the run: groups of 8, loads then
-    // stores (a group's stores keep the next group's loads from being hoisted,
-    // which bounds the live registers)
-#pragma unroll
-    for (int g = 0; g < W; g += 8) {
-        uint32_t old[8];
-        uint64_t a[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            a[e] = fm_encode(ci, cj0 + g + e, c.c_lt);
-            old[e] = (c.op != FM_OP_SET && j0 + g + e < c.N) ? c.C[a[e]] : 0u;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-            if (j0 + g + e < c.N) c.C[a[e]] = op_combine(old[e], sres[g + e], p, mu32, c.op);
-    }
-}
-
 // GF(2) output: the residues (0 or 1) of columns j0 .. j0+31 of row gi become
 // one word of bits, combined into the bit-packed Morton-hybrid C (T' = 32: word
 // Z(I, J) * 32 + u holds tile row u). SET replaces the bits, ADD and SUB flip
@@ -262,7 +106,7 @@ __device__ __forceinline__ void gf2_apply(uint32_t* w, uint32_t m, uint32_t x, i
     }
 }
 
-__device__ __forceinline__ void write_gf2_run(const LimbCall& c, int64_t gi, int64_t j0,
+__device__ __forceinline__ void write_gf2_run(const CView& c, int64_t gi, int64_t j0,
                                               const uint32_t (&r)[32])
 {
     const int64_t nvalid = c.N - j0;
@@ -279,25 +123,6 @@ __device__ __forceinline__ void write_gf2_run(const LimbCall& c, int64_t gi, int
     if (b != 0) {
         const uint32_t m1 = vmask >> (32 - b);
         if (m1) gf2_apply(c.C + (fm_encode(ci, cj + (32 - b), 5) >> 5), m1, bits >> (32 - b), c.op);
-    }
-}
-
-// Prefetch into L2 the C entries of row gi, columns j0 .. j0+n-1 (n > 0): one
-// request per 128-byte line of each run that is contiguous in the
-// Morton-hybrid layout (a tile row).
-__device__ __forceinline__ void prefetch_c_row(const LimbCall& c, int64_t gi, int64_t j0, int64_t n)
-{
-    const int lt = c.c_lt;
-    const int64_t T = (int64_t)1 << lt;
-    const uint64_t ci = (uint64_t)(c.c_row0 + gi);
-    int64_t j = c.c_col0 + j0;
-    const int64_t end = j + n;
-    while (j < end) {
-        const int64_t run = min(end, (j | (T - 1)) + 1) - j;
-        const uint32_t* a = c.C + fm_encode(ci, (uint64_t)j, lt);
-        const uintptr_t lo = (uintptr_t)a & ~(uintptr_t)127, hi = (uintptr_t)(a + run);
-        for (uintptr_t q = lo; q < hi; q += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
-        j += run;
     }
 }
 
@@ -506,15 +331,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             int mb, nb;
             const LimbCall& cl = tile_call(tile, mb, nb);
+            const CView cv = c_view(cl);
             const int njobs = cl.njobs;
             // 32-column chunks of this warp inside C (none when its lane
             // quarter lies below the last row): the rest is never written
             const int live_cols = quarter * 32 < tile_rows(cl, mb) ? tile_cols(cl, nb) - (int)col0 : 0;
             const int n32 = max(0, min(kCols / 32, (live_cols + 31) / 32));
             // C of this tile is read at its end: start moving it into L2 now
-            if (KIND != kE4M3Gf2 && cl.op != FM_OP_SET && live_cols > 0 &&
-                (int64_t)mb * kBM + quarter * 32 + lane < cl.M)
-                prefetch_c_row(cl, (int64_t)mb * kBM + quarter * 32 + lane, (int64_t)nb * BN + col0,
+            if (KIND != kE4M3Gf2 && cv.op != FM_OP_SET && live_cols > 0 &&
+                (int64_t)mb * kBM + quarter * 32 + lane < cv.M)
+                prefetch_c_row(cv, (int64_t)mb * kBM + quarter * 32 + lane, (int64_t)nb * BN + col0,
                                min(live_cols, kCols));
             int idx = 0;
             for (int t = 0; t < njobs; ++t, ++T) {
@@ -639,11 +465,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint32_t col = col0 + cc * 32;
                 fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
                 fm_tmem_wait_ld();
-                if (gi < cl.M) {
+                if (gi < cv.M) {
                     if (KIND == kE4M3Gf2)
-                        write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
+                        write_gf2_run(cv, gi, (int64_t)nb * BN + col, sres);
                     else
-                        write_c_run<32>(cl, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cl.c_lt) - 1,
+                        write_c_run<32>(cv, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cv.c_lt) - 1,
                                         sres);
                 }
             }
@@ -939,7 +765,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                 fm_tmem_wait_ld();
                 if (gi < cl.M) {
                     if (KIND == kE4M3Gf2)
-                        write_gf2_run(cl, gi, (int64_t)nb * BN + col, sres);
+                        write_gf2_run(c_view(cl), gi, (int64_t)nb * BN + col, sres);
                     else
                         write_c_run<32>(cl, p, args.mu32, gi, (int64_t)nb * BN + col, cmask, sres);
                 }
@@ -1255,7 +1081,9 @@ int fm_limb_run(const FmLimbPlan& q, fm_sub C, fm_sub A, fm_sub B, uint32_t p, i
 // Every call of a batch gets its own limb planes in one workspace. Three
 // launches run the whole batch: the A splits of every call, the B splits of
 // every call, and one persistent GEMM over the output tiles of every call
-// (longest first; each CTA walks tiles blockIdx.x, + gridDim.x, ...).
+// (longest first; each CTA walks tiles blockIdx.x, + gridDim.x, ...). On
+// request (fm_opts.fused_batch) the batch runs as one fused launch instead
+// (limb_fused.cu).
 struct FmLimbBatch {
     FmLimbPlan q;  // limb parameters shared by every call (products, chunks, BN)
     uint32_t p = 0;
@@ -1269,6 +1097,7 @@ struct FmLimbBatch {
     int4* d_tiles = nullptr;
     int n_tiles = 0;
     bool gf2 = false;                      // bit-packed GF(2) operands
+    FmFusedBatch* fused = nullptr;         // one launch, operands split on the fly
     std::vector<fm_gemm_call> zero_calls;  // K = 0: only FM_OP_SET changes C
     std::vector<fm_gf2_sub> zero_subs;     // GF(2), K = 0 under FM_OP_SET
 };
@@ -1289,6 +1118,7 @@ int upload_vec(const std::vector<T>& v, T** out)
 void fm_limb_batch_destroy(FmLimbBatch* b)
 {
     if (!b) return;
+    fm_fused_batch_destroy(b->fused);
     cudaFree(b->ws);
     cudaFree(b->d_adesc);
     cudaFree(b->d_bdesc);
@@ -1414,6 +1244,16 @@ int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const
         bc.op = g.op;
         in.push_back(bc);
     }
+    if (o.fused_batch) {
+        const int rf = fm_fused_batch_create(calls, n, p, q, &b->fused);
+        if (rf != FM_OK) {
+            fm_limb_batch_destroy(b);
+            return rf;
+        }
+        b->n_tiles = (int)fm_fused_batch_tiles(b->fused);
+        *out = b;
+        return FM_OK;
+    }
     const int rc = build_batch(in, q.block_n, kBK, b);
     if (rc != FM_OK) {
         fm_limb_batch_destroy(b);
@@ -1474,6 +1314,14 @@ int64_t fm_limb_batch_tiles(const FmLimbBatch* b)
     return b ? b->n_tiles : 0;
 }
 
+int fm_limb_batch_launches(const FmLimbBatch* b)
+{
+    if (!b) return 0;
+    int n = (int)b->zero_subs.size();
+    if (b->n_tiles > 0) n += b->fused ? 1 : 3;
+    return n;
+}
+
 const std::vector<fm_gemm_call>& fm_limb_batch_zero_calls(const FmLimbBatch* b)
 {
     return b->zero_calls;
@@ -1483,6 +1331,7 @@ int fm_limb_batch_run(FmLimbBatch* b, int* status, cudaStream_t s)
 {
     for (const fm_gf2_sub& z : b->zero_subs) FM_TRY(fm_gf2_zero_sub(z, s));
     if (b->n_tiles == 0) return FM_OK;
+    if (b->fused) return fm_fused_batch_run(b->fused, status, s);
     if (b->gf2) {
         FM_TRY(fm_gf2_split_batch_run(FM_LIMB_A, b->d_adesc, b->d_ajobs, b->n_ajobs, s));
         FM_TRY(fm_gf2_split_batch_run(FM_LIMB_B, b->d_bdesc, b->d_bjobs, b->n_bjobs, s));

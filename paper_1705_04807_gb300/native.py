@@ -26,7 +26,7 @@ FM_LIMB_A, FM_LIMB_B = 0, 1
 EXPORTS = (
     "fm_layout_to_morton", "fm_layout_to_morton_permuted", "fm_layout_from_morton",
     "fm_permute_rows_cols", "fm_gemm_modp", "fm_gemm_modp_workspace_size", "fm_plan_create",
-    "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_destroy", "fm_decompose",
+    "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_launches", "fm_plan_destroy", "fm_decompose",
     "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
     "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
@@ -64,7 +64,7 @@ class fm_gf2_sub(ctypes.Structure):
 class fm_opts(ctypes.Structure):
     _fields_ = [("k_chunk", ctypes.c_int32), ("block_n", ctypes.c_int32),
                 ("no_karatsuba", ctypes.c_int32), ("cta_pair", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("fused_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class fm_tune_result(ctypes.Structure):
@@ -112,6 +112,7 @@ def lib():
                             ctypes.POINTER(fm_opts)], ctypes.c_int),
         "fm_gemm_modp_batched": ([P, P], ctypes.c_int),
         "fm_plan_work_items": ([P], I64),
+        "fm_plan_launches": ([P], I64),
         "fm_plan_destroy": ([P], ctypes.c_int),
         "fm_decompose": ([fm_sub, fm_sub, fm_sub, ctypes.POINTER(ctypes.c_int64), I64], I64),
         "fm_get_last_device_status": ([P], ctypes.c_int),
@@ -196,12 +197,14 @@ def gf2_sub(m: fm_gf2_matrix, row0: int, col0: int, rows: int, cols: int) -> fm_
     return fm_gf2_sub(m, int(row0), int(col0), int(rows), int(cols))
 
 
-def opts(k_chunk: int = 0, block_n: int = 0, no_karatsuba: int = 0, cta_pair: int = 0) -> fm_opts:
+def opts(k_chunk: int = 0, block_n: int = 0, no_karatsuba: int = 0, cta_pair: int = 0,
+         fused_batch: int = 0) -> fm_opts:
     o = fm_opts()
     o.k_chunk = int(k_chunk)
     o.block_n = int(block_n)
     o.no_karatsuba = int(no_karatsuba)
     o.cta_pair = int(cta_pair)
+    o.fused_batch = int(fused_batch)
     return o
 
 
@@ -276,6 +279,10 @@ class Plan:
     @property
     def work_items(self) -> int:
         return int(lib().fm_plan_work_items(self.handle))
+
+    @property
+    def launches(self) -> int:
+        return int(lib().fm_plan_launches(self.handle))
 
     def close(self):
         if self.handle:

@@ -162,11 +162,13 @@ def test_limb_batched_with_empty_and_k0_calls(env, orc):
     plan.close()
 
 
-def test_limb_batched_graph_capture_and_replay(env, orc):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_limb_batched_graph_capture_and_replay(env, orc, fused):
     import torch
     fm, dev = env
     MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 24, seed=11, lt=7)
-    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC)
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=fused))
+    assert plan.launches == (1 if fused else 3)
     fm.fm_get_last_device_status()
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -192,3 +194,87 @@ def test_limb_batched_rejects_pairs_and_overlap(env):
     call.A = M.sub(4, 4, 8, 8)  # overlaps C
     with pytest.raises(fm.FmError):
         fm.fm_plan_create([call], P16, fm.FM_ALGO_LIMB_TC)
+
+
+@pytest.mark.parametrize("lt,k_chunk,lo,hi,count,block,big,p", [
+    (3, 0, 1, 40, 48, 64, 512, P16),          # T' = 8: a stage's 8-row runs of B cross tile rows
+    (5, 64, 1, 300, 24, 320, 2048, P16),      # a fold of every product after every stage
+    (6, 0, 300, 1100, 4, 1152, 4096, P16),    # K beyond 960: folds of the outer products as well
+    (7, 128, 32, 600, 12, 640, 4096, 257),
+])
+def test_fused_batch_matches_oracle_and_plane_form(env, orc, lt, k_chunk, lo, hi, count, block, big, p):
+    # the one-launch fused batch (operands split on the fly, K window and output
+    # columns shifted by the operands' column offsets mod 4) against the oracle
+    # and against the three-launch form with limb planes in a workspace
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, count, seed=lt * 7 + k_chunk, lt=lt, lo=lo,
+                                                     hi=hi, block=block, big=big)
+    if p < P16:
+        Cf, Af, Bf = Cf % p, Af % p, Bf % p
+        MC.load(Cf)
+        MA.load(Af)
+        MB.load(Bf)
+    if count >= 12:  # random column offsets: every shift of A and of B occurs
+        assert {int(m[6]) % 4 for m in meta} == {0, 1, 2, 3} == {int(m[8]) % 4 for m in meta}
+    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC, fm.opts(k_chunk=k_chunk, fused_batch=1))
+    assert plan.launches == 1
+    saved = MC.t.clone()
+    plan.run()
+    got = MC.read()
+    assert fm.fm_get_last_device_status() == 0
+    assert np.array_equal(got, expected(orc, Cf, Af, Bf, meta, p=p))
+    MC.t.copy_(saved)
+    staged = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC, fm.opts(k_chunk=k_chunk))
+    assert staged.launches == 3
+    staged.run()
+    assert np.array_equal(MC.read(), got)
+    plan.close()
+    staged.close()
+
+
+def test_fused_batch_tiny_and_shifted_calls(env, orc):
+    # every combination of A's and B's column offset mod 4 with M, N, K in 1..7
+    fm, dev = env
+    lt = 5
+    Cf = fm_inputs.uniform_residues(41, (1024, 1024), P16, 1)
+    Af = fm_inputs.uniform_residues(41, (1024, 1024), P16, 2)
+    Bf = fm_inputs.uniform_residues(41, (1024, 1024), P16, 3)
+    MC, MA, MB = (MortonMatrix(fm, dev, 5, lt, fill=x) for x in (Cf, Af, Bf))
+    calls, meta = [], []
+    dims = fm_inputs.integers(42, 3 * 64, 1, 7).reshape(64, 3)
+    for c in range(64):
+        M, N, K = (int(x) for x in dims[c])
+        ra, rb = c % 4, (c // 4) % 4
+        cr, cc = (c // 8) * 16, (c % 8) * 16 + (c // 16)
+        ar, ac = 3 * c, 100 + 8 * c + ra
+        br, bc = 5 * c, 200 + 8 * c + rb
+        call = fm.fm_gemm_call()
+        call.C, call.A, call.B = MC.sub(cr, cc, M, N), MA.sub(ar, ac, M, K), MB.sub(br, bc, K, N)
+        call.op = c % 3
+        calls.append(call)
+        meta.append((M, N, K, cr, cc, ar, ac, br, bc, c % 3))
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1))
+    assert plan.launches == 1
+    plan.run()
+    assert fm.fm_get_last_device_status() == 0
+    assert np.array_equal(MC.read(), expected(orc, Cf, Af, Bf, meta))
+    plan.close()
+
+
+def test_fused_batch_rejects_small_tiles_and_other_forms(env, orc):
+    # T' = 4 operands (an 8-row run of B may cross two tile rows) and forms
+    # other than two-limb Karatsuba are not fused; the plane form runs them
+    fm, dev = env
+    MC, MA, MB, Cf, Af, Bf, calls, meta = make_batch(fm, dev, 6, seed=5, lt=2, lo=8, hi=60, block=64, big=256)
+    with pytest.raises(fm.FmError):
+        fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1))
+    for o in ({"no_karatsuba": 1}, {"block_n": 256}):
+        with pytest.raises(fm.FmError):
+            fm.fm_plan_create(calls[:1], P16, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1, **o))
+    with pytest.raises(fm.FmError):
+        fm.fm_plan_create(calls[:1], P31, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1))
+    plan = fm.fm_plan_create(calls, P16, fm.FM_ALGO_LIMB_TC)
+    assert plan.launches == 3
+    plan.run()
+    assert np.array_equal(MC.read(), expected(orc, Cf, Af, Bf, meta))
+    plan.close()
