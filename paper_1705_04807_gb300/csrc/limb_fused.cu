@@ -21,12 +21,18 @@
 // load a 64-wide K stage of A (128 x 64) and B (64 x 128) from the
 // Morton-hybrid layout with 16-byte loads, split it and store the six planes in
 // the 128-byte-swizzled K-major layout (two stages in shared memory, the next
-// stage's loads in flight while the current one is converted); one MMA thread
-// issues tcgen05.mma kind::f16 for the three products into three FP32
-// accumulators in tensor memory; four epilogue warps fold the accumulators at
-// exact-chunk boundaries, combine them at the tile end into residues (a fourth
-// tensor-memory slice, so the accumulators are free for the next tile at
-// once) and update C in the Morton-hybrid layout.
+// stage's loads in flight while the current one is converted); once all eight
+// have stored a stage, lane 0 of converter warp 0 issues its tcgen05.mma
+// kind::f16 for the three products into three FP32 accumulators in tensor
+// memory; four epilogue warps fold the accumulators at exact-chunk boundaries,
+// combine them at the tile end into residues (a fourth tensor-memory slice,
+// so the accumulators are free for the next tile at once) and update C in the
+// Morton-hybrid layout.
+//
+// Each operand entry is split once per output tile that uses it, which costs
+// more than the planes' round trip through HBM on batches of products a few
+// hundred wide: the plane form is the default and this one is requested with
+// fm_opts.fused_batch (one launch and no plane workspace).
 //
 // 16-byte loads need 4-aligned columns: a call's K window is shifted by A's
 // column offset mod 4 (ra zero entries in front, the same shift on B's rows),
