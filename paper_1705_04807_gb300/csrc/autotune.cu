@@ -125,8 +125,8 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
                 if (!q.fold && bn == 256) continue;
                 for (int kc : {full, full / 2}) {
                     if (kc < 64 || kc % 64) continue;
-                    for (int pair : {0, 1}) {
-                        if (pair && bn != 256) continue;
+                    for (int pair : {-1, 1}) {
+                        if (pair == 1 && bn != 256) continue;
                         limb(bn, kc, 0, pair);
                         if (q.n_planes == 3) limb(bn, kc, 1, pair);
                     }

@@ -191,12 +191,15 @@ __device__ __forceinline__ void fm_mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fm_smem_u32(bar)) : "memory");
 }
 
+// A thread whose phase is not complete sleeps in the instruction until it
+// completes, for at most the suspend-time hint (1 ms): a waiting warp then
+// takes no issue slots from the warps doing the work on its SM sub-partition.
 __device__ __forceinline__ bool fm_mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000000;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(fm_smem_u32(bar)), "r"(parity)

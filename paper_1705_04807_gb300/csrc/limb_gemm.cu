@@ -879,6 +879,7 @@ uint64_t gcd_u64(uint64_t a, uint64_t b)
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan)
 {
+    constexpr int64_t kPairMinK = 1024;
     if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
     FmLimbPlan q;
     q.M = M;
@@ -942,8 +943,13 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
             for (int k = 0; k < w * w; ++k)
                 if (gcd_u64(q.prod_w[k], p) != 1) return FM_EUNSUPPORTED;
     }
-    if (opts && opts->cta_pair && (!q.fold || bn != 256)) return FM_EINVAL;
-    q.pair = (opts && opts->cta_pair == 1) ? 1 : 0;
+    if (opts && opts->cta_pair == 1 && (!q.fold || bn != 256)) return FM_EINVAL;
+    // automatic: CTA pairs for the fold form on 256-wide tiles of a product
+    // with several tiles in each direction and a K loop long enough to hide
+    // the pair's two-epilogue coupling
+    int pair = opts ? opts->cta_pair : 0;
+    if (pair == 0) pair = (q.fold && bn == 256 && M > 256 && N > 256 && K >= kPairMinK) ? 1 : -1;
+    q.pair = pair == 1 ? 1 : 0;
     q.MB = (int)((M + kBM - 1) / kBM);
     if (bn == 256) q.MB += q.MB & 1;  // the A plane layout depends on BN only
     q.NB = (int)((N + bn - 1) / bn);
@@ -1217,7 +1223,7 @@ int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const
                          FmLimbBatch** out)
 {
     *out = nullptr;
-    if (opts && opts->cta_pair) return FM_EUNSUPPORTED;
+    if (opts && opts->cta_pair == 1) return FM_EUNSUPPORTED;
     // batches of small products waste less on 128-wide output tiles
     fm_opts o = opts ? *opts : fm_opts{};
     if (o.block_n == 0) o.block_n = 128;
@@ -1266,7 +1272,7 @@ int fm_limb_batch_create(const fm_gemm_call* calls, int64_t n, uint32_t p, const
 int fm_gf2_batch_create(const fm_gf2_call* calls, int64_t n, const fm_opts* opts, FmLimbBatch** out)
 {
     *out = nullptr;
-    if (opts && opts->cta_pair) return FM_EUNSUPPORTED;
+    if (opts && opts->cta_pair == 1) return FM_EUNSUPPORTED;
     FmLimbPlan q;
     FM_TRY(fm_gf2_plan(1, 1, 1, false, &q));
     q.prod_cs[0] = (int)((((int64_t)1 << 24) - 2) / 128);  // one accumulation for any K < 2^24

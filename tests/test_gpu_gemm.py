@@ -100,7 +100,7 @@ def test_limb_cta_pair_and_single_cta(env, orc, M, N, K):
     # and more pair tiles than pairs resident on the device (the persistent walk)
     fm = env[0]
     for p in (P16, 251, 2):
-        for pair in (0, 1):
+        for pair in (-1, 1):
             got, want = run_case(env, orc, p, 2, fm.FM_ALGO_LIMB_TC, M, N, K, (0, 3, 5, 0, 0, 7),
                                  (7, 7, 7), seed=M + N + p, options=fm.opts(0, 256, 0, pair))
             assert np.array_equal(got, want), (p, pair)
