@@ -760,7 +760,10 @@ def run_fm(args, world, rank, local):
                                "limb_gemm_n8192.md")
     roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                 "frac": achieved / sustained, "traffic": traffic,
-                "kernel": "limb_gemm_kernel<256,fold>",
+                # the library's automatic choice for this shape (fold form,
+                # 256-wide tiles): CTA pairs once M, N > 256 and K >= 1024
+                "kernel": ("limb_gemm_pair_kernel (cta_group::2, 256 x 256 tiles)" if n > 256 and n >= 1024
+                           else "limb_gemm_kernel<256,fold>"),
                 "work": f"2*M*N*K*{n_products} f16 MMA flops per launch ({n_products} limb "
                         f"products: Karatsuba on w={w} limbs), n={n}",
                 "peak_source": f"bf16 sustained, {src} (f16 = bf16 rate)",
