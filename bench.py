@@ -10,7 +10,9 @@ Sec. 2.2, T' = 64) and the FP64 DFMA form run the same step for comparison.
 
 value     = 2 M N K / (device time of one step), Gop/s (algorithmic ops only)
 e2e       = same, through host buffers: pinned H2D of A, B, C and D2H of C
-            inside the timed region
+            inside the timed region, as 16-bit residues for p < 2^16 (the
+            library's _u16 layout calls; the 32-bit transfer is reported in
+            e2e.u32)
 roofline  = the limb GEMM kernel: tensor work 2 M N K x (limb products: 3
             with Karatsuba on w = 2 limbs) per launch / its CUDA-event
             duration, against the measured bf16 sustained peak (f16 runs at
@@ -600,17 +602,22 @@ def run_fm(args, world, rank, local):
                      device=dev)
     s = stream.cuda_stream
 
-    def layout_in(srcA, srcB, srcC, mA_, mB_, mC_):
-        fm.fm_layout_to_morton_permuted(srcA, n, n, n, drp, dcp, mA_, s)
-        fm.fm_layout_to_morton(srcB, n, n, n, mB_, s)
-        fm.fm_layout_to_morton(srcC, n, n, n, mC_, s)
+    def layout_in(srcA, srcB, srcC, mA_, mB_, mC_, u16=False):
+        if u16:  # 16-bit row-major residues (p < 2^16)
+            fm.fm_layout_to_morton_permuted_u16(srcA, n, n, n, drp, dcp, mA_, s)
+            fm.fm_layout_to_morton_u16(srcB, n, n, n, mB_, s)
+            fm.fm_layout_to_morton_u16(srcC, n, n, n, mC_, s)
+        else:
+            fm.fm_layout_to_morton_permuted(srcA, n, n, n, drp, dcp, mA_, s)
+            fm.fm_layout_to_morton(srcB, n, n, n, mB_, s)
+            fm.fm_layout_to_morton(srcC, n, n, n, mC_, s)
 
     kern = {"layout_in": [], "limb_split": [], "limb_gemm": [], "layout_out": []}
 
-    def limb_step(srcA=dA, srcB=dB, srcC=dC, out=dOut, ev=None):
+    def limb_step(srcA=dA, srcB=dB, srcC=dC, out=dOut, ev=None, u16=False):
         if ev:
             ev[0].record(stream)
-        layout_in(srcA, srcB, srcC, mA, mB, mC)
+        layout_in(srcA, srcB, srcC, mA, mB, mC, u16)
         if ev:
             ev[1].record(stream)
         fm.fm_limb_split(sA, fm.FM_LIMB_A, p, pa, None, s)
@@ -620,7 +627,10 @@ def run_fm(args, world, rank, local):
         fm.fm_limb_gemm(sC, pa, pb, n, p, fm.FM_OP_SUB, None, s)
         if ev:
             ev[3].record(stream)
-        fm.fm_layout_from_morton(mC, n, n, out, n, s)
+        if u16:
+            fm.fm_layout_from_morton_u16(mC, n, n, out, n, s)
+        else:
+            fm.fm_layout_from_morton(mC, n, n, out, n, s)
         if ev:
             ev[4].record(stream)
 
@@ -661,53 +671,70 @@ def run_fm(args, world, rank, local):
     # Every step copies its inputs from pinned host memory and reads its result
     # back. Steps are pipelined: the host-to-device copies of step k+1 and the
     # device-to-host copy of step k-1 run on their own streams while step k
-    # computes (double-buffered device inputs and outputs).
-    hA = torch.from_numpy(A.view(np.int32)).pin_memory()
-    hB = torch.from_numpy(B.view(np.int32)).pin_memory()
-    hC = torch.from_numpy(C.view(np.int32)).pin_memory()
-    hOut = [torch.empty((n, n), dtype=torch.int32).pin_memory() for _ in range(2)]
-    xin = [(torch.empty_like(dA), torch.empty_like(dB), torch.empty_like(dC)) for _ in range(2)]
-    xout = [torch.empty_like(dOut) for _ in range(2)]
+    # computes (double-buffered device inputs and outputs). Residues mod
+    # p < 2^16 travel as 16-bit entries (the library's _u16 layout calls), half
+    # the bytes of the 32-bit form, which is measured as well.
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_comp = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_steps(count):
-        for k in range(count):
-            b = k & 1
-            with torch.cuda.stream(s_in):
+    def e2e(u16):
+        hdt, ddt = (np.uint16, torch.int16) if u16 else (np.uint32, torch.int32)
+        view = np.int16 if u16 else np.int32
+        hA, hB, hC = (torch.from_numpy(x.astype(hdt).view(view)).pin_memory() for x in (A, B, C))
+        hOut = [torch.empty((n, n), dtype=ddt).pin_memory() for _ in range(2)]
+        xin = [tuple(torch.empty((n, n), dtype=ddt, device=dev) for _ in range(3)) for _ in range(2)]
+        xout = [torch.empty((n, n), dtype=ddt, device=dev) for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_comp = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+
+        def steps_(count):
+            for k in range(count):
+                b = k & 1
+                with torch.cuda.stream(s_in):
+                    if k >= 2:
+                        s_in.wait_event(ev_comp[b])    # step k-2 no longer reads these buffers
+                    for dst, src in zip(xin[b], (hA, hB, hC)):
+                        dst.copy_(src, non_blocking=True)
+                    ev_in[b].record(s_in)
+                stream.wait_event(ev_in[b])
                 if k >= 2:
-                    s_in.wait_event(ev_comp[b])    # step k-2 no longer reads these buffers
-                for dst, src in zip(xin[b], (hA, hB, hC)):
-                    dst.copy_(src, non_blocking=True)
-                ev_in[b].record(s_in)
-            stream.wait_event(ev_in[b])
-            if k >= 2:
-                stream.wait_event(ev_out[b])       # step k-2's result has left xout[b]
-            limb_step(xin[b][0], xin[b][1], xin[b][2], xout[b])
-            ev_comp[b].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_comp[b])
-                hOut[b].copy_(xout[b], non_blocking=True)
-                ev_out[b].record(s_out)
-        stream.wait_stream(s_out)
-        stream.wait_stream(s_in)
+                    stream.wait_event(ev_out[b])       # step k-2's result has left xout[b]
+                limb_step(xin[b][0], xin[b][1], xin[b][2], xout[b], u16=u16)
+                ev_comp[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_comp[b])
+                    hOut[b].copy_(xout[b], non_blocking=True)
+                    ev_out[b].record(s_out)
+            stream.wait_stream(s_out)
+            stream.wait_stream(s_in)
 
-    e2e_steps(2)
-    torch.cuda.synchronize()
-    barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s_in.wait_stream(stream)
-    e2e_steps(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
-    e2e_value = world * ops * args.steps / (e2e_ms / 1e3) / 1e9
-    # the results read back equal the device-resident result
-    assert torch.equal(hOut[(args.steps - 1) & 1], dOut.cpu())
+        steps_(2)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        steps_(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = allreduce_max(e0.elapsed_time(e1), world)
+        # the results read back equal the device-resident result
+        last = hOut[(args.steps - 1) & 1]
+        want = dOut.cpu()
+        same = bool(torch.equal(last.to(torch.int32) & 0xFFFF, want) if u16 else torch.equal(last, want))
+        assert same
+        esz = 2 if u16 else 4
+        return {"value": world * ops * args.steps / (ms / 1e3) / 1e9, "unit": "Gop/s",
+                "h2d_bytes_per_step": 3 * n * n * esz, "d2h_bytes_per_step": n * n * esz,
+                "host_dtype": "u16" if u16 else "u32", "ms_per_step": ms / args.steps}
+
+    e2e_u32 = e2e(False)
+    if p < (1 << 16):
+        e2e_line = e2e(True)
+        e2e_line["u32"] = e2e_u32
+    else:
+        e2e_line = e2e_u32
 
     out = {}
     # ---- comparison forms on the same inputs (same step, other GEMM) ----
@@ -779,8 +806,7 @@ def run_fm(args, world, rank, local):
         "config": {"workload": f"C -= (P A Q) * B mod {p}, n={n}, Morton-hybrid T'=128, "
                                "row-major in/out", "n": n, "p": p, "T": 1 << lt_limb,
                    "l2": f"inputs larger than L2 (3 x {4 * n * n >> 20} MiB)"},
-        "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 3 * 4 * n * n,
-                "d2h_bytes_per_step": 4 * n * n},
+        "e2e": e2e_line,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": roofline,

@@ -123,6 +123,19 @@ int fm_layout_to_morton_permuted(const uint32_t* src, int64_t rows, int64_t cols
 int fm_layout_from_morton(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst, int64_t ld,
                           fm_stream stream);
 
+/* The same three conversions with 16-bit row-major entries, for residues
+ * mod p <= 65536: half the bytes on the row-major side (for example across
+ * the host link). The Morton-hybrid matrix stays 32-bit; the _u16 reads
+ * widen every entry, fm_layout_from_morton_u16 stores the low 16 bits of
+ * every entry. Arguments and errors as for the 32-bit calls. */
+int fm_layout_to_morton_u16(const uint16_t* src, int64_t rows, int64_t cols, int64_t ld,
+                            fm_matrix dst, fm_stream stream);
+int fm_layout_to_morton_permuted_u16(const uint16_t* src, int64_t rows, int64_t cols, int64_t ld,
+                                     const int32_t* row_perm, const int32_t* col_perm,
+                                     fm_matrix dst, fm_stream stream);
+int fm_layout_from_morton_u16(fm_matrix src, int64_t rows, int64_t cols, uint16_t* dst,
+                              int64_t ld, fm_stream stream);
+
 /* Morton-hybrid to Morton-hybrid permutation (Sec. 1, TURBO's virtual row and
  * column permutations made explicit): dst(i, j) = src(row_perm[i], col_perm[j])
  * for i < rows, j < cols; the rest of dst is set to 0. src and dst must not

@@ -5,7 +5,9 @@
 // index conversion between the curve and Cartesian order. These kernels are
 // HBM-bound gathers: each CTA walks whole tiles of the Morton matrix, so the
 // Morton side is read or written as contiguous 16-byte vectors and the
-// row-major side in row segments of T' elements.
+// row-major side in row segments of T' elements. The row-major side holds
+// 32-bit entries, or 16-bit ones (residues mod p < 2^16: half the bytes to
+// move, e.g. across the host link); the Morton-hybrid side is always 32-bit.
 #include <algorithm>
 
 #include "fm_internal.cuh"
@@ -14,9 +16,36 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Four consecutive row-major entries starting at p (4-entry aligned).
+__device__ __forceinline__ uint4 ld4(const uint32_t* p)
+{
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+__device__ __forceinline__ uint4 ld4(const uint16_t* p)
+{
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    return make_uint4(v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16);
+}
+
+__device__ __forceinline__ void st4(uint32_t* p, uint4 v)
+{
+    *reinterpret_cast<uint4*>(p) = v;
+}
+
+// 16-bit destination: the low 16 bits of every entry
+__device__ __forceinline__ void st4(uint16_t* p, uint4 v)
+{
+    *reinterpret_cast<uint2*>(p) = make_uint2((v.x & 0xFFFFu) | (v.y << 16), (v.z & 0xFFFFu) | (v.w << 16));
+}
+
+// byte alignment of a 4-entry vector of T
+template <typename T>
+constexpr uintptr_t kVec4Align = 4 * sizeof(T) - 1;
+
 // dst(i, j) = src[rp(i) * ld + cp(j)] (0 outside rows x cols), dst Morton.
-template <bool kPerm>
-__global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __restrict__ src,
+template <bool kPerm, typename T>
+__global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict__ src,
                                                              int64_t rows, int64_t cols, int64_t ld,
                                                              const int32_t* __restrict__ rp,
                                                              const int32_t* __restrict__ cp,
@@ -27,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
     const int64_t tile_elems = (int64_t)1 << (2 * lt);
     // 16-byte row segments whenever no column permutation scatters them
     const bool vec_ok = (!kPerm || cp == nullptr) && lt >= 2 && ((ld & 3) == 0) &&
-                        (((uintptr_t)src & 15) == 0);
+                        (((uintptr_t)src & kVec4Align<T>) == 0);
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         // Z order keeps the Morton writes sequential; with a column permutation
         // the reads are a random gather inside each source row, so tiles are
@@ -50,14 +79,14 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
                 if (i < rows) {
                     const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
                     if (vec_ok && j + 3 < cols) {
-                        v = __ldg(reinterpret_cast<const uint4*>(src + si * ld + j));
+                        v = ld4(src + si * ld + j);
                     } else {
                         uint32_t w[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int64_t jj = j + q;
                             const int64_t sj = kPerm && cp && jj < cols ? (int64_t)__ldg(cp + jj) : jj;
-                            w[q] = jj < cols ? __ldg(src + si * ld + sj) : 0u;
+                            w[q] = jj < cols ? (uint32_t)__ldg(src + si * ld + sj) : 0u;
                         }
                         v = make_uint4(w[0], w[1], w[2], w[3]);
                     }
@@ -72,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
                 if (i < rows && j < cols) {
                     const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
                     const int64_t sj = kPerm && cp ? (int64_t)__ldg(cp + j) : j;
-                    v = __ldg(src + si * ld + sj);
+                    v = (uint32_t)__ldg(src + si * ld + sj);
                 }
                 tile[e] = v;
             }
@@ -85,22 +114,23 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const uint32_t* __r
 // gathers the permuted columns from shared memory and writes the destination
 // row as contiguous runs of T' entries (one per Morton tile it crosses), so
 // HBM sees one read and one write per element.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    to_morton_rowgather_kernel(const uint32_t* __restrict__ src, int64_t rows, int64_t cols,
+    to_morton_rowgather_kernel(const T* __restrict__ src, int64_t rows, int64_t cols,
                                int64_t ld, const int32_t* __restrict__ rp,
                                const int32_t* __restrict__ cp, uint32_t* __restrict__ dst, int lg,
                                int lt)
 {
     extern __shared__ __align__(16) uint32_t srow[];
     const int64_t n = (int64_t)1 << (lg + lt);
-    const bool vec = ((ld & 3) == 0) && (((uintptr_t)src & 15) == 0);
+    const bool vec = ((ld & 3) == 0) && (((uintptr_t)src & kVec4Align<T>) == 0);
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
         if (i < rows) {
-            const uint32_t* sr = src + (rp ? (int64_t)__ldg(rp + i) : i) * ld;
+            const T* sr = src + (rp ? (int64_t)__ldg(rp + i) : i) * ld;
             const int64_t c4 = vec ? cols / 4 : 0;
             for (int64_t q = threadIdx.x; q < c4; q += kThreads)
-                *reinterpret_cast<uint4*>(srow + 4 * q) = __ldg(reinterpret_cast<const uint4*>(sr) + q);
-            for (int64_t j = 4 * c4 + threadIdx.x; j < cols; j += kThreads) srow[j] = __ldg(sr + j);
+                *reinterpret_cast<uint4*>(srow + 4 * q) = ld4(sr + 4 * q);
+            for (int64_t j = 4 * c4 + threadIdx.x; j < cols; j += kThreads) srow[j] = (uint32_t)__ldg(sr + j);
         }
         __syncthreads();
         for (int64_t j = 4 * (int64_t)threadIdx.x; j < n; j += 4 * kThreads) {
@@ -118,10 +148,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // dst[i * ld + j] = src(i, j) for i < rows, j < cols, src Morton.
+template <typename E>
 __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* __restrict__ src,
                                                                int lg, int lt, int64_t rows,
-                                                               int64_t cols,
-                                                               uint32_t* __restrict__ dst,
+                                                               int64_t cols, E* __restrict__ dst,
                                                                int64_t ld)
 {
     const int64_t tiles_side = (int64_t)1 << lg;
@@ -130,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* _
     const int64_t tr = (rows + T - 1) >> lt, tc = (cols + T - 1) >> lt;
     const int64_t ntiles = tr * tc;
     const int64_t tile_elems = T * T;
-    const bool vec_ok = lt >= 2 && ((ld & 3) == 0) && (((uintptr_t)dst & 15) == 0);
+    const bool vec_ok = lt >= 2 && ((ld & 3) == 0) && (((uintptr_t)dst & kVec4Align<E>) == 0);
     (void)tiles_side;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t I = t / tc, J = t % tc;
@@ -143,19 +173,19 @@ __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* _
                 if (i >= rows || j >= cols) continue;
                 const uint4 v = __ldg(reinterpret_cast<const uint4*>(tile + e));
                 if (vec_ok && j + 3 < cols) {
-                    *reinterpret_cast<uint4*>(dst + i * ld + j) = v;
+                    st4(dst + i * ld + j, v);
                 } else {
                     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (j + q < cols) dst[i * ld + j + q] = w[q];
+                        if (j + q < cols) dst[i * ld + j + q] = (E)w[q];
                 }
             }
         } else {
             for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
                 const int64_t i = i_base + (e >> lt);
                 const int64_t j = j_base + (e & (T - 1));
-                if (i < rows && j < cols) dst[i * ld + j] = __ldg(tile + e);
+                if (i < rows && j < cols) dst[i * ld + j] = (E)__ldg(tile + e);
             }
         }
     }
@@ -197,8 +227,9 @@ int grid_for(int64_t tiles)
     return (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
 }
 
-int to_morton_impl(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
-                   const int32_t* rp, const int32_t* cp, fm_matrix dst, fm_stream stream)
+template <typename T>
+int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const int32_t* rp,
+                   const int32_t* cp, fm_matrix dst, fm_stream stream)
 {
     FM_TRY(fm_check_matrix(dst));
     const int64_t n = fm_side(dst);
@@ -209,16 +240,32 @@ int to_morton_impl(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
     if (cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
         const int64_t n = fm_side(dst);
         const int grid = (int)std::min<int64_t>(n, (int64_t)fm_sm_count() * 8);
-        FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel,
+        FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        to_morton_rowgather_kernel<<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
+        to_morton_rowgather_kernel<T><<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
     } else if (rp || cp)
-        to_morton_kernel<true><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        to_morton_kernel<true, T><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
     else
-        to_morton_kernel<false><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        to_morton_kernel<false, T><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, nullptr, nullptr, dst.base, dst.log2_grid, dst.log2_T);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
+}
+
+template <typename E>
+int from_morton_impl(fm_matrix src, int64_t rows, int64_t cols, E* dst, int64_t ld, fm_stream stream)
+{
+    FM_TRY(fm_check_matrix(src));
+    const int64_t n = fm_side(src);
+    if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
+    if (rows == 0 || cols == 0) return FM_OK;
+    if (dst == nullptr) return FM_EINVAL;
+    const int64_t T = (int64_t)1 << src.log2_T;
+    const int64_t tiles = ((rows + T - 1) / T) * ((cols + T - 1) / T);
+    from_morton_kernel<E><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        src.base, src.log2_grid, src.log2_T, rows, cols, dst, ld);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
 }
@@ -245,17 +292,30 @@ extern "C" int fm_layout_from_morton(fm_matrix src, int64_t rows, int64_t cols, 
                                      int64_t ld, fm_stream stream)
 {
     FmRange range("fm_layout_from_morton");
-    FM_TRY(fm_check_matrix(src));
-    const int64_t n = fm_side(src);
-    if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
-    if (rows == 0 || cols == 0) return FM_OK;
-    if (dst == nullptr) return FM_EINVAL;
-    const int64_t T = (int64_t)1 << src.log2_T;
-    const int64_t tiles = ((rows + T - 1) / T) * ((cols + T - 1) / T);
-    from_morton_kernel<<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
-        src.base, src.log2_grid, src.log2_T, rows, cols, dst, ld);
-    FM_CUDA_TRY(cudaGetLastError());
-    return FM_OK;
+    return from_morton_impl(src, rows, cols, dst, ld, stream);
+}
+
+extern "C" int fm_layout_to_morton_u16(const uint16_t* src, int64_t rows, int64_t cols, int64_t ld,
+                                       fm_matrix dst, fm_stream stream)
+{
+    FmRange range("fm_layout_to_morton_u16");
+    return to_morton_impl(src, rows, cols, ld, nullptr, nullptr, dst, stream);
+}
+
+extern "C" int fm_layout_to_morton_permuted_u16(const uint16_t* src, int64_t rows, int64_t cols,
+                                                int64_t ld, const int32_t* row_perm,
+                                                const int32_t* col_perm, fm_matrix dst,
+                                                fm_stream stream)
+{
+    FmRange range("fm_layout_to_morton_permuted_u16");
+    return to_morton_impl(src, rows, cols, ld, row_perm, col_perm, dst, stream);
+}
+
+extern "C" int fm_layout_from_morton_u16(fm_matrix src, int64_t rows, int64_t cols, uint16_t* dst,
+                                         int64_t ld, fm_stream stream)
+{
+    FmRange range("fm_layout_from_morton_u16");
+    return from_morton_impl(src, rows, cols, dst, ld, stream);
 }
 
 extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,

@@ -93,3 +93,33 @@ def test_config2_layout_full_size(env, orc):
         fm.fm_layout_to_morton_permuted(to_dev(x, dev), rows, cols, cols, to_dev(rp, dev),
                                         to_dev(cp, dev), M.m)
         assert np.array_equal(to_host(M.t), orc.to_morton(orc.permute(x, rp, cp), 6, 64))
+
+
+@pytest.mark.parametrize("rows,cols,ld,lg,lt", [(37, 53, 53, 2, 4), (300, 301, 304, 3, 6), (130, 250, 251, 1, 7),
+                                                (5, 3, 7, 3, 0), (1000, 17, 20, 5, 5), (64, 64, 64, 0, 6)])
+def test_u16_layout_matches_u32(env, orc, rows, cols, ld, lg, lt):
+    # 16-bit row-major entries (residues mod 65521): the same Morton-hybrid
+    # matrix as the 32-bit conversion, with and without permutations, and the
+    # 16-bit read-back returns the entries and leaves the columns past cols
+    import torch
+    fm, dev = env
+    x = fm_inputs.uniform_residues(rows + 3 * cols, (rows, ld), 65521)
+    x16 = x.astype(np.uint16)
+    d16 = torch.from_numpy(x16.view(np.int16)).to(dev)
+    M = MortonMatrix(fm, dev, lg, lt)
+    M.t.fill_(-1)
+    fm.fm_layout_to_morton_u16(d16, rows, cols, ld, M.m)
+    assert np.array_equal(to_host(M.t), orc.to_morton(x[:, :cols], lg, 1 << lt))
+    out = torch.full((rows, ld), -1, dtype=torch.int16, device=dev)
+    fm.fm_layout_from_morton_u16(M.m, rows, cols, out, ld)
+    back = out.cpu().numpy().view(np.uint16)
+    assert np.array_equal(back[:, :cols], x16[:, :cols])
+    assert np.all(back[:, cols:] == 0xFFFF)
+    rp = fm_inputs.permutation(rows, rows, 1)
+    cp = fm_inputs.permutation(cols, cols, 2)
+    for r, c in ((rp, cp), (rp, None), (None, cp)):
+        P = MortonMatrix(fm, dev, lg, lt)
+        fm.fm_layout_to_morton_permuted_u16(d16, rows, cols, ld, None if r is None else to_dev(r, dev),
+                                            None if c is None else to_dev(c, dev), P.m)
+        want = orc.to_morton(orc.permute(x[:, :cols], r, c), lg, 1 << lt)
+        assert np.array_equal(to_host(P.t), want)
