@@ -534,8 +534,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
     const int n_tiles = MB2 * cl.NB;
     const int njobs = cl.njobs;
 
+    // grouped raster: a wave of 76 pairs covers 8 pair rows x 9.5 pair
+    // columns, near the fewest A and B panel bytes per wave
     auto coords = [&](int tile, int& mb2, int& nb) {
-        const int GROUP = 4;
+        const int GROUP = 8;
         const int per_group = GROUP * cl.NB;
         const int first = (tile / per_group) * GROUP;
         const int gsz = min(MB2 - first, GROUP);
