@@ -749,7 +749,8 @@ def run_fm(args, world, rank, local):
             fm.fm_gemm_modp(s6[0], s6[1], s6[2], p, fm.FM_OP_SUB, algo, None, s)
             fm.fm_layout_from_morton(mC6, n, n, dOut, n, s)
 
-        ref = None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         limb_step()
         torch.cuda.synchronize()
         ref = dOut.clone()
