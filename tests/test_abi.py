@@ -113,3 +113,23 @@ def test_autotune_table_roundtrip(fm, tmp_path):
     with pytest.raises(fm.FmError):
         fm.fm_autotune_load(str(bad))
     fm.fm_autotune_clear()
+
+
+def test_layout_calls_reject_bad_arguments_on_the_host(fm):
+    # argument checks of the 32-bit and 16-bit layout calls run on the host,
+    # before any device work (the matrices here are host-only fake bases)
+    M = fm.matrix(1 << 20, 1, 5)   # 64 x 64 grid
+    for to_morton, from_morton in ((fm.fm_layout_to_morton, fm.fm_layout_from_morton),
+                                   (fm.fm_layout_to_morton_u16, fm.fm_layout_from_morton_u16)):
+        with pytest.raises(fm.FmError):
+            to_morton(1 << 24, 65, 10, 10, M)      # more rows than the grid
+        with pytest.raises(fm.FmError):
+            to_morton(1 << 24, 10, 10, 5, M)       # ld < cols
+        with pytest.raises(fm.FmError):
+            to_morton(0, 10, 10, 10, M)            # no source
+        with pytest.raises(fm.FmError):
+            from_morton(M, 10, 70, 1 << 24, 70)    # more columns than the grid
+        with pytest.raises(fm.FmError):
+            from_morton(M, 10, 10, 0, 10)          # no destination
+    with pytest.raises(fm.FmError):
+        fm.fm_layout_to_morton_permuted_u16(1 << 24, 10, 10, 8, 0, 0, M)   # ld < cols
