@@ -426,6 +426,14 @@ int fm_debug_expire_wait(int32_t which, fm_stream stream);
  * kernels raise on an expired bounded wait (FM_OK or FM_ETIMEOUT). */
 int fm_get_last_device_status(fm_stream stream);
 
+/* Validation: every entry of the sub-matrix X must be a residue in [0, p)
+ * (the inputs the paper's arithmetic assumes; the library's kernels do not
+ * check them). Scans X on stream and, if an entry is >= p, records FM_ERANGE
+ * in the device status word, read with fm_get_last_device_status.
+ * Errors (returned): FM_EMODULUS if p < 2 or p >= 2^31, FM_EINVAL for a bad
+ * descriptor. */
+int fm_validate_residues(fm_sub X, uint32_t p, fm_stream stream);
+
 /* Static string for a status code. */
 const char* fm_strerror(int status);
 

@@ -221,6 +221,32 @@ __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __res
     }
 }
 
+// Raises FM_ERANGE in *status when an entry of the rows x cols sub-matrix at
+// (row0, col0) of a Morton-hybrid matrix is >= p. One warp per sub-matrix row:
+// the row's entries inside one tile row are contiguous, so the lanes read
+// consecutive entries.
+__global__ void __launch_bounds__(kThreads) validate_kernel(const uint32_t* __restrict__ base, int lt,
+                                                            int64_t row0, int64_t col0, int64_t rows,
+                                                            int64_t cols, uint32_t p, int* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t T = (int64_t)1 << lt;
+    bool bad = false;
+    for (int64_t r = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const uint64_t gi = (uint64_t)(row0 + r);
+        for (int64_t j = 0; j < cols;) {
+            const uint64_t gj = (uint64_t)(col0 + j);
+            const int64_t left = T - (int64_t)(gj & (uint64_t)(T - 1));
+            const int64_t run = cols - j < left ? cols - j : left;
+            const uint32_t* seg = base + fm_encode(gi, gj, lt);
+            for (int64_t e = lane; e < run; e += 32) bad |= __ldg(seg + e) >= p;
+            j += run;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) fm_raise(status, FM_ERANGE);
+}
+
 int grid_for(int64_t tiles)
 {
     const int64_t cap = (int64_t)fm_sm_count() * 8;
@@ -316,6 +342,21 @@ extern "C" int fm_layout_from_morton_u16(fm_matrix src, int64_t rows, int64_t co
 {
     FmRange range("fm_layout_from_morton_u16");
     return from_morton_impl(src, rows, cols, dst, ld, stream);
+}
+
+extern "C" int fm_validate_residues(fm_sub X, uint32_t p, fm_stream stream)
+{
+    FmRange range("fm_validate_residues");
+    if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
+    FM_TRY(fm_check_sub(X));
+    if (X.rows == 0 || X.cols == 0) return FM_OK;
+    int* status = fm_device_status();
+    if (!status) return FM_ECUDA;
+    const int64_t blocks = (X.rows + kThreads / 32 - 1) / (kThreads / 32);
+    validate_kernel<<<grid_for(blocks), kThreads, 0, (cudaStream_t)stream>>>(
+        X.m.base, X.m.log2_T, X.row0, X.col0, X.rows, X.cols, p, status);
+    FM_CUDA_TRY(cudaGetLastError());
+    return FM_OK;
 }
 
 extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,

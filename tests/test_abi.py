@@ -133,3 +133,12 @@ def test_layout_calls_reject_bad_arguments_on_the_host(fm):
             from_morton(M, 10, 10, 0, 10)          # no destination
     with pytest.raises(fm.FmError):
         fm.fm_layout_to_morton_permuted_u16(1 << 24, 10, 10, 8, 0, 0, M)   # ld < cols
+
+
+def test_validate_residues_rejects_bad_arguments_on_the_host(fm):
+    M = fm.matrix(1 << 20, 1, 5)   # 64 x 64 grid, host-only fake base
+    for p in (0, 1, 1 << 31):
+        with pytest.raises(fm.FmError):
+            fm.fm_validate_residues(fm.sub(M, 0, 0, 8, 8), p)
+    with pytest.raises(fm.FmError):
+        fm.fm_validate_residues(fm.sub(M, 60, 0, 8, 8), 65521)   # outside the matrix

@@ -123,3 +123,33 @@ def test_u16_layout_matches_u32(env, orc, rows, cols, ld, lg, lt):
                                             None if c is None else to_dev(c, dev), P.m)
         want = orc.to_morton(orc.permute(x[:, :cols], r, c), lg, 1 << lt)
         assert np.array_equal(to_host(P.t), want)
+
+
+@pytest.mark.parametrize("lt,row0,col0,rows,cols", [(5, 3, 7, 100, 90), (6, 0, 0, 256, 256), (3, 17, 5, 1, 200)])
+def test_validate_residues(env, lt, row0, col0, rows, cols):
+    # a sub-matrix of residues passes; one entry equal to p inside it raises
+    # FM_ERANGE; an out-of-range entry outside the sub-matrix is not its business
+    import torch
+    fm, dev = env
+    p = 65521
+    n = 256
+    lg = 0
+    while (1 << lg) << lt < n:
+        lg += 1
+    x = fm_inputs.uniform_residues(lt + row0, (n, n), p)
+    M = MortonMatrix(fm, dev, lg, lt, fill=x)
+    X = M.sub(row0, col0, rows, cols)
+    fm.fm_get_last_device_status()
+    fm.fm_validate_residues(X, p)
+    assert fm.fm_get_last_device_status() == 0
+    y = x.copy()
+    y[row0 + rows // 2, col0 + cols - 1] = p
+    if row0 > 0:
+        y[row0 - 1, col0] = 0xFFFFFFFF   # outside the sub-matrix
+    M.load(y)
+    fm.fm_validate_residues(X, p)
+    assert fm.fm_get_last_device_status() == fm.FM_ERANGE
+    y[row0 + rows // 2, col0 + cols - 1] = p - 1
+    M.load(y)
+    fm.fm_validate_residues(X, p)
+    assert fm.fm_get_last_device_status() == 0
