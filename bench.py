@@ -20,6 +20,9 @@ roofline  = the limb GEMM kernel: tensor work 2 M N K x (limb products: 3
 gf2       = C += A*B over GF(2) on bit-packed Morton-hybrid matrices (the
             paper's experimental field; E4M3 tensor cores), and the paper's
             workload of 468 random sub-matrix products in 2048 x 2048 matrices
+configs   = the other workloads: 256^3 (launch-latency bound, next to the floor of
+            one launch), the 3000 x 1700 x 2200 Schur update with permuted
+            conversion, and 4096^3 at p = 2^31 - 1 on the limb form
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fm|reference]
 For N > 1 launch with torchrun; every rank runs an independent replica.
@@ -55,6 +58,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-GEMM measurement")
     ap.add_argument("--no-tu", action="store_true", help="skip the TU decomposition measurement")
     ap.add_argument("--no-gf2", action="store_true", help="skip the GF(2) measurements")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the small, Schur-update and 31-bit workloads")
     return ap.parse_args()
 
 
@@ -409,6 +414,145 @@ def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
                         f"seeded uniform factors), 128-column panels, trailing updates via fm_gemm_modp",
             "ms": ms, "rank": r, "rank_expected": k, "value": ops / (ms / 1e3) / 1e9, "unit": "Gop/s",
             "ops": "2*(m n r - (m+n) r^2/2 + r^3/3)"}
+
+
+def run_configs(fm, torch, dev, stream, seed=21):
+    """The other workloads of the hot path, each timed with CUDA events after
+    warm-up, and each result checked bit-identical against a second GEMM form
+    on the same inputs:
+    small   -- C = A*B mod 65521 at 256^3, T' = 32, plain form: a launch-latency
+               bound call, reported in microseconds next to the floor of one
+               launch of the library's smallest kernel (a 1 x 1 validation scan);
+               checked against the limb form;
+    schur   -- C (3000 x 2200) -= A (3000 x 1700) * B (1700 x 2200) mod 65521,
+               T' = 64, row-major inputs converted on the device with random row
+               and column permutations of A, plain form (aligned/contained
+               decomposition); checked against the limb form;
+    p31     -- C = A*B mod 2^31 - 1 at 4096^3, limb form (four limbs, 16 limb
+               products on the tensor cores); checked against the plain form."""
+    import numpy as np
+
+    import fm_inputs
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    s = stream.cuda_stream
+    out = {}
+
+    def dev_i32(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int32)).to(dev)
+
+    def morton(side, lt):
+        lg = 0
+        while (1 << lg) << lt < side:
+            lg += 1
+        n_ = (1 << lg) << lt
+        t = torch.zeros(n_ * n_, dtype=torch.int32, device=dev)
+        return t, fm.matrix(t, lg, lt)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def same_as(tC, snap, run_other):
+        # the result in tC against the other form run on the same inputs
+        got = tC.clone()
+        tC.copy_(snap)
+        run_other()
+        torch.cuda.synchronize()
+        return bool(torch.equal(tC, got))
+
+    # small: 256^3, plain, T' = 32
+    p = 65521
+    n = 256
+    A = fm_inputs.uniform_residues(seed, (n, n), p, 1)
+    B = fm_inputs.uniform_residues(seed, (n, n), p, 2)
+    (tA, mA), (tB, mB), (tC, mC) = morton(n, 5), morton(n, 5), morton(n, 5)
+    fm.fm_layout_to_morton(dev_i32(A), n, n, n, mA, s)
+    fm.fm_layout_to_morton(dev_i32(B), n, n, n, mB, s)
+    sub = [fm.sub(m_, 0, 0, n, n) for m_ in (mC, mA, mB)]
+
+    def small(algo):
+        fm.fm_gemm_modp(sub[0], sub[1], sub[2], p, fm.FM_OP_SET, algo, None, s)
+
+    us = timed(lambda: small(fm.FM_ALGO_PLAIN), 200) * 1e3
+    one = fm.sub(mA, 0, 0, 1, 1)
+    floor_us = timed(lambda: fm.fm_validate_residues(one, p, s), 200) * 1e3
+    torch.cuda.synchronize()
+    same = same_as(tC, tC.clone(), lambda: small(fm.FM_ALGO_LIMB_TC))
+    out["small"] = {"workload": "C = A*B mod 65521, M=N=K=256, Morton-hybrid T'=32, plain form",
+                    "us_per_call": us, "launch_floor_us": floor_us, "floor_frac": floor_us / us,
+                    "value": 2.0 * n ** 3 / (us / 1e6) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same}
+    del tA, tB, tC
+
+    # schur: 3000 x 1700 x 2200 with permutations, plain, T' = 64
+    M, K, N = 3000, 1700, 2200
+    dA = dev_i32(fm_inputs.uniform_residues(seed, (M, K), p, 3))
+    dB = dev_i32(fm_inputs.uniform_residues(seed, (K, N), p, 4))
+    dC = dev_i32(fm_inputs.uniform_residues(seed, (M, N), p, 5))
+    drp, dcp = dev_i32(fm_inputs.permutation(seed, M, 6)), dev_i32(fm_inputs.permutation(seed, K, 7))
+    side = max(M, K, N)  # one common 2^m T' grid (4096 x 4096 at T' = 64)
+    (tA, mA), (tB, mB), (tC, mC) = morton(side, 6), morton(side, 6), morton(side, 6)
+    sC, sA, sB = fm.sub(mC, 0, 0, M, N), fm.sub(mA, 0, 0, M, K), fm.sub(mB, 0, 0, K, N)
+
+    def layout():
+        fm.fm_layout_to_morton_permuted(dA, M, K, K, drp, dcp, mA, s)
+        fm.fm_layout_to_morton(dB, K, N, N, mB, s)
+        fm.fm_layout_to_morton(dC, M, N, N, mC, s)
+
+    lay_ms = timed(layout, 10)
+    gemm_ms = timed(lambda: fm.fm_gemm_modp(sC, sA, sB, p, fm.FM_OP_SUB, fm.FM_ALGO_PLAIN, None, s), 5)
+    layout()
+    snap = tC.clone()
+    fm.fm_gemm_modp(sC, sA, sB, p, fm.FM_OP_SUB, fm.FM_ALGO_PLAIN, None, s)
+    torch.cuda.synchronize()
+    same = same_as(tC, snap, lambda: fm.fm_gemm_modp(sC, sA, sB, p, fm.FM_OP_SUB, fm.FM_ALGO_LIMB_TC, None, s))
+    ops = 2.0 * M * N * K
+    lay_bytes = 8.0 * (M * K + K * N + M * N)
+    out["schur"] = {"workload": "C(3000x2200) -= A(3000x1700) * B(1700x2200) mod 65521, Morton-hybrid T'=64, "
+                                "row and column permutations of A in the conversion, plain form",
+                    "layout_ms": lay_ms, "layout_gbs": lay_bytes / (lay_ms / 1e3) / 1e9, "gemm_ms": gemm_ms,
+                    "value": ops / (gemm_ms / 1e3) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same}
+    del tA, tB, tC, dA, dB, dC, snap
+
+    # p31: 4096^3 at p = 2^31 - 1, limb form (T' = 128); the plain form, which
+    # takes T' = 32 or 64, computes the same product on T' = 64 copies
+    p = 2147483647
+    n = 4096
+    xa = dev_i32(fm_inputs.uniform_residues(seed, (n, n), p, 10))
+    xb = dev_i32(fm_inputs.uniform_residues(seed, (n, n), p, 11))
+    res = []
+    for lt, algo in ((7, fm.FM_ALGO_LIMB_TC), (6, fm.FM_ALGO_PLAIN)):
+        (tA, mA), (tB, mB), (tC, mC) = morton(n, lt), morton(n, lt), morton(n, lt)
+        fm.fm_layout_to_morton(xa, n, n, n, mA, s)
+        fm.fm_layout_to_morton(xb, n, n, n, mB, s)
+        sub = [fm.sub(m_, 0, 0, n, n) for m_ in (mC, mA, mB)]
+        run = lambda: fm.fm_gemm_modp(sub[0], sub[1], sub[2], p, fm.FM_OP_SET, algo, None, s)  # noqa: E731
+        if algo == fm.FM_ALGO_LIMB_TC:
+            ms = timed(run, 5)
+        else:
+            run()
+        o = torch.empty((n, n), dtype=torch.int32, device=dev)
+        fm.fm_layout_from_morton(mC, n, n, o, n, s)
+        res.append(o)
+        del tA, tB, tC
+    torch.cuda.synchronize()
+    same = bool(torch.equal(res[0], res[1]))
+    del xa, xb, res
+    _, sustained, _, src = measured_peaks()
+    mma = 16 * 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    out["p31"] = {"workload": "C = A*B mod 2^31-1, M=N=K=4096, Morton-hybrid T'=128, limb form (4 limbs, "
+                              "16 limb products)", "ms": ms, "value": 2.0 * n ** 3 / (ms / 1e3) / 1e9,
+                  "unit": "Gop/s", "mma_tflops": mma, "frac_of_tensor_peak": mma / sustained,
+                  "peak_source": f"bf16 sustained, {src}", "bit_identical_to_plain": same}
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_gf2(fm, torch, dev, stream, n=8192, paper_n=2048, paper_calls=468, seed=7):
@@ -776,6 +920,8 @@ def run_fm(args, world, rank, local):
         out["tu"] = run_tu(fm, torch, dev, stream)
     if not args.no_gf2:
         out["gf2"] = run_gf2(fm, torch, dev, stream)
+    if not args.no_configs:
+        out["configs"] = run_configs(fm, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
     burst, sustained, hbm, src = measured_peaks()
@@ -819,6 +965,8 @@ def run_fm(args, world, rank, local):
         line["tu"] = out["tu"]
     if "gf2" in out:
         line["gf2"] = out["gf2"]
+    if "configs" in out:
+        line["configs"] = out["configs"]
     if "plain" in out:
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]
