@@ -23,6 +23,8 @@ gf2       = C += A*B over GF(2) on bit-packed Morton-hybrid matrices (the
 configs   = the other workloads: 256^3 (launch-latency bound, next to the floor of
             one launch), the 3000 x 1700 x 2200 Schur update with permuted
             conversion, and 4096^3 at p = 2^31 - 1 on the limb form
+curves    = Morton-hybrid against Hilbert-hybrid tile order: layout conversion
+            and the permutation gather (index conversion per entry)
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fm|reference]
 For N > 1 launch with torchrun; every rank runs an independent replica.
@@ -555,6 +557,62 @@ def run_configs(fm, torch, dev, stream, seed=21):
     return out
 
 
+def run_curves(fm, torch, dev, stream, n=8192, seed=31):
+    """The curve comparison of Sec. 1 on this GPU: layout conversion (one index
+    conversion per tile) and the row/column permutation gather (one index
+    conversion per entry) at n x n, for the Morton-hybrid and the Hilbert-hybrid
+    layouts, at T' = 32 and 128. Rates are bytes moved (4 B read + 4 B written
+    per entry) per second; the two curves' results are checked to hold the same
+    matrix."""
+    import numpy as np
+
+    import fm_inputs
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    s = stream.cuda_stream
+    x = torch.from_numpy(fm_inputs.uniform_residues(seed, (n, n), 65521).view(np.int32)).to(dev)
+    rp = torch.from_numpy(fm_inputs.permutation(seed, n, 1).view(np.int32)).to(dev)
+    cp = torch.from_numpy(fm_inputs.permutation(seed, n, 2).view(np.int32)).to(dev)
+    buf = [torch.empty(n * n, dtype=torch.int32, device=dev) for _ in range(2)]
+    scratch = torch.empty((n, n), dtype=torch.int32, device=dev)
+    permuted = {k: torch.empty((n, n), dtype=torch.int32, device=dev) for k in ("morton", "hilbert")}
+    gbs = lambda ms: 8.0 * n * n / (ms / 1e3) / 1e9  # noqa: E731
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    for lt in (5, 7):
+        lg = (n >> lt).bit_length() - 1
+        m0, m1 = fm.matrix(buf[0], lg, lt), fm.matrix(buf[1], lg, lt)
+        row = {}
+        for name, to_, from_, perm in (
+                ("morton", fm.fm_layout_to_morton, fm.fm_layout_from_morton, fm.fm_permute_rows_cols),
+                ("hilbert", fm.fm_layout_to_hilbert, fm.fm_layout_from_hilbert, fm.fm_permute_rows_cols_hilbert)):
+            t_to = timed(lambda: to_(x, n, n, n, m0, s))
+            t_from = timed(lambda: from_(m0, n, n, scratch, n, s))
+            t_perm = timed(lambda: perm(m0, m1, n, n, rp, cp, s))
+            from_(m1, n, n, permuted[name], n, s)
+            row[name] = {"to_layout_gbs": gbs(t_to), "from_layout_gbs": gbs(t_from),
+                         "permute_gbs": gbs(t_perm), "permute_ms": t_perm}
+        torch.cuda.synchronize()
+        row["same_permuted_matrix"] = bool(torch.equal(permuted["morton"], permuted["hilbert"]))
+        row["hilbert_over_morton_permute_time"] = row["hilbert"]["permute_ms"] / row["morton"]["permute_ms"]
+        res[f"T'={1 << lt}"] = row
+    del x, rp, cp, buf, scratch, permuted
+    torch.cuda.empty_cache()
+    return {"workload": f"{n} x {n} residues: row-major <-> curve layout, and the row/column "
+                        "permutation gather inside the layout", "unit": "GB/s", "by_T": res}
+
+
 def run_gf2(fm, torch, dev, stream, n=8192, paper_n=2048, paper_calls=468, seed=7):
     """GF(2) on bit-packed Morton-hybrid matrices (T' = 32): C += A*B at n, checked
     bit-identical to the uint32 limb form at p = 2 on the same inputs, then timed
@@ -922,6 +980,7 @@ def run_fm(args, world, rank, local):
         out["gf2"] = run_gf2(fm, torch, dev, stream)
     if not args.no_configs:
         out["configs"] = run_configs(fm, torch, dev, stream)
+        out["curves"] = run_curves(fm, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
     burst, sustained, hbm, src = measured_peaks()
@@ -967,6 +1026,7 @@ def run_fm(args, world, rank, local):
         line["gf2"] = out["gf2"]
     if "configs" in out:
         line["configs"] = out["configs"]
+        line["curves"] = out["curves"]
     if "plain" in out:
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]

@@ -143,6 +143,25 @@ int fm_layout_from_morton_u16(fm_matrix src, int64_t rows, int64_t cols, uint16_
 int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
                          const int32_t* row_perm, const int32_t* col_perm, fm_stream stream);
 
+/* ---- curve variant: Hilbert-hybrid ----------------------------------------
+ * Sec. 1 picks the Morton-hybrid order because its index conversion costs the
+ * least among the Hilbert, Peano and Morton orders. A Hilbert-hybrid matrix is
+ * an fm_matrix whose T' x T' row-major tiles follow the Hilbert curve over the
+ * 2^log2_grid x 2^log2_grid tile grid instead of the Z curve: tile (I, J)
+ * starts at H(I, J) * T'^2, where the order-1 curve visits (I, J) = (0, 0),
+ * (0, 1), (1, 1), (1, 0) and each quadrant holds the order-(k-1) curve, the
+ * first transposed and the last reflected across the anti-diagonal. Only the
+ * three calls below take Hilbert-hybrid matrices (the products take
+ * Morton-hybrid ones); arguments and errors as for their Morton-hybrid
+ * counterparts. */
+int fm_layout_to_hilbert(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                         fm_matrix dst, fm_stream stream);
+int fm_layout_from_hilbert(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst, int64_t ld,
+                           fm_stream stream);
+int fm_permute_rows_cols_hilbert(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
+                                 const int32_t* row_perm, const int32_t* col_perm,
+                                 fm_stream stream);
+
 /* ---- the modular product (Sec. 2, 2.2) ---------------------------------- */
 
 /* C <- C op A*B mod p on sub-matrices: C is rows x cols, A is C.rows x K,

@@ -26,6 +26,9 @@ What the oracle computes, each part citing the passage it follows:
   and rank; the paper defers TURBO's details to its reference, so the textbook
   elimination stands in).
 * ``freivalds``: probabilistic check of a product through ``matvec_modp``.
+* ``hilbert``: the Hilbert-hybrid layout (the curve Sec. 1 weighs against the
+  Morton-hybrid order), built from the curve's recursive definition (module
+  ``oracle.hilbert``).
 * ``gf2_pack`` / ``gf2_unpack``: the bit-packed Morton-hybrid matrix over GF(2)
   (the field of the experiments, Sec. 2.2 "Performance Analysis", T' = 32): the
   Morton-hybrid element order with 32 consecutive entries per word, entry e of

@@ -68,6 +68,44 @@ __host__ __device__ __forceinline__ void fm_extract(uint64_t z, int lt, uint64_t
     *j = (fm_compact_bits(tz) << lt) | (off & mask);
 }
 
+// Hilbert-hybrid variant (the curve Sec. 1 weighs against Morton's for index
+// conversion cost): tile (I, J) of a 2^lg x 2^lg grid sits at position
+// H(I, J) of the Hilbert curve, whose order-1 pattern visits (I, J) = (0, 0),
+// (0, 1), (1, 1), (1, 0). Going down one level per bit: the quadrant's rank
+// along the curve is appended to the index, and the coordinates inside the
+// quadrant are mapped onto the order-(level-1) curve -- the first quadrant is
+// traversed transposed, the last anti-transposed (reflected across the other
+// diagonal), the middle two as they are.
+__host__ __device__ __forceinline__ uint64_t fm_hilbert_tile(uint64_t I, uint64_t J, int lg)
+{
+    uint64_t d = 0;
+    for (int b = lg - 1; b >= 0; --b) {
+        const uint64_t qi = (I >> b) & 1, qj = (J >> b) & 1;
+        d = (d << 2) | (qi << 1) | (qi ^ qj);
+        const uint64_t low = (1ull << b) - 1;
+        const uint64_t i = I & low, j = J & low;
+        if (!qi && !qj) {
+            I = j;
+            J = i;
+        } else if (qi && !qj) {
+            I = low - j;
+            J = low - i;
+        } else {
+            I = i;
+            J = j;
+        }
+    }
+    return d;
+}
+
+// Hilbert-hybrid index of Cartesian (i, j): tile base H(I, J) T'^2 plus the
+// row-major offset inside the tile, T' = 2^lt, 2^lg tiles per side.
+__host__ __device__ __forceinline__ uint64_t fm_hilbert_encode(uint64_t i, uint64_t j, int lg, int lt)
+{
+    const uint64_t mask = (1ull << lt) - 1;
+    return (fm_hilbert_tile(i >> lt, j >> lt, lg) << (2 * lt)) | ((i & mask) << lt) | (j & mask);
+}
+
 __host__ __device__ __forceinline__ int64_t fm_side(const fm_matrix& m)
 {
     return (int64_t)1 << (m.log2_grid + m.log2_T);

@@ -8,6 +8,9 @@
 // row-major side in row segments of T' elements. The row-major side holds
 // 32-bit entries, or 16-bit ones (residues mod p < 2^16: half the bytes to
 // move, e.g. across the host link); the Morton-hybrid side is always 32-bit.
+// The same kernels also lay the tiles along the Hilbert curve instead of the
+// Z curve (the Hilbert-hybrid variant, for comparing the curves' index
+// conversion cost).
 #include <algorithm>
 
 #include "fm_internal.cuh"
@@ -43,8 +46,24 @@ __device__ __forceinline__ void st4(uint16_t* p, uint4 v)
 template <typename T>
 constexpr uintptr_t kVec4Align = 4 * sizeof(T) - 1;
 
+// The curve the tiles follow: the Z curve (Morton-hybrid) or the Hilbert
+// curve (Hilbert-hybrid); tiles are T' x T' row-major in both.
+enum { kMorton = 0, kHilbert = 1 };
+
+template <int CURVE>
+__device__ __forceinline__ uint64_t curve_tile_base(uint64_t I, uint64_t J, int lg, int lt)
+{
+    return CURVE == kHilbert ? fm_hilbert_tile(I, J, lg) << (2 * lt) : fm_tile_base(I, J, lt);
+}
+
+template <int CURVE>
+__device__ __forceinline__ uint64_t curve_encode(uint64_t i, uint64_t j, int lg, int lt)
+{
+    return CURVE == kHilbert ? fm_hilbert_encode(i, j, lg, lt) : fm_encode(i, j, lt);
+}
+
 // dst(i, j) = src[rp(i) * ld + cp(j)] (0 outside rows x cols), dst Morton.
-template <bool kPerm, typename T>
+template <bool kPerm, typename T, int CURVE = kMorton>
 __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict__ src,
                                                              int64_t rows, int64_t cols, int64_t ld,
                                                              const int32_t* __restrict__ rp,
@@ -62,14 +81,14 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
         // the reads are a random gather inside each source row, so tiles are
         // walked row band by row band to keep one band of source rows in L2.
         uint64_t I, J;
-        if (kPerm) {
+        if (kPerm || CURVE == kHilbert) {
             I = (uint64_t)t >> lg;
             J = (uint64_t)t & ((1ull << lg) - 1);
         } else {
             I = fm_compact_bits((uint64_t)t >> 1);
             J = fm_compact_bits((uint64_t)t);
         }
-        uint32_t* tile = dst + fm_tile_base(I, J, lt);
+        uint32_t* tile = dst + curve_tile_base<CURVE>(I, J, lg, lt);
         const int64_t i_base = (int64_t)I << lt, j_base = (int64_t)J << lt;
         if (lt >= 2) {
             for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
@@ -148,7 +167,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // dst[i * ld + j] = src(i, j) for i < rows, j < cols, src Morton.
-template <typename E>
+template <typename E, int CURVE = kMorton>
 __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* __restrict__ src,
                                                                int lg, int lt, int64_t rows,
                                                                int64_t cols, E* __restrict__ dst,
@@ -164,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* _
     (void)tiles_side;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t I = t / tc, J = t % tc;
-        const uint32_t* tile = src + fm_tile_base((uint64_t)I, (uint64_t)J, lt);
+        const uint32_t* tile = src + curve_tile_base<CURVE>((uint64_t)I, (uint64_t)J, lg, lt);
         const int64_t i_base = I << lt, j_base = J << lt;
         if (lt >= 2) {
             for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
@@ -191,8 +210,10 @@ __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* _
     }
 }
 
-// dst(i, j) = src(rp[i], cp[j]) for i < rows, j < cols, else 0; both Morton.
-__global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __restrict__ src,
+// dst(i, j) = src(rp[i], cp[j]) for i < rows, j < cols, else 0; both on the
+// same curve. Every entry's source index is converted from Cartesian order.
+template <int CURVE = kMorton>
+__global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __restrict__ src, int lgs,
                                                            int lts, uint32_t* __restrict__ dst,
                                                            int lgd, int ltd, int64_t rows,
                                                            int64_t cols,
@@ -203,9 +224,9 @@ __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __res
     const int64_t tile_elems = (int64_t)1 << (2 * ltd);
     const int64_t Td = (int64_t)1 << ltd;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t I = fm_compact_bits((uint64_t)t >> 1);
-        const uint64_t J = fm_compact_bits((uint64_t)t);
-        uint32_t* tile = dst + (t << (2 * ltd));
+        const uint64_t I = CURVE == kHilbert ? (uint64_t)t >> lgd : fm_compact_bits((uint64_t)t >> 1);
+        const uint64_t J = CURVE == kHilbert ? (uint64_t)t & ((1ull << lgd) - 1) : fm_compact_bits((uint64_t)t);
+        uint32_t* tile = dst + curve_tile_base<CURVE>(I, J, lgd, ltd);
         const int64_t i_base = (int64_t)I << ltd, j_base = (int64_t)J << ltd;
         for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
             const int64_t i = i_base + (e >> ltd);
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __res
             if (i < rows && j < cols) {
                 const uint64_t si = rp ? (uint64_t)__ldg(rp + i) : (uint64_t)i;
                 const uint64_t sj = cp ? (uint64_t)__ldg(cp + j) : (uint64_t)j;
-                v = __ldg(src + fm_encode(si, sj, lts));
+                v = __ldg(src + curve_encode<CURVE>(si, sj, lgs, lts));
             }
             tile[e] = v;
         }
@@ -253,7 +274,7 @@ int grid_for(int64_t tiles)
     return (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
 }
 
-template <typename T>
+template <typename T, int CURVE = kMorton>
 int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const int32_t* rp,
                    const int32_t* cp, fm_matrix dst, fm_stream stream)
 {
@@ -263,7 +284,7 @@ int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const i
     if ((rows > 0 && cols > 0) && src == nullptr) return FM_EINVAL;
     const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
     const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
-    if (cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
+    if (CURVE == kMorton && cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
         const int64_t n = fm_side(dst);
         const int grid = (int)std::min<int64_t>(n, (int64_t)fm_sm_count() * 8);
         FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel<T>,
@@ -271,16 +292,16 @@ int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const i
         to_morton_rowgather_kernel<T><<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
     } else if (rp || cp)
-        to_morton_kernel<true, T><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        to_morton_kernel<true, T, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
     else
-        to_morton_kernel<false, T><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        to_morton_kernel<false, T, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, nullptr, nullptr, dst.base, dst.log2_grid, dst.log2_T);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
 }
 
-template <typename E>
+template <typename E, int CURVE = kMorton>
 int from_morton_impl(fm_matrix src, int64_t rows, int64_t cols, E* dst, int64_t ld, fm_stream stream)
 {
     FM_TRY(fm_check_matrix(src));
@@ -290,7 +311,7 @@ int from_morton_impl(fm_matrix src, int64_t rows, int64_t cols, E* dst, int64_t 
     if (dst == nullptr) return FM_EINVAL;
     const int64_t T = (int64_t)1 << src.log2_T;
     const int64_t tiles = ((rows + T - 1) / T) * ((cols + T - 1) / T);
-    from_morton_kernel<E><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+    from_morton_kernel<E, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
         src.base, src.log2_grid, src.log2_T, rows, cols, dst, ld);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
@@ -359,11 +380,12 @@ extern "C" int fm_validate_residues(fm_sub X, uint32_t p, fm_stream stream)
     return FM_OK;
 }
 
-extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
-                                    const int32_t* row_perm, const int32_t* col_perm,
-                                    fm_stream stream)
+namespace {
+
+template <int CURVE>
+int permute_impl(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols, const int32_t* row_perm,
+                 const int32_t* col_perm, fm_stream stream)
 {
-    FmRange range("fm_permute_rows_cols");
     FM_TRY(fm_check_matrix(src));
     FM_TRY(fm_check_matrix(dst));
     const int64_t ns = fm_side(src), nd = fm_side(dst);
@@ -372,8 +394,41 @@ extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, 
     const uintptr_t s0 = (uintptr_t)src.base, d0 = (uintptr_t)dst.base;
     if (s0 < d0 + dbytes && d0 < s0 + sbytes) return FM_EINVAL;  // src and dst overlap
     const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
-    permute_kernel<<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
-        src.base, src.log2_T, dst.base, dst.log2_grid, dst.log2_T, rows, cols, row_perm, col_perm);
+    permute_kernel<CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
+        src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid, dst.log2_T, rows, cols, row_perm,
+        col_perm);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
+}
+
+}  // namespace
+
+extern "C" int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
+                                    const int32_t* row_perm, const int32_t* col_perm,
+                                    fm_stream stream)
+{
+    FmRange range("fm_permute_rows_cols");
+    return permute_impl<kMorton>(src, dst, rows, cols, row_perm, col_perm, stream);
+}
+
+extern "C" int fm_layout_to_hilbert(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
+                                    fm_matrix dst, fm_stream stream)
+{
+    FmRange range("fm_layout_to_hilbert");
+    return to_morton_impl<uint32_t, kHilbert>(src, rows, cols, ld, nullptr, nullptr, dst, stream);
+}
+
+extern "C" int fm_layout_from_hilbert(fm_matrix src, int64_t rows, int64_t cols, uint32_t* dst,
+                                      int64_t ld, fm_stream stream)
+{
+    FmRange range("fm_layout_from_hilbert");
+    return from_morton_impl<uint32_t, kHilbert>(src, rows, cols, dst, ld, stream);
+}
+
+extern "C" int fm_permute_rows_cols_hilbert(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
+                                            const int32_t* row_perm, const int32_t* col_perm,
+                                            fm_stream stream)
+{
+    FmRange range("fm_permute_rows_cols_hilbert");
+    return permute_impl<kHilbert>(src, dst, rows, cols, row_perm, col_perm, stream);
 }

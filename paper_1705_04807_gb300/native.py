@@ -26,7 +26,7 @@ FM_LIMB_A, FM_LIMB_B = 0, 1
 EXPORTS = (
     "fm_layout_to_morton", "fm_layout_to_morton_permuted", "fm_layout_from_morton",
     "fm_layout_to_morton_u16", "fm_layout_to_morton_permuted_u16", "fm_layout_from_morton_u16",
-    "fm_validate_residues",
+    "fm_validate_residues", "fm_layout_to_hilbert", "fm_layout_from_hilbert", "fm_permute_rows_cols_hilbert",
     "fm_permute_rows_cols", "fm_gemm_modp", "fm_gemm_modp_workspace_size", "fm_plan_create",
     "fm_gemm_modp_batched", "fm_plan_work_items", "fm_plan_launches", "fm_plan_destroy", "fm_decompose",
     "fm_get_last_device_status", "fm_strerror", "fm_release_workspace", "fm_version",
@@ -109,6 +109,9 @@ def lib():
         "fm_layout_to_morton_permuted_u16": ([P, I64, I64, I64, P, P, fm_matrix, P], ctypes.c_int),
         "fm_layout_from_morton_u16": ([fm_matrix, I64, I64, P, I64, P], ctypes.c_int),
         "fm_validate_residues": ([fm_sub, ctypes.c_uint32, P], ctypes.c_int),
+        "fm_layout_to_hilbert": ([P, I64, I64, I64, fm_matrix, P], ctypes.c_int),
+        "fm_layout_from_hilbert": ([fm_matrix, I64, I64, P, I64, P], ctypes.c_int),
+        "fm_permute_rows_cols_hilbert": ([fm_matrix, fm_matrix, I64, I64, P, P, P], ctypes.c_int),
         "fm_permute_rows_cols": ([fm_matrix, fm_matrix, I64, I64, P, P, P], ctypes.c_int),
         "fm_gemm_modp": ([fm_sub, fm_sub, fm_sub, U32, I32, I32, ctypes.POINTER(fm_opts), P],
                          ctypes.c_int),
@@ -247,6 +250,23 @@ def fm_layout_to_morton_permuted_u16(src, rows, cols, ld, row_perm, col_perm, ds
 def fm_layout_from_morton_u16(src: fm_matrix, rows, cols, dst, ld, stream=None):
     return _check(lib().fm_layout_from_morton_u16(src, rows, cols, _ptr(dst), ld, _stream(stream)),
                   "fm_layout_from_morton_u16")
+
+
+def fm_layout_to_hilbert(src, rows, cols, ld, dst: fm_matrix, stream=None):
+    return _check(lib().fm_layout_to_hilbert(_ptr(src), rows, cols, ld, dst, _stream(stream)),
+                  "fm_layout_to_hilbert")
+
+
+def fm_layout_from_hilbert(src: fm_matrix, rows, cols, dst, ld, stream=None):
+    return _check(lib().fm_layout_from_hilbert(src, rows, cols, _ptr(dst), ld, _stream(stream)),
+                  "fm_layout_from_hilbert")
+
+
+def fm_permute_rows_cols_hilbert(src: fm_matrix, dst: fm_matrix, rows, cols, row_perm, col_perm,
+                                 stream=None):
+    return _check(lib().fm_permute_rows_cols_hilbert(src, dst, rows, cols, _ptr(row_perm),
+                                                     _ptr(col_perm), _stream(stream)),
+                  "fm_permute_rows_cols_hilbert")
 
 
 def fm_validate_residues(X: fm_sub, p: int, stream=None):

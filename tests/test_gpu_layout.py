@@ -153,3 +153,30 @@ def test_validate_residues(env, lt, row0, col0, rows, cols):
     M.load(y)
     fm.fm_validate_residues(X, p)
     assert fm.fm_get_last_device_status() == 0
+
+
+@pytest.mark.parametrize("rows,cols,ld,lg,lt", [(37, 53, 53, 2, 4), (300, 301, 304, 3, 6), (130, 250, 251, 1, 7),
+                                                (5, 3, 7, 3, 0), (64, 64, 64, 0, 6), (200, 100, 100, 5, 3)])
+def test_hilbert_layout_matches_oracle(env, orc, rows, cols, ld, lg, lt):
+    # the Hilbert-hybrid variant: conversion both ways and the permutation
+    # gather against the oracle's curve (built by its recursive definition)
+    import torch
+    from oracle import hilbert
+    fm, dev = env
+    x = fm_inputs.uniform_residues(rows * 5 + cols, (rows, ld), 65521)
+    H = MortonMatrix(fm, dev, lg, lt)
+    H.t.fill_(-1)
+    fm.fm_layout_to_hilbert(to_dev(x, dev), rows, cols, ld, H.m)
+    assert np.array_equal(to_host(H.t), hilbert.to_hilbert(x[:, :cols], lg, 1 << lt))
+    out = torch.full((rows, ld), -1, dtype=torch.int32, device=dev)
+    fm.fm_layout_from_hilbert(H.m, rows, cols, out, ld)
+    back = to_host(out)
+    assert np.array_equal(back[:, :cols], x[:, :cols])
+    assert np.all(back[:, cols:] == 0xFFFFFFFF)
+    rp = fm_inputs.permutation(lt + 1, rows, 1)
+    cp = fm_inputs.permutation(lt + 1, cols, 2)
+    D = MortonMatrix(fm, dev, lg, lt)
+    D.t.fill_(-1)
+    fm.fm_permute_rows_cols_hilbert(H.m, D.m, rows, cols, to_dev(rp, dev), to_dev(cp, dev))
+    want = hilbert.to_hilbert(orc.permute(x[:, :cols], rp, cp), lg, 1 << lt)
+    assert np.array_equal(to_host(D.t), want)
