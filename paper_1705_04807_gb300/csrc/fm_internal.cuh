@@ -98,6 +98,34 @@ __host__ __device__ __forceinline__ uint64_t fm_hilbert_tile(uint64_t I, uint64_
     return d;
 }
 
+// The tile at position d of the Hilbert curve (the inverse of fm_hilbert_tile):
+// built up from the lowest level, each level's quadrant rank placing the cell
+// found so far inside that quadrant of the next larger curve (transposed in the
+// first quadrant, reflected across the anti-diagonal in the last).
+__host__ __device__ __forceinline__ void fm_hilbert_cell(uint64_t d, int lg, uint64_t* I, uint64_t* J)
+{
+    uint64_t i = 0, j = 0;
+    for (int b = 0; b < lg; ++b) {
+        const uint64_t q = (d >> (2 * b)) & 3, s = 1ull << b;
+        if (q == 0) {
+            const uint64_t t = i;
+            i = j;
+            j = t;
+        } else if (q == 1) {
+            j += s;
+        } else if (q == 2) {
+            i += s;
+            j += s;
+        } else {
+            const uint64_t ni = 2 * s - 1 - j, nj = s - 1 - i;
+            i = ni;
+            j = nj;
+        }
+    }
+    *I = i;
+    *J = j;
+}
+
 // Hilbert-hybrid index of Cartesian (i, j): tile base H(I, J) T'^2 plus the
 // row-major offset inside the tile, T' = 2^lt, 2^lg tiles per side.
 __host__ __device__ __forceinline__ uint64_t fm_hilbert_encode(uint64_t i, uint64_t j, int lg, int lt)

@@ -77,18 +77,25 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
     const bool vec_ok = (!kPerm || cp == nullptr) && lt >= 2 && ((ld & 3) == 0) &&
                         (((uintptr_t)src & kVec4Align<T>) == 0);
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        // Z order keeps the Morton writes sequential; with a column permutation
-        // the reads are a random gather inside each source row, so tiles are
-        // walked row band by row band to keep one band of source rows in L2.
+        // Walking the tiles in the curve's own order (Z or Hilbert) keeps the
+        // destination writes sequential; with a permutation the reads are a
+        // random gather inside each source row, so tiles are walked row band
+        // by row band to keep one band of source rows in L2.
         uint64_t I, J;
-        if (kPerm || CURVE == kHilbert) {
+        uint32_t* tile;
+        if (kPerm) {
             I = (uint64_t)t >> lg;
             J = (uint64_t)t & ((1ull << lg) - 1);
+            tile = dst + curve_tile_base<CURVE>(I, J, lg, lt);
         } else {
-            I = fm_compact_bits((uint64_t)t >> 1);
-            J = fm_compact_bits((uint64_t)t);
+            if (CURVE == kHilbert) {
+                fm_hilbert_cell((uint64_t)t, lg, &I, &J);
+            } else {
+                I = fm_compact_bits((uint64_t)t >> 1);
+                J = fm_compact_bits((uint64_t)t);
+            }
+            tile = dst + ((uint64_t)t << (2 * lt));
         }
-        uint32_t* tile = dst + curve_tile_base<CURVE>(I, J, lg, lt);
         const int64_t i_base = (int64_t)I << lt, j_base = (int64_t)J << lt;
         if (lt >= 2) {
             for (int64_t e = 4 * (int64_t)threadIdx.x; e < tile_elems; e += 4 * kThreads) {
