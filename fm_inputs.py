@@ -127,3 +127,28 @@ def sub_rectangles(seed: int, count: int, n: int, min_dim: int = 1,
         for q in range(6):
             out[t, 3 + q] = int(u[t, q]) % spans[q]
     return out
+
+
+def batch_workload(seed: int, count: int = 4096, lo: int = 32, hi: int = 512,
+                   big: int = 16384) -> tuple:
+    """The independent-call batch: ``count`` products with M, N, K uniform in
+    [lo, hi]. Call c writes the top-left M x N corner of its own hi x hi cell of
+    a C matrix with ``cells`` x ``cells`` cells (cells the smallest power of two
+    with cells^2 >= count; cell c at row (c // cells) * hi, column
+    (c % cells) * hi); its A and B parts are random rectangles of two shared
+    big x big matrices (reads may overlap).
+
+    Returns (rows, cells): rows as int64 (count, 9) =
+    (M, N, K, row0_C, col0_C, row0_A, col0_A, row0_B, col0_B)."""
+    cells = 1
+    while cells * cells < count:
+        cells *= 2
+    shapes = batch_shapes(seed, count, lo, hi)
+    offs = raw_u64(seed, 4 * count, 9).reshape(count, 4)
+    out = np.zeros((count, 9), dtype=np.int64)
+    for c in range(count):
+        M, N, K = (int(x) for x in shapes[c])
+        out[c] = (M, N, K, (c // cells) * hi, (c % cells) * hi,
+                  int(offs[c, 0]) % (big - M + 1), int(offs[c, 1]) % (big - K + 1),
+                  int(offs[c, 2]) % (big - K + 1), int(offs[c, 3]) % (big - N + 1))
+    return out, cells

@@ -112,8 +112,10 @@ int fm_layout_to_morton(const uint32_t* src, int64_t rows, int64_t cols, int64_t
 
 /* Same, with TURBO's permutations applied first (Sec. 1):
  * dst(i, j) = src[row_perm[i]*ld + col_perm[j]]; a NULL permutation is the
- * identity. Permutation entries must lie in [0, rows) / [0, cols) (not
- * checked on the device; out-of-range entries are undefined behaviour). */
+ * identity. Permutation entries must lie in [0, rows) / [0, cols). The kernel
+ * checks every entry it uses: one outside that range is never used as an
+ * index; the destination entries it would fill are set to 0 and FM_EINVAL is
+ * raised in the device status word (read with fm_get_last_device_status). */
 int fm_layout_to_morton_permuted(const uint32_t* src, int64_t rows, int64_t cols, int64_t ld,
                                  const int32_t* row_perm, const int32_t* col_perm,
                                  fm_matrix dst, fm_stream stream);
@@ -139,7 +141,13 @@ int fm_layout_from_morton_u16(fm_matrix src, int64_t rows, int64_t cols, uint16_
 /* Morton-hybrid to Morton-hybrid permutation (Sec. 1, TURBO's virtual row and
  * column permutations made explicit): dst(i, j) = src(row_perm[i], col_perm[j])
  * for i < rows, j < cols; the rest of dst is set to 0. src and dst must not
- * overlap and may have different T'. NULL permutation = identity. */
+ * overlap and may have different T'. NULL permutation = identity. Permutation
+ * entries must lie in [0, rows) / [0, cols); an entry outside is never used as
+ * an index: the entries it would fill are set to 0 and FM_EINVAL is raised in
+ * the device status word (read with fm_get_last_device_status). With T' >= 4
+ * on both sides and cols <= 51200 each source row is staged whole in shared
+ * memory (16-byte vectors in and out); otherwise entries are gathered one by
+ * one. */
 int fm_permute_rows_cols(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols,
                          const int32_t* row_perm, const int32_t* col_perm, fm_stream stream);
 
@@ -226,26 +234,31 @@ int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K
 
 /* ---- the limb product without allocation ----------------------------------
  * The paper has no counterpart: this is a library service. fm_gemm_modp
- * allocates its limb-plane workspace with cudaMalloc on first use. Callers that
- * must not allocate -- code running while a CUDA graph is captured, or
- * programs whose device memory comes only from their own allocator or a fixed
- * budget -- use this entry point instead. It computes exactly what
- * fm_gemm_modp with FM_ALGO_LIMB_TC computes (C <- C op A*B mod p on
- * Morton-hybrid sub-matrices, any T', default fm_opts) and allocates nothing:
- * its scratch is a fixed device array of 64 MiB of limb planes plus a status
- * word, compiled into the library (every GPU that loads it holds that array
- * until the process exits). A product whose limb planes need more than 64 MiB
- * returns FM_ETOOBIG (e.g. M = N = K = 2048 fits for p < 2^16; the planes take
- * 6 * K * (M + N) bytes for odd p < 2^16 with three planes, 8 * K * (M + N) for
- * p = 2^31 - 1, rounded up to whole tiles).
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. All calls share
- * the one array, so calls that can overlap on the GPU (different streams
- * without ordering) race and must be serialised by the caller; the array
- * keeps the last call's contents, and every call rewrites all of it that it
- * reads. A device-side wait that expires is recorded in the array's own status
- * word, which each call clears and no entry point reads: callers that need
- * that report use fm_gemm_modp and fm_get_last_device_status. */
+ * allocates its limb-plane workspace with cudaMalloc on first use. Some callers
+ * cannot let a library do that: programs whose device memory comes only from
+ * their own allocator or a fixed budget (a serving process that reserves the
+ * GPU's memory for its pool at start-up, where a hidden cudaMalloc can fail at
+ * any point or take memory a co-tenant counted on), and code that must not
+ * stall on the device synchronisation cudaMalloc and cudaFree imply. They use
+ * this entry point instead. It computes exactly what fm_gemm_modp with
+ * FM_ALGO_LIMB_TC computes (C <- C op A*B mod p on Morton-hybrid sub-matrices,
+ * any T', default fm_opts) and allocates nothing: its scratch is a fixed
+ * device array of 64 MiB of limb planes plus a status word, compiled into the
+ * library (every GPU that loads it holds that array until the process exits).
+ * A product whose limb planes need more than 64 MiB returns FM_ETOOBIG (e.g.
+ * M = N = K = 2048 fits for p < 2^16; the planes take 6 * K * (M + N) bytes for
+ * odd p < 2^16 with three planes, 8 * K * (M + N) for p = 2^31 - 1, rounded up
+ * to whole tiles). Calls with M, N or K equal to 0 touch no scratch (K = 0
+ * with FM_OP_SET zeroes the C sub-matrix; with ADD or SUB it leaves C as is).
+ * The first call on a device that multiplies (K > 0) does that device's
+ * one-time set-up: it looks up the array's device address and queries how
+ * many CTA pairs of the limb kernel fit at once; make that first call before
+ * any stream capture. All calls share the one array, so calls that can overlap
+ * on the GPU (different streams without ordering) race and must be serialised
+ * by the caller; the array keeps the last call's contents, and every call
+ * rewrites all of it that it reads. A device-side wait that expires raises
+ * FM_ETIMEOUT in the array's own status word; fm_get_last_device_status reads
+ * (and clears) that word together with the library's, without allocating. */
 int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, fm_stream stream);
 
 /* ---- TU decomposition (Sec. 1: the consumer of the product) ------------
@@ -429,9 +442,11 @@ int fm_gf2_plan_create(fm_plan** plan, const fm_gf2_call* calls, int64_t n, cons
  * FM_ETIMEOUT in the device status word and the kernel winds down, leaving the
  * context usable. This hook launches a kernel whose wait cannot complete so
  * that tests can watch that happen: which = 0, an mbarrier phase that nothing
- * completes; which = 1, a grid barrier that one CTA of the grid never reaches.
- * Returns launch errors only; the outcome is read with
- * fm_get_last_device_status. Nothing faults or hangs.
+ * completes; which = 1, a grid barrier that one CTA of the grid never reaches;
+ * which = 2, the mbarrier of which = 0 raising into the status word of
+ * fm_gemm_modp_noalloc's fixed scratch. Returns launch errors only (FM_EINVAL
+ * for another which); the outcome is read with fm_get_last_device_status.
+ * Nothing faults or hangs.
  *
  * Tracing: with the environment variable FM_TRACE set (to "1" for stderr, or
  * to a file path), every fm_gemm_modp, fm_gemm_modp_batched, fm_gf2_gemm and
@@ -441,8 +456,12 @@ int fm_debug_expire_wait(int32_t which, fm_stream stream);
 
 /* ---- status ------------------------------------------------------------- */
 
-/* Synchronises stream, returns and clears the device status word that
- * kernels raise on an expired bounded wait (FM_OK or FM_ETIMEOUT). */
+/* Synchronises stream, returns and clears the device status words that
+ * kernels raise into (FM_ETIMEOUT on an expired bounded wait, FM_ERANGE from
+ * fm_validate_residues, FM_EINVAL for an out-of-range permutation entry): the
+ * library's own word and that of fm_gemm_modp_noalloc's fixed scratch. Each
+ * word keeps the first code raised since it was last read; FM_OK if none.
+ * Allocates nothing. */
 int fm_get_last_device_status(fm_stream stream);
 
 /* Validation: every entry of the sub-matrix X must be a residue in [0, p)

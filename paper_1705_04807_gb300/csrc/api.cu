@@ -500,13 +500,25 @@ extern "C" int fm_plan_destroy(fm_plan* plan)
 // ---------------------------------------------------------------------------
 extern "C" int fm_get_last_device_status(fm_stream stream)
 {
-    int* st = fm_device_status();
-    if (!st) return FM_ECUDA;
+    const int d = current_device();
+    if (d < 0) return FM_ECUDA;
     FM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    int h = 0;
-    FM_CUDA_TRY(cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost));
-    FM_CUDA_TRY(cudaMemset(st, 0, sizeof(int)));
-    return h;
+    // No allocation here: a status word that does not exist yet has had no
+    // kernel raise into it.
+    int* st = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        st = g_dev[d].status;
+    }
+    int h = FM_OK;
+    if (st) {
+        FM_CUDA_TRY(cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost));
+        FM_CUDA_TRY(cudaMemset(st, 0, sizeof(int)));
+    }
+    // the word fm_gemm_modp_noalloc's kernels raise into
+    int h2 = FM_OK;
+    FM_TRY(fm_noalloc_take_status((cudaStream_t)stream, &h2));
+    return h != FM_OK ? h : h2;
 }
 
 extern "C" const char* fm_strerror(int status)

@@ -5,7 +5,11 @@
 // hook launches a kernel whose wait cannot complete, through the same wait code
 // the GEMM and PLUQ kernels use, so that a test can watch the limit expire and
 // the status arrive while the context stays usable. Nothing faults or hangs.
+// One kind raises into the status word of fm_gemm_modp_noalloc's fixed
+// scratch instead of the library's own, which shows that a wait that runs out
+// on that path reaches fm_get_last_device_status as well.
 #include "fm_internal.cuh"
+#include "fm_kernels.h"
 
 namespace {
 
@@ -36,10 +40,11 @@ __global__ void expire_grid_kernel(unsigned* bar, int* status)
 extern "C" int fm_debug_expire_wait(int32_t which, fm_stream stream)
 {
     FmRange range("fm_debug_expire_wait");
-    int* status = fm_device_status();
+    if (which < 0 || which > 2) return FM_EINVAL;
+    int* status = which == 2 ? fm_noalloc_status_word() : fm_device_status();
     if (!status) return FM_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    if (which == 0) {
+    if (which == 0 || which == 2) {
         expire_mbar_kernel<<<1, 32, 0, s>>>(status);
     } else if (which == 1) {
         unsigned* bar = static_cast<unsigned*>(fm_workspace(2, 2 * sizeof(unsigned)));

@@ -95,5 +95,16 @@ int fm_gf2_split_batch_run(int role, const FmSplitDesc* d_descs, const int2* d_j
 int fm_gf2_zero_sub(const fm_gf2_sub& C, cudaStream_t s);
 int fm_gf2_check_call(const fm_gf2_call& g);  // argument checks of fm_gf2_gemm
 
+// One-time per-device queries of the limb kernels (how many CTA pairs fit at
+// once), made ahead of the first launch that needs them (limb_gemm.cu).
+int fm_limb_prepare_device();
+
+// The fixed scratch of fm_gemm_modp_noalloc (noalloc.cu): the device address of
+// its status word on the current device (set up on first use), and a reader
+// that copies that word to *out and clears it (FM_OK in *out when no call has
+// used the array on this device).
+int* fm_noalloc_status_word();
+int fm_noalloc_take_status(cudaStream_t s, int* out);
+
 // Remembered autotune choice for a problem class (autotune.cu).
 bool fm_tuned_choice(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result* out);

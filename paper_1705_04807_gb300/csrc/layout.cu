@@ -63,19 +63,22 @@ __device__ __forceinline__ uint64_t curve_encode(uint64_t i, uint64_t j, int lg,
 }
 
 // dst(i, j) = src[rp(i) * ld + cp(j)] (0 outside rows x cols), dst Morton.
+// A permutation entry outside [0, rows) / [0, cols) is not dereferenced: the
+// entries it would fill become 0 and FM_EINVAL is raised in *status.
 template <bool kPerm, typename T, int CURVE = kMorton>
 __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict__ src,
                                                              int64_t rows, int64_t cols, int64_t ld,
                                                              const int32_t* __restrict__ rp,
                                                              const int32_t* __restrict__ cp,
                                                              uint32_t* __restrict__ dst, int lg,
-                                                             int lt)
+                                                             int lt, int* status)
 {
     const int64_t tiles = (int64_t)1 << (2 * lg);
     const int64_t tile_elems = (int64_t)1 << (2 * lt);
     // 16-byte row segments whenever no column permutation scatters them
     const bool vec_ok = (!kPerm || cp == nullptr) && lt >= 2 && ((ld & 3) == 0) &&
                         (((uintptr_t)src & kVec4Align<T>) == 0);
+    bool bad = false;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         // Walking the tiles in the curve's own order (Z or Hilbert) keeps the
         // destination writes sequential; with a permutation the reads are a
@@ -102,8 +105,15 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
                 const int64_t i = i_base + (e >> lt);
                 const int64_t j = j_base + (e & ((1 << lt) - 1));
                 uint4 v = make_uint4(0, 0, 0, 0);
-                if (i < rows) {
-                    const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
+                int64_t si = i < rows ? i : -1;
+                if (kPerm && rp && si >= 0) {
+                    si = (int64_t)__ldg(rp + i);
+                    if (si < 0 || si >= rows) {
+                        bad = true;
+                        si = -1;
+                    }
+                }
+                if (si >= 0) {
                     if (vec_ok && j + 3 < cols) {
                         v = ld4(src + si * ld + j);
                     } else {
@@ -111,8 +121,15 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int64_t jj = j + q;
-                            const int64_t sj = kPerm && cp && jj < cols ? (int64_t)__ldg(cp + jj) : jj;
-                            w[q] = jj < cols ? (uint32_t)__ldg(src + si * ld + sj) : 0u;
+                            int64_t sj = jj < cols ? jj : -1;
+                            if (kPerm && cp && sj >= 0) {
+                                sj = (int64_t)__ldg(cp + jj);
+                                if (sj < 0 || sj >= cols) {
+                                    bad = true;
+                                    sj = -1;
+                                }
+                            }
+                            w[q] = sj >= 0 ? (uint32_t)__ldg(src + si * ld + sj) : 0u;
                         }
                         v = make_uint4(w[0], w[1], w[2], w[3]);
                     }
@@ -127,32 +144,43 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
                 if (i < rows && j < cols) {
                     const int64_t si = kPerm && rp ? (int64_t)__ldg(rp + i) : i;
                     const int64_t sj = kPerm && cp ? (int64_t)__ldg(cp + j) : j;
-                    v = (uint32_t)__ldg(src + si * ld + sj);
+                    if (si >= 0 && si < rows && sj >= 0 && sj < cols)
+                        v = (uint32_t)__ldg(src + si * ld + sj);
+                    else
+                        bad = true;
                 }
                 tile[e] = v;
             }
         }
     }
+    if (kPerm && __syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
 // Column-permuted conversion: dst(i, j) = src[rp(i) * ld + cp(j)]. Each CTA
 // stages a whole source row in shared memory with coalesced 16-byte loads,
 // gathers the permuted columns from shared memory and writes the destination
 // row as contiguous runs of T' entries (one per Morton tile it crosses), so
-// HBM sees one read and one write per element.
+// HBM sees one read and one write per element. Out-of-range permutation
+// entries are not dereferenced (0 and FM_EINVAL, as above).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     to_morton_rowgather_kernel(const T* __restrict__ src, int64_t rows, int64_t cols,
                                int64_t ld, const int32_t* __restrict__ rp,
                                const int32_t* __restrict__ cp, uint32_t* __restrict__ dst, int lg,
-                               int lt)
+                               int lt, int* status)
 {
     extern __shared__ __align__(16) uint32_t srow[];
     const int64_t n = (int64_t)1 << (lg + lt);
     const bool vec = ((ld & 3) == 0) && (((uintptr_t)src & kVec4Align<T>) == 0);
+    bool bad = false;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-        if (i < rows) {
-            const T* sr = src + (rp ? (int64_t)__ldg(rp + i) : i) * ld;
+        int64_t si = i < rows ? (rp ? (int64_t)__ldg(rp + i) : i) : -1;
+        if (i < rows && (si < 0 || si >= rows)) {
+            bad = true;
+            si = -1;
+        }
+        if (si >= 0) {
+            const T* sr = src + si * ld;
             const int64_t c4 = vec ? cols / 4 : 0;
             for (int64_t q = threadIdx.x; q < c4; q += kThreads)
                 *reinterpret_cast<uint4*>(srow + 4 * q) = ld4(sr + 4 * q);
@@ -161,16 +189,24 @@ __global__ void __launch_bounds__(kThreads)
         __syncthreads();
         for (int64_t j = 4 * (int64_t)threadIdx.x; j < n; j += 4 * kThreads) {
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (i < rows) {
+            if (si >= 0) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j + q < cols) w[q] = srow[__ldg(cp + j + q)];
+                for (int q = 0; q < 4; ++q) {
+                    if (j + q < cols) {
+                        const int64_t sj = __ldg(cp + j + q);
+                        if (sj >= 0 && sj < cols)
+                            w[q] = srow[sj];
+                        else
+                            bad = true;
+                    }
+                }
             }
             *reinterpret_cast<uint4*>(dst + fm_encode((uint64_t)i, (uint64_t)j, lt)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
         __syncthreads();
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
 // dst[i * ld + j] = src(i, j) for i < rows, j < cols, src Morton.
@@ -219,17 +255,21 @@ __global__ void __launch_bounds__(kThreads) from_morton_kernel(const uint32_t* _
 
 // dst(i, j) = src(rp[i], cp[j]) for i < rows, j < cols, else 0; both on the
 // same curve. Every entry's source index is converted from Cartesian order.
+// The general form (any T'); permutations between layouts with T' >= 4 take
+// permute_staged_kernel below. Out-of-range permutation entries are not
+// dereferenced (0 and FM_EINVAL).
 template <int CURVE = kMorton>
 __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __restrict__ src, int lgs,
                                                            int lts, uint32_t* __restrict__ dst,
                                                            int lgd, int ltd, int64_t rows,
                                                            int64_t cols,
                                                            const int32_t* __restrict__ rp,
-                                                           const int32_t* __restrict__ cp)
+                                                           const int32_t* __restrict__ cp, int* status)
 {
     const int64_t tiles = (int64_t)1 << (2 * lgd);
     const int64_t tile_elems = (int64_t)1 << (2 * ltd);
     const int64_t Td = (int64_t)1 << ltd;
+    bool bad = false;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t I = CURVE == kHilbert ? (uint64_t)t >> lgd : fm_compact_bits((uint64_t)t >> 1);
         const uint64_t J = CURVE == kHilbert ? (uint64_t)t & ((1ull << lgd) - 1) : fm_compact_bits((uint64_t)t);
@@ -240,13 +280,94 @@ __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __res
             const int64_t j = j_base + (e & (Td - 1));
             uint32_t v = 0;
             if (i < rows && j < cols) {
-                const uint64_t si = rp ? (uint64_t)__ldg(rp + i) : (uint64_t)i;
-                const uint64_t sj = cp ? (uint64_t)__ldg(cp + j) : (uint64_t)j;
-                v = __ldg(src + curve_encode<CURVE>(si, sj, lgs, lts));
+                const int64_t si = rp ? (int64_t)__ldg(rp + i) : i;
+                const int64_t sj = cp ? (int64_t)__ldg(cp + j) : j;
+                if (si >= 0 && si < rows && sj >= 0 && sj < cols)
+                    v = __ldg(src + curve_encode<CURVE>((uint64_t)si, (uint64_t)sj, lgs, lts));
+                else
+                    bad = true;
             }
             tile[e] = v;
         }
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
+}
+
+// The same permutation, row-staged, for layouts with T' >= 4 on both sides:
+// one CTA per destination row at a time. The source row rp[i] is read from
+// the tiles it crosses as runs of T'_src contiguous entries (16-byte vectors,
+// one curve index conversion per vector) into shared memory; the destination
+// row is written as runs of T'_dst contiguous entries (16-byte vectors), each
+// entry gathered from shared memory through cp. HBM sees each entry read once
+// and written once in whole 16-byte vectors, against one scattered 4-byte read
+// per entry in permute_kernel. The last vector of a source row may read past
+// cols, but not past the tile (T'_src is a multiple of 4), and those entries are
+// never gathered. Out-of-range permutation entries are not dereferenced (0 and
+// FM_EINVAL).
+template <int CURVE = kMorton>
+__global__ void __launch_bounds__(kThreads)
+    permute_staged_kernel(const uint32_t* __restrict__ src, int lgs, int lts, uint32_t* __restrict__ dst,
+                          int lgd, int ltd, int64_t rows, int64_t cols, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ cp, int* status)
+{
+    extern __shared__ __align__(16) uint32_t srow[];
+    const int64_t nd = (int64_t)1 << (lgd + ltd);
+    const int64_t Ts = (int64_t)1 << lts, Td = (int64_t)1 << ltd;
+    const int64_t c4 = (cols + 3) >> 2;
+    const bool cp_vec = cp != nullptr && (((uintptr_t)cp & 15) == 0);
+    bool bad = false;
+    for (int64_t i = blockIdx.x; i < nd; i += gridDim.x) {
+        int64_t si = i < rows ? (rp ? (int64_t)__ldg(rp + i) : i) : -1;
+        if (i < rows && (si < 0 || si >= rows)) {
+            bad = true;
+            si = -1;
+        }
+        if (si >= 0) {
+            const uint64_t I = (uint64_t)si >> lts;
+            const uint64_t off = (uint64_t)(si & (Ts - 1)) << lts;
+#pragma unroll 4
+            for (int64_t q = threadIdx.x; q < c4; q += kThreads) {
+                const int64_t j = 4 * q;
+                const uint64_t a = curve_tile_base<CURVE>(I, (uint64_t)j >> lts, lgs, lts) + off +
+                                   (uint64_t)(j & (Ts - 1));
+                *reinterpret_cast<uint4*>(srow + j) = __ldg(reinterpret_cast<const uint4*>(src + a));
+            }
+        }
+        __syncthreads();
+        const uint64_t Id = (uint64_t)i >> ltd;
+        const uint64_t doff = (uint64_t)(i & (Td - 1)) << ltd;
+        for (int64_t j = 4 * (int64_t)threadIdx.x; j < nd; j += 4 * kThreads) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (si >= 0 && j < cols) {
+                int32_t sj[4];
+                if (cp_vec && j + 3 < cols) {
+                    const int4 v = __ldg(reinterpret_cast<const int4*>(cp + j));
+                    sj[0] = v.x;
+                    sj[1] = v.y;
+                    sj[2] = v.z;
+                    sj[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        sj[q] = j + q < cols ? (cp ? __ldg(cp + j + q) : (int32_t)(j + q)) : -1;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j + q < cols) {
+                        if (sj[q] >= 0 && sj[q] < cols)
+                            w[q] = srow[sj[q]];
+                        else
+                            bad = true;
+                    }
+                }
+            }
+            const uint64_t a = curve_tile_base<CURVE>(Id, (uint64_t)j >> ltd, lgd, ltd) + doff +
+                               (uint64_t)(j & (Td - 1));
+            *reinterpret_cast<uint4*>(dst + a) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
 // Raises FM_ERANGE in *status when an entry of the rows x cols sub-matrix at
@@ -289,21 +410,25 @@ int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const i
     const int64_t n = fm_side(dst);
     if (rows < 0 || cols < 0 || rows > n || cols > n || ld < cols) return FM_EINVAL;
     if ((rows > 0 && cols > 0) && src == nullptr) return FM_EINVAL;
+    int* status = nullptr;
+    if (rp || cp) {
+        status = fm_device_status();
+        if (!status) return FM_ECUDA;
+    }
     const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
     const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
     if (CURVE == kMorton && cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
-        const int64_t n = fm_side(dst);
         const int grid = (int)std::min<int64_t>(n, (int64_t)fm_sm_count() * 8);
         FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
         to_morton_rowgather_kernel<T><<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
-            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
+            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T, status);
     } else if (rp || cp)
         to_morton_kernel<true, T, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
-            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T);
+            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T, status);
     else
         to_morton_kernel<false, T, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
-            src, rows, cols, ld, nullptr, nullptr, dst.base, dst.log2_grid, dst.log2_T);
+            src, rows, cols, ld, nullptr, nullptr, dst.base, dst.log2_grid, dst.log2_T, nullptr);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
 }
@@ -389,6 +514,10 @@ extern "C" int fm_validate_residues(fm_sub X, uint32_t p, fm_stream stream)
 
 namespace {
 
+// Largest staged source row: the row-staged permutation keeps one source row of
+// up to this many bytes in shared memory.
+constexpr size_t kStagedRowMax = 200 * 1024;
+
 template <int CURVE>
 int permute_impl(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols, const int32_t* row_perm,
                  const int32_t* col_perm, fm_stream stream)
@@ -400,10 +529,25 @@ int permute_impl(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols, const
     const uint64_t sbytes = (uint64_t)ns * ns * 4, dbytes = (uint64_t)nd * nd * 4;
     const uintptr_t s0 = (uintptr_t)src.base, d0 = (uintptr_t)dst.base;
     if (s0 < d0 + dbytes && d0 < s0 + sbytes) return FM_EINVAL;  // src and dst overlap
-    const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
-    permute_kernel<CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
-        src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid, dst.log2_T, rows, cols, row_perm,
-        col_perm);
+    int* status = fm_device_status();
+    if (!status) return FM_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
+    if (src.log2_T >= 2 && dst.log2_T >= 2 && row_bytes <= kStagedRowMax) {
+        auto k = permute_staged_kernel<CURVE>;
+        FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedRowMax));
+        int per_sm = 0;
+        FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, row_bytes));
+        const int64_t cap = (int64_t)fm_sm_count() * std::max(1, per_sm);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nd, cap));
+        k<<<grid, kThreads, row_bytes, s>>>(src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid,
+                                            dst.log2_T, rows, cols, row_perm, col_perm, status);
+    } else {
+        const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
+        permute_kernel<CURVE><<<grid_for(tiles), kThreads, 0, s>>>(
+            src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid, dst.log2_T, rows, cols, row_perm,
+            col_perm, status);
+    }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
 }

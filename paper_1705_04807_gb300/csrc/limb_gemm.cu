@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fm_internal.cuh"
@@ -831,14 +832,48 @@ int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
     return FM_OK;
 }
 
+// How many CTA pairs of limb_gemm_pair_kernel<KIND> fit on the current device
+// at once; queried once per device and kind.
+template <int KIND>
+int pair_capacity(int* out)
+{
+    static std::mutex mu;
+    static int max_pairs[64] = {0};
+    int dev = 0;
+    FM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && max_pairs[dev] > 0) {
+        *out = max_pairs[dev];
+        return FM_OK;
+    }
+    auto k = limb_gemm_pair_kernel<KIND>;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * fm_sm_count());
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = kPairSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    FM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, k, &cfg));
+    n = n > 0 ? n : fm_sm_count() / 2;
+    if (dev < 64) max_pairs[dev] = n;
+    *out = n;
+    return FM_OK;
+}
+
 // Clusters of two CTAs, one per pair tile up to the number of pairs that fit
 // on the device at once (the kernel walks further tiles itself).
 template <int KIND>
 int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
 {
-    static int max_pairs[64] = {0};
-    int dev = 0;
-    FM_CUDA_TRY(cudaGetDevice(&dev));
+    int cap = 0;
+    FM_TRY(pair_capacity<KIND>(&cap));
     auto k = limb_gemm_pair_kernel<KIND>;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
     cudaLaunchConfig_t cfg = {};
@@ -852,13 +887,7 @@ int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (dev < 64 && max_pairs[dev] == 0) {
-        cfg.gridDim = dim3(2 * pair_tiles);
-        int n = 0;
-        FM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, k, &cfg));
-        max_pairs[dev] = n > 0 ? n : fm_sm_count() / 2;
-    }
-    const int pairs = std::max(1, std::min(pair_tiles, dev < 64 ? max_pairs[dev] : fm_sm_count() / 2));
+    const int pairs = std::max(1, std::min(pair_tiles, cap));
     cfg.gridDim = dim3(2 * pairs);
     FM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a));
     return FM_OK;
@@ -988,6 +1017,13 @@ int fm_gf2_plan(int64_t M, int64_t N, int64_t K, bool pair, FmLimbPlan* plan)
     q.b_plane_bytes = (size_t)q.NB * q.KB * 256 * 128;
     *plan = q;
     return FM_OK;
+}
+
+int fm_limb_prepare_device()
+{
+    int cap = 0;
+    FM_TRY(pair_capacity<kF16Res>(&cap));
+    return pair_capacity<kE4M3Gf2>(&cap);
 }
 
 size_t fm_limb_workspace_bytes(const FmLimbPlan& q)

@@ -278,3 +278,62 @@ def test_fused_batch_rejects_small_tiles_and_other_forms(env, orc):
     plan.run()
     assert np.array_equal(MC.read(), expected(orc, Cf, Af, Bf, meta))
     plan.close()
+
+
+def test_batch_workload_full_size_against_oracle(env, orc):
+    # The bench's batch at full size and in the launch configuration it times:
+    # 4096 calls C -= A*B mod 65521 with M, N, K uniform in [32, 512], each in
+    # its own 512 x 512 cell of a 32768 x 32768 C, A and B random rectangles of
+    # 16384 x 16384 matrices, T' = 64. C starts random inside every call's part.
+    # The tensor-core limb plan (3 launches) is compared with the oracle call by
+    # call, every entry; the fused limb plan and the decomposed plain plan must
+    # give the same matrix.
+    import torch
+    fm, dev = env
+    p, seed, count, hi, big, lt = P16, 5, 4096, 512, 16384, 6
+    rows, cells = fm_inputs.batch_workload(seed, count, 32, hi, big)
+    nC = cells * hi
+    lgA = (big >> lt).bit_length() - 1
+    lgC = (nC >> lt).bit_length() - 1
+    Af = fm_inputs.uniform_residues(seed, (big, big), p, 1)
+    Bf = fm_inputs.uniform_residues(seed, (big, big), p, 2)
+    MA = MortonMatrix(fm, dev, lgA, lt, fill=Af)
+    MB = MortonMatrix(fm, dev, lgA, lt, fill=Bf)
+    Cf = np.zeros((nC, nC), dtype=np.uint32)
+    for c in range(count):
+        M, N, K, rC, cC = (int(x) for x in rows[c, :5])
+        Cf[rC:rC + M, cC:cC + N] = fm_inputs.uniform_residues(seed, (M, N), p, 100 + c)
+    MC = MortonMatrix(fm, dev, lgC, lt, fill=Cf)
+    calls = []
+    for c in range(count):
+        M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rows[c])
+        call = fm.fm_gemm_call()
+        call.C, call.A, call.B = MC.sub(rC, cC, M, N), MA.sub(rA, cA, M, K), MB.sub(rB, cB, K, N)
+        call.op = fm.FM_OP_SUB
+        calls.append(call)
+    saved = MC.t.clone()
+    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC)
+    assert plan.launches == 3
+    plan.run()
+    got = MC.read()
+    assert fm.fm_get_last_device_status() == 0
+    for c in range(count):
+        M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rows[c])
+        want = orc.gemm_modp(Cf[rC:rC + M, cC:cC + N], Af[rA:rA + M, cA:cA + K], Bf[rB:rB + K, cB:cB + N], p,
+                             fm.FM_OP_SUB)
+        assert np.array_equal(got[rC:rC + M, cC:cC + N], want), c
+        got[rC:rC + M, cC:cC + N] = Cf[rC:rC + M, cC:cC + N]
+    assert np.array_equal(got, Cf)  # nothing outside the calls' parts changed
+    del got
+    limb = MC.t.clone()
+    plan.close()
+    for algo, o in ((fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1)), (fm.FM_ALGO_PLAIN, None)):
+        MC.t.copy_(saved)
+        other = fm.fm_plan_create(calls, p, algo, o)
+        other.run()
+        torch.cuda.synchronize()
+        assert fm.fm_get_last_device_status() == 0
+        assert torch.equal(MC.t, limb), algo
+        other.close()
+    del MA, MB, MC, saved, limb
+    torch.cuda.empty_cache()

@@ -49,22 +49,120 @@ def test_to_morton_permuted(env, orc, rows, cols, lg, lt):
         assert np.array_equal(to_host(M.t), want)
 
 
-@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", [(100, 90, 2, 5, 1, 6), (33, 47, 3, 3, 1, 5),
-                                                        (128, 128, 1, 6, 1, 6)])
+# (rows, cols, source grid and T', destination grid and T'): T' >= 4 on both
+# sides takes the row-staged gather (ragged cols, rows and cols below the
+# grid, different T' on the two sides, several tiles), T' < 4 on either side
+# the entry-by-entry one
+PERMUTE_CASES = [(100, 90, 2, 5, 1, 6), (33, 47, 3, 3, 1, 5), (128, 128, 1, 6, 1, 6),
+                 (37, 53, 2, 4, 3, 2), (255, 250, 1, 7, 3, 5), (64, 61, 0, 6, 4, 2),
+                 (20, 30, 5, 0, 3, 2), (17, 9, 2, 3, 4, 1), (1, 1, 0, 2, 0, 2), (0, 0, 1, 2, 1, 2)]
+
+
+@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", PERMUTE_CASES)
 def test_permute_rows_cols(env, orc, rows, cols, lgs, lts, lgd, ltd):
     fm, dev = env
     ns = (1 << lgs) << lts
     x = fm_inputs.uniform_residues(5, (ns, ns), 2147483647)
     S = MortonMatrix(fm, dev, lgs, lts, fill=x)
-    D = MortonMatrix(fm, dev, lgd, ltd)
-    D.t.fill_(-1)
+    nd = (1 << lgd) << ltd
     rp = fm_inputs.permutation(5, rows, 1)
     cp = fm_inputs.permutation(5, cols, 2)
-    fm.fm_permute_rows_cols(S.m, D.m, rows, cols, to_dev(rp, dev), to_dev(cp, dev))
-    nd = (1 << lgd) << ltd
-    canvas = np.zeros((nd, nd), dtype=np.uint32)
-    canvas[:rows, :cols] = orc.permute(x[:rows, :cols], rp, cp)
-    assert np.array_equal(to_host(D.t), orc.to_morton(canvas, lgd, 1 << ltd))
+    for r, c in ((rp, cp), (rp, None), (None, cp), (None, None)):
+        D = MortonMatrix(fm, dev, lgd, ltd)
+        D.t.fill_(-1)  # everything outside rows x cols must become 0
+        fm.fm_permute_rows_cols(S.m, D.m, rows, cols, None if r is None or rows == 0 else to_dev(r, dev),
+                                None if c is None or cols == 0 else to_dev(c, dev))
+        canvas = np.zeros((nd, nd), dtype=np.uint32)
+        canvas[:rows, :cols] = orc.permute(x[:rows, :cols], r, c)
+        assert np.array_equal(to_host(D.t), orc.to_morton(canvas, lgd, 1 << ltd))
+    assert fm.fm_get_last_device_status() == 0
+
+
+def test_permute_rows_cols_full_size(env, orc):
+    # 8192 x 8192 at T' = 32 into T' = 128 (the row-staged gather with 32 KB
+    # source rows), every entry compared with the oracle's permutation
+    import torch
+    fm, dev = env
+    n = 8192
+    x = fm_inputs.uniform_residues(8, (n, n), 65521)
+    rp = fm_inputs.permutation(8, n, 1)
+    cp = fm_inputs.permutation(8, n, 2)
+    S = MortonMatrix(fm, dev, 8, 5, fill=x)
+    D = MortonMatrix(fm, dev, 6, 7)
+    fm.fm_permute_rows_cols(S.m, D.m, n, n, to_dev(rp, dev), to_dev(cp, dev))
+    got = D.read()
+    assert fm.fm_get_last_device_status() == 0
+    assert np.array_equal(got, orc.permute(x, rp, cp))
+    del S, D
+    torch.cuda.empty_cache()
+
+
+def _bad(perm, where, value):
+    out = perm.copy()
+    out[where] = value
+    return out
+
+
+@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", [(100, 90, 2, 5, 1, 6), (37, 53, 2, 4, 3, 2),
+                                                        (20, 30, 5, 0, 3, 2)])
+def test_permute_out_of_range_entries(env, orc, rows, cols, lgs, lts, lgd, ltd):
+    # a permutation entry outside [0, rows) / [0, cols) (too large, or
+    # negative) is never used as an index: the entries it would fill are 0,
+    # everything else is the permutation, and FM_EINVAL arrives in the status
+    fm, dev = env
+    ns, nd = (1 << lgs) << lts, (1 << lgd) << ltd
+    x = fm_inputs.uniform_residues(6, (ns, ns), 65521)
+    S = MortonMatrix(fm, dev, lgs, lts, fill=x)
+    rp = fm_inputs.permutation(6, rows, 1)
+    cp = fm_inputs.permutation(6, cols, 2)
+    assert fm.fm_get_last_device_status() == 0
+    for r, c, zero_row, zero_col in ((_bad(rp, 3, rows), cp, 3, None), (_bad(rp, 5, -7), cp, 5, None),
+                                     (rp, _bad(cp, 4, cols + 1000), None, 4), (rp, _bad(cp, 2, -1), None, 2),
+                                     (None, _bad(cp, cols - 1, 1 << 30), None, cols - 1)):
+        D = MortonMatrix(fm, dev, lgd, ltd)
+        fm.fm_permute_rows_cols(S.m, D.m, rows, cols, None if r is None else to_dev(r, dev), to_dev(c, dev))
+        got = D.read(rows, cols)
+        assert fm.fm_get_last_device_status() == fm.FM_EINVAL
+        good_r = np.arange(rows) if r is None else np.where((r >= 0) & (r < rows), r, 0)
+        good_c = np.where((c >= 0) & (c < cols), c, 0)
+        want = orc.permute(x[:rows, :cols], good_r, good_c)
+        if zero_row is not None:
+            want[zero_row, :] = 0
+        if zero_col is not None:
+            want[:, zero_col] = 0
+        assert np.array_equal(got, want)
+    assert fm.fm_get_last_device_status() == 0  # reading cleared it
+
+
+@pytest.mark.parametrize("rows,cols,lg,lt,u16", [(37, 53, 2, 4, False), (300, 170, 3, 6, True), (9, 15, 3, 1, False)])
+def test_to_morton_permuted_out_of_range_entries(env, orc, rows, cols, lg, lt, u16):
+    # the same for the row-major -> Morton-hybrid conversion: with a column
+    # permutation (the row-staged kernel; T' >= 4), with only a row permutation
+    # (the tile walk), and at T' = 2 (entry by entry)
+    import torch
+    fm, dev = env
+    x = fm_inputs.uniform_residues(7, (rows, cols), 65521)
+    src = torch.from_numpy(x.astype(np.uint16).view(np.int16)).to(dev) if u16 else to_dev(x, dev)
+    conv = fm.fm_layout_to_morton_permuted_u16 if u16 else fm.fm_layout_to_morton_permuted
+    rp = fm_inputs.permutation(7, rows, 1)
+    cp = fm_inputs.permutation(7, cols, 2)
+    assert fm.fm_get_last_device_status() == 0
+    for r, c, zero_row, zero_col in ((_bad(rp, 1, rows), cp, 1, None), (_bad(rp, 2, -3), None, 2, None),
+                                     (rp, _bad(cp, 6, cols), None, 6), (None, _bad(cp, 0, -100), None, 0)):
+        M = MortonMatrix(fm, dev, lg, lt)
+        M.t.fill_(-1)
+        conv(src, rows, cols, cols, None if r is None else to_dev(r, dev), None if c is None else to_dev(c, dev),
+             M.m)
+        got = M.read(rows, cols)
+        assert fm.fm_get_last_device_status() == fm.FM_EINVAL
+        good_r = np.arange(rows) if r is None else np.where((r >= 0) & (r < rows), r, 0)
+        good_c = np.arange(cols) if c is None else np.where((c >= 0) & (c < cols), c, 0)
+        want = orc.permute(x, good_r, good_c)
+        if zero_row is not None:
+            want[zero_row, :] = 0
+        if zero_col is not None:
+            want[:, zero_col] = 0
+        assert np.array_equal(got, want)
 
 
 def test_layout_errors(env):

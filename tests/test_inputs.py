@@ -40,3 +40,18 @@ def test_permutation_and_shapes():
     assert np.all(r[:, 3] + M <= 64) and np.all(r[:, 4] + N <= 64)
     assert np.all(r[:, 5] + M <= 64) and np.all(r[:, 6] + K <= 64)
     assert np.all(r[:, 7] + K <= 64) and np.all(r[:, 8] + N <= 64)
+
+
+def test_batch_workload_geometry():
+    # every call inside its own cell of C and inside the shared A and B
+    rows, cells = fm_inputs.batch_workload(5, 300, 32, 512, 4096)
+    assert cells == 32 and rows.shape == (300, 9)
+    rows2, _ = fm_inputs.batch_workload(5, 300, 32, 512, 4096)
+    assert np.array_equal(rows, rows2)
+    M, N, K = rows[:, 0], rows[:, 1], rows[:, 2]
+    assert M.min() >= 32 and max(M.max(), N.max(), K.max()) <= 512
+    c = np.arange(300)
+    assert np.array_equal(rows[:, 3], (c // cells) * 512) and np.array_equal(rows[:, 4], (c % cells) * 512)
+    assert np.all(rows[:, 5] + M <= 4096) and np.all(rows[:, 6] + K <= 4096)
+    assert np.all(rows[:, 7] + K <= 4096) and np.all(rows[:, 8] + N <= 4096)
+    assert np.all(rows[:, 5:] >= 0)
