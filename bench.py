@@ -239,124 +239,145 @@ def run_reference(args, world, rank):
 def run_batched(fm, torch, dev, stream, args, count=4096, lo=32, hi=512, seed=5):
     """The batching form: count independent calls C_c -= A_c * B_c mod p with
     M, N, K uniform in [lo, hi], each on its own cell of a large Morton C and
-    on random rectangles of shared Morton A and B (T' = 64). The batch as one
-    tensor-core limb plan (limb planes of every call: 3 launches; and the
-    fused form: 1 launch) and as one decomposed plain plan (1 persistent
-    launch), against one fm_gemm_modp launch per call; every result is checked
-    equal. The roofline is HBM: each call's A, B and C read and C written once."""
+    on random rectangles of shared Morton A and B. The workload is laid out at
+    T' = 32, 64 and 128; at each T' the autotuner (fm_autotune_batch) times the
+    plan forms on the batch and an FM_ALGO_AUTO plan takes the fastest; the
+    fastest T' is the tuned choice. At T' = 64 the fixed forms are timed as
+    well: the tensor-core limb plan (3 launches), the fused limb plan (1
+    launch), the decomposed plain plan (1 persistent launch) and one
+    fm_gemm_modp launch per call; every result is checked equal to the
+    tuned plan's. The roofline is HBM: each call's A, B and C read and C
+    written once."""
     import numpy as np
 
     import fm_inputs
     p = P
-    lt, cell = 6, hi
-    cells = 1
-    while cells * cells < count:
-        cells *= 2
     big = 16384
-    lgA = (big >> lt).bit_length() - 1
-    lgC = ((cells * cell) >> lt).bit_length() - 1
+    rows, cells = fm_inputs.batch_workload(seed, count, lo, hi, big)
+    nC = cells * hi
     A = torch.from_numpy(fm_inputs.uniform_residues(seed, (big, big), p, 1).view(np.int32)).to(dev)
     B = torch.from_numpy(fm_inputs.uniform_residues(seed, (big, big), p, 2).view(np.int32)).to(dev)
-    tA = torch.empty(big * big, dtype=torch.int32, device=dev)
-    tB = torch.empty_like(tA)
-    mA, mB = fm.matrix(tA, lgA, lt), fm.matrix(tB, lgA, lt)
-    fm.fm_layout_to_morton(A, big, big, big, mA)
-    fm.fm_layout_to_morton(B, big, big, big, mB)
-    del A, B
-    nC = cells * cell
-    tC = torch.zeros(nC * nC, dtype=torch.int32, device=dev)
-    mC = fm.matrix(tC, lgC, lt)
-    rows, _ = fm_inputs.batch_workload(seed, count, lo, hi, big)
-    calls = []
     ops = 0.0
     algo_bytes = 0.0  # each call reads A, B and C and writes C once (4-byte residues)
     for c in range(count):
-        M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rows[c])
+        M, N, K = (int(x) for x in rows[c, :3])
         algo_bytes += 4.0 * (M * K + K * N + 2 * M * N)
-        call = fm.fm_gemm_call()
-        call.C = fm.sub(mC, rC, cC, M, N)
-        call.A = fm.sub(mA, rA, cA, M, K)
-        call.B = fm.sub(mB, rB, cB, K, N)
-        call.op = fm.FM_OP_SUB
-        calls.append(call)
         ops += 2.0 * M * N * K
-    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_PLAIN)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 3
-    for _ in range(2):
-        plan.run(stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        plan.run(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1) / reps
-    snap = tC.clone()
-    for call in calls:  # one launch per call, from the same state
-        fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_PLAIN, None, stream)
-    per_call_result = tC.clone()
-    tC.copy_(snap)
-    plan.run(stream)
-    torch.cuda.synchronize()
-    same = bool(torch.equal(tC, per_call_result))
-    del per_call_result
-    # the same batch in the tensor-core limb form: limb planes of every call
-    # (3 launches), and the fused form (1 launch, operands split on the fly)
-    plain_result = tC.clone()
 
-    def limb_plan(fused):
-        lplan = fm.fm_plan_create(calls, p, fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=fused))
-        tC.copy_(snap)
-        lplan.run(stream)
-        torch.cuda.synchronize()
-        same_ = bool(torch.equal(tC, plain_result))
+    def timed(run):
         for _ in range(2):
-            lplan.run(stream)
+            run()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(reps):
-            lplan.run(stream)
+            run()
         e1.record(stream)
         torch.cuda.synchronize()
-        res = (e0.elapsed_time(e1) / reps, lplan.work_items, lplan.launches, same_)
-        lplan.close()
-        return res
+        return e0.elapsed_time(e1) / reps
 
-    limb_ms, limb_tiles, limb_launches, limb_same = limb_plan(0)
-    fused_ms, fused_tiles, fused_launches, fused_same = limb_plan(1)
-    del plain_result
+    def layout(lt):
+        tA = torch.empty(big * big, dtype=torch.int32, device=dev)
+        tB = torch.empty_like(tA)
+        mA = fm.matrix(tA, (big >> lt).bit_length() - 1, lt)
+        mB = fm.matrix(tB, (big >> lt).bit_length() - 1, lt)
+        fm.fm_layout_to_morton(A, big, big, big, mA)
+        fm.fm_layout_to_morton(B, big, big, big, mB)
+        tC = torch.zeros(nC * nC, dtype=torch.int32, device=dev)
+        mC = fm.matrix(tC, (nC >> lt).bit_length() - 1, lt)
+        calls = []
+        for c in range(count):
+            M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rows[c])
+            call = fm.fm_gemm_call()
+            call.C, call.A, call.B = fm.sub(mC, rC, cC, M, N), fm.sub(mA, rA, cA, M, K), fm.sub(mB, rB, cB, K, N)
+            call.op = fm.FM_OP_SUB
+            calls.append(call)
+        return (tA, tB, tC), calls
+
+    def form_name(r):
+        if r.algo == fm.FM_ALGO_PLAIN:
+            return "decomposed plain plan (1 persistent launch)"
+        o = r.opts
+        if o.fused_batch:
+            return "fused limb plan (1 launch)"
+        return (f"limb plan with planes (3 launches), tile width {o.block_n or 'default'}, K chunk "
+                f"{o.k_chunk or 'full'}, {'no ' if o.no_karatsuba else ''}Karatsuba")
+
+    fm.fm_autotune_clear()
+    by_T = {}
+    best = None
+    for lt in (5, 6, 7):
+        bufs, calls = layout(lt)
+        r = fm.fm_autotune_batch(calls, p, 0, stream)
+        plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_AUTO)
+        ms = timed(lambda: plan.run(stream))
+        by_T[f"T'={1 << lt}"] = {"form": form_name(r), "ms": ms, "value": ops / (ms / 1e3) / 1e9,
+                                 "launches": plan.launches, "candidates": r.candidates,
+                                 "tuner_ms": r.ms}
+        if best is None or ms < best[1]:
+            best = (lt, ms, plan.launches, form_name(r))
+        plan.close()
+        del bufs, calls
+        torch.cuda.empty_cache()
+    tuned_lt, tuned_ms, tuned_launches, tuned_form = best
+
+    # the tuned choice again from scratch (its result is the reference below),
+    # then the fixed forms at T' = 64 on the same inputs
+    bufs, calls = layout(tuned_lt)
+    plan = fm.fm_plan_create(calls, p, fm.FM_ALGO_AUTO)
+    plan.run(stream)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        for call in calls:
-            fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_PLAIN, None, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    per_call_ms = e0.elapsed_time(e1) / reps
-    items = plan.work_items
+    tuned_out = torch.empty((nC, nC), dtype=torch.int32, device=dev)
+    fm.fm_layout_from_morton(fm.matrix(bufs[2], (nC >> tuned_lt).bit_length() - 1, tuned_lt), nC, nC, tuned_out,
+                             nC, stream)
     plan.close()
-    del tA, tB, tC, snap
+    del bufs, calls
+    bufs, calls = layout(6)
+    tC = bufs[2]
+    mC = fm.matrix(tC, (nC >> 6).bit_length() - 1, 6)
+    snap = tC.clone()
+    check = torch.empty_like(tuned_out)
+
+    def same_as_tuned():
+        torch.cuda.synchronize()
+        fm.fm_layout_from_morton(mC, nC, nC, check, nC, stream)
+        torch.cuda.synchronize()
+        return bool(torch.equal(check, tuned_out))
+
+    fixed = {}
+    for name, algo, o in (("limb", fm.FM_ALGO_LIMB_TC, None), ("fused", fm.FM_ALGO_LIMB_TC, fm.opts(fused_batch=1)),
+                          ("plain", fm.FM_ALGO_PLAIN, None)):
+        pl = fm.fm_plan_create(calls, p, algo, o)
+        tC.copy_(snap)
+        pl.run(stream)
+        same = same_as_tuned()
+        ms = timed(lambda: pl.run(stream))
+        fixed[name] = {"ms": ms, "value": ops / (ms / 1e3) / 1e9, "launches": pl.launches,
+                       "output_tiles_or_items": pl.work_items, "bit_identical_to_tuned": same}
+        pl.close()
+    tC.copy_(snap)
+    for call in calls:  # one launch per call, from the same state
+        fm.fm_gemm_modp(call.C, call.A, call.B, p, call.op, fm.FM_ALGO_PLAIN, None, stream)
+    per_call_same = same_as_tuned()
+    per_call_ms = timed(lambda: [fm.fm_gemm_modp(c_.C, c_.A, c_.B, p, c_.op, fm.FM_ALGO_PLAIN, None, stream)
+                                 for c_ in calls])
+    del bufs, calls, snap, check, tuned_out, A, B
+    torch.cuda.empty_cache()
     _, _, hbm_peak, peak_src = measured_peaks()
-    return {"workload": f"{count} calls C -= A*B mod {p}, M,N,K ~ U[{lo},{hi}], T'=64, "
-                        f"one tensor-core limb plan (planes of every call in one workspace)",
-            "value": ops / (limb_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": limb_ms, "launches": limb_launches,
-            "output_tiles": limb_tiles, "bit_identical_to_plain_batched": limb_same,
-            "roofline": {"bound": "hbm", "achieved": algo_bytes / (limb_ms / 1e3) / 1e9,
-                         "peak": hbm_peak, "unit": "GB/s", "frac": algo_bytes / (limb_ms / 1e3) / 1e9 / hbm_peak,
+    ach = algo_bytes / (tuned_ms / 1e3) / 1e9
+    return {"workload": f"{count} calls C -= A*B mod {p}, M,N,K ~ U[{lo},{hi}], Morton-hybrid, T' and plan form "
+                        "chosen by the autotuner",
+            "value": ops / (tuned_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": tuned_ms, "launches": tuned_launches,
+            "tuned": {"T": 1 << tuned_lt, "form": tuned_form, "by_T": by_T},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "per_call_frac": algo_bytes / (per_call_ms / 1e3) / 1e9 / hbm_peak,
                          "work": "algorithmic bytes: A, B, C read and C written once per call, 4 B each "
                                  f"({algo_bytes / 1e9:.3f} GB)", "peak_source": f"HBM copy, {peak_src}"},
-            "fused": {"workload": "the same calls as one fused launch (operands split into limbs on the fly)",
-                      "value": ops / (fused_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": fused_ms,
-                      "launches": fused_launches, "output_tiles": fused_tiles,
-                      "bit_identical_to_plain_batched": fused_same},
             "per_call_ms": per_call_ms, "per_call_value": ops / (per_call_ms / 1e3) / 1e9,
-            "speedup_vs_per_call": per_call_ms / limb_ms, "per_call_launches": count,
-            "plain": {"workload": "the same calls as one decomposed plan (plain form, one persistent launch)",
-                      "value": ops / (batched_ms / 1e3) / 1e9, "unit": "Gop/s", "ms": batched_ms,
-                      "work_items": items, "launches": 1, "bit_identical_to_per_call": same,
-                      "speedup_vs_per_call": per_call_ms / batched_ms}}
+            "speedup_vs_per_call": per_call_ms / tuned_ms, "per_call_launches": count,
+            "per_call_bit_identical_to_tuned": per_call_same,
+            "fixed_forms_at_T64": fixed}
 
 
 def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
@@ -414,7 +435,7 @@ def run_tu(fm, torch, dev, stream, m=16384, n=12288, k=10000, seed=5):
             "ops": "2*(m n r - (m+n) r^2/2 + r^3/3)"}
 
 
-def run_configs(fm, torch, dev, stream, seed=21):
+def run_configs(fm, torch, dev, stream, peaks, seed=21):
     """The other workloads of the hot path, each timed with CUDA events after
     warm-up, and each result checked bit-identical against a second GEMM form
     on the same inputs:
@@ -516,7 +537,8 @@ def run_configs(fm, torch, dev, stream, seed=21):
     out["schur"] = {"workload": "C(3000x2200) -= A(3000x1700) * B(1700x2200) mod 65521, Morton-hybrid T'=64, "
                                 "row and column permutations of A in the conversion, plain form",
                     "layout_ms": lay_ms, "layout_gbs": lay_bytes / (lay_ms / 1e3) / 1e9, "gemm_ms": gemm_ms,
-                    "value": ops / (gemm_ms / 1e3) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same}
+                    "value": ops / (gemm_ms / 1e3) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same,
+                    "gemm_frac_of_imad_wide": ops / 2 / (gemm_ms / 1e3) / 1e12 / peaks["imad_wide"]}
     del tA, tB, tC, dA, dB, dC, snap
 
     # p31: 4096^3 at p = 2^31 - 1, limb form (T' = 128); the plain form, which
@@ -934,6 +956,11 @@ def run_fm(args, world, rank, local):
     else:
         e2e_line = e2e_u32
 
+    # ---- measured arithmetic rates of the non-tensor pipes (T multiply-adds/s) ----
+    peaks = {name: fm.fm_measure_peak(kind, 1 << 16, s) / 1e12 for name, kind in (
+        ("imad_wide", fm.FM_PEAK_IMAD_WIDE), ("imad32", fm.FM_PEAK_IMAD32), ("dfma", fm.FM_PEAK_DFMA),
+        ("ffma", fm.FM_PEAK_FFMA), ("mma_s8", fm.FM_PEAK_MMA_S8))}
+
     out = {}
     # ---- comparison forms on the same inputs (same step, other GEMM) ----
     if not args.no_compare:
@@ -942,9 +969,13 @@ def run_fm(args, world, rank, local):
         tC6, mC6 = morton(lt_plain)
         s6 = [fm.sub(m_, 0, 0, n, n) for m_ in (mC6, mA6, mB6)]
 
-        def plain_step(algo):
+        def plain_step(algo, ev=None):
             layout_in(dA, dB, dC, mA6, mB6, mC6)
+            if ev:
+                ev[0].record(stream)
             fm.fm_gemm_modp(s6[0], s6[1], s6[2], p, fm.FM_OP_SUB, algo, None, s)
+            if ev:
+                ev[1].record(stream)
             fm.fm_layout_from_morton(mC6, n, n, dOut, n, s)
 
         e0 = torch.cuda.Event(enable_timing=True)
@@ -952,18 +983,26 @@ def run_fm(args, world, rank, local):
         limb_step()
         torch.cuda.synchronize()
         ref = dOut.clone()
-        for name, algo, steps in (("plain", fm.FM_ALGO_PLAIN, 3), ("dfma", fm.FM_ALGO_DFMA, 1)):
+        for name, algo, steps, kind in (("plain", fm.FM_ALGO_PLAIN, 3, "imad_wide"),
+                                        ("dfma", fm.FM_ALGO_DFMA, 1, "dfma")):
             plain_step(algo)
             torch.cuda.synchronize()
+            gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
             e0.record(stream)
-            for _ in range(steps):
-                plain_step(algo)
+            for k in range(steps):
+                plain_step(algo, gev[k])
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            gemm_ms = sum(g[0].elapsed_time(g[1]) for g in gev) / steps
             same = bool(torch.equal(dOut, ref))
+            macs = float(n) ** 3 / (gemm_ms / 1e3) / 1e12
             out[name] = {"value": ops * steps / (ms / 1e3) / 1e9, "unit": "Gop/s",
-                         "ms_per_step": ms / steps, "bit_identical_to_limb": same}
+                         "ms_per_step": ms / steps, "bit_identical_to_limb": same, "gemm_ms": gemm_ms,
+                         "roofline": {"bound": "alu", "achieved": macs, "peak": peaks[kind],
+                                      "unit": "T multiply-adds/s", "frac": macs / peaks[kind],
+                                      "work": "one multiply-add per (i, j, l) of the product",
+                                      "peak_source": f"measured {kind} rate (fm_measure_peak)"}}
         del tA6, tB6, tC6
 
     # ---- batching form: 4096 independent GEMMs, M, N, K uniform in [32, 512] ----
@@ -975,7 +1014,7 @@ def run_fm(args, world, rank, local):
     if not args.no_gf2:
         out["gf2"] = run_gf2(fm, torch, dev, stream)
     if not args.no_configs:
-        out["configs"] = run_configs(fm, torch, dev, stream)
+        out["configs"] = run_configs(fm, torch, dev, stream, peaks)
         out["curves"] = run_curves(fm, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (limb GEMM, one launch per step) ----
@@ -1032,6 +1071,13 @@ def run_fm(args, world, rank, local):
         line["plain"] = out["plain"]
         line["dfma"] = out["dfma"]
         line["limb_over_plain"] = value / out["plain"]["value"]
+    # The int8 question: mma.sync s8 carries 8-bit limbs exactly with int32
+    # accumulation but needs 4 limb products per modular multiply-add (the
+    # Karatsuba digit sums do not fit in 8 bits); the f16 carrier on tcgen05
+    # runs at the bf16 burst rate with 3 (Karatsuba).
+    line["peaks"] = dict(peaks, unit="T multiply-adds/s",
+                         modular_ceiling_gops={"mma_s8_4_products": 2e3 * peaks["mma_s8"] / 4,
+                                               "tcgen05_f16_3_products": 1e3 * burst / 3})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, secs = cpu_oracle_rate(n, p, target_s=12.0)
         line["cpu_baseline"] = {"value": v, "unit": "Gop/s", "cores": cores, "kind": "oracle",

@@ -366,6 +366,21 @@ int fm_autotune_save(const char* path);
 int fm_autotune_load(const char* path);
 int fm_autotune_clear(void);
 
+/* Times the candidate forms of the batch calls[0..n-1] (host array, as for
+ * fm_plan_create) on the current device and remembers the fastest for its
+ * batch class (number of calls, mean M, N and K rounded up to powers of two,
+ * modulus class, T'); fm_plan_create with FM_ALGO_AUTO and opts == NULL then
+ * builds that form for batches of the class. Candidates: the decomposed plain
+ * plan (all matrices with T' = 32 or 64), the limb plan with planes at output
+ * tile width 128 and 256 (256 for odd p < 2^16 only), full and half K chunk,
+ * with and without Karatsuba, and the fused limb plan. Each runs once untimed
+ * and three times timed (CUDA events) on the batch itself, with every C matrix
+ * replaced by a scratch copy (allocated and freed here), so the caller's
+ * matrices do not change. The batch's layout T' is the caller's: to tune T',
+ * lay the batch out at each T' and tune each. Synchronises stream. */
+int fm_autotune_batch(const fm_gemm_call* calls, int64_t n, uint32_t p, int32_t flags, fm_stream stream,
+                      fm_tune_result* out);
+
 /* ---- decomposition (host only; Sec. 2.2 Steps 1-4) ---------------------- */
 
 /* Writes the base-case products of C <- C op A*B as local index ranges
@@ -453,6 +468,21 @@ int fm_gf2_plan_create(fm_plan** plan, const fm_gf2_call* calls, int64_t n, cons
  * fm_pluq call appends one line with its shapes and work (products, tiles,
  * plane bytes). The public entry points are also NVTX ranges. */
 int fm_debug_expire_wait(int32_t which, fm_stream stream);
+
+/* ---- measured pipe rates (the paper has no counterpart) -------------------
+ * The roofline of the non-tensor forms: the plain form spends one 32 x 32 ->
+ * 64-bit integer multiply-add (mad.wide.u32) per (i, j, l), the DFMA form one
+ * FP64 fused multiply-add; the legacy warp-level int8 MMA (mma.sync m16n8k32,
+ * s8 x s8 -> s32) is the true-INT8 alternative to the f16 carrier on tcgen05.
+ * fm_measure_peak runs a probe kernel of that one instruction (4 CTAs of 256
+ * threads per SM, independent chains, no memory traffic in the loop; iters
+ * loop iterations, 8 multiply-adds per thread each, or four m16n8k32 MMAs per
+ * warp) after one shorter warm-up launch, times it with CUDA events on stream
+ * and writes multiply-adds per second to *ops_per_s (host; for the MMA, its
+ * m * n * k products per second). Synchronous. FM_EINVAL for an unknown kind
+ * or iters <= 0. */
+enum { FM_PEAK_IMAD_WIDE = 0, FM_PEAK_IMAD32 = 1, FM_PEAK_DFMA = 2, FM_PEAK_FFMA = 3, FM_PEAK_MMA_S8 = 4 };
+int fm_measure_peak(int32_t kind, int64_t iters, fm_stream stream, double* ops_per_s);
 
 /* ---- status ------------------------------------------------------------- */
 

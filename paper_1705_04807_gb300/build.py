@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfm.so")
 
 SOURCES = ["api.cu", "layout.cu", "gemm_plain.cu", "limb_split.cu", "limb_gemm.cu", "noalloc.cu",
-           "autotune.cu", "pluq.cu", "gf2.cu", "debug.cu", "limb_fused.cu", "schedule.cpp"]
+           "autotune.cu", "pluq.cu", "gf2.cu", "debug.cu", "limb_fused.cu", "peaks.cu", "schedule.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -349,10 +349,16 @@ struct fm_plan {
 extern "C" int fm_plan_create(fm_plan** out, const fm_gemm_call* calls, int64_t n, uint32_t p,
                               int32_t algo, const fm_opts* opts)
 {
-    (void)opts;
     if (!out || (n > 0 && !calls) || n < 0) return FM_EINVAL;
     *out = nullptr;
     if (p < 2 || p >= (1u << 31)) return FM_EMODULUS;
+    if (algo == FM_ALGO_AUTO && opts == nullptr && n > 0) {
+        // the form fm_autotune_batch measured fastest for batches of this class
+        fm_tune_result r;
+        if (fm_tuned_batch_choice(calls, n, p, &r) &&
+            fm_plan_create(out, calls, n, p, r.algo, r.algo == FM_ALGO_LIMB_TC ? &r.opts : nullptr) == FM_OK)
+            return FM_OK;
+    }
     if (algo == FM_ALGO_LIMB_TC) {
         for (int64_t c = 0; c < n; ++c) {
             const fm_gemm_call& g = calls[c];

@@ -106,5 +106,6 @@ int fm_limb_prepare_device();
 int* fm_noalloc_status_word();
 int fm_noalloc_take_status(cudaStream_t s, int* out);
 
-// Remembered autotune choice for a problem class (autotune.cu).
+// Remembered autotune choice for a problem class, and for a batch class (autotune.cu).
 bool fm_tuned_choice(int64_t M, int64_t N, int64_t K, uint32_t p, fm_tune_result* out);
+bool fm_tuned_batch_choice(const fm_gemm_call* calls, int64_t n, uint32_t p, fm_tune_result* out);

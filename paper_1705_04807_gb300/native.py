@@ -21,6 +21,7 @@ FM_ETOOBIG = -8
 FM_OP_SET, FM_OP_ADD, FM_OP_SUB = 0, 1, 2
 FM_ALGO_AUTO, FM_ALGO_PLAIN, FM_ALGO_LIMB_TC, FM_ALGO_LIMB_MMA_S8, FM_ALGO_DFMA = 0, 1, 2, 3, 4
 FM_LIMB_A, FM_LIMB_B = 0, 1
+FM_PEAK_IMAD_WIDE, FM_PEAK_IMAD32, FM_PEAK_DFMA, FM_PEAK_FFMA, FM_PEAK_MMA_S8 = 0, 1, 2, 3, 4
 
 # Every symbol include/fm.h declares.
 EXPORTS = (
@@ -33,7 +34,7 @@ EXPORTS = (
     "fm_limb_planes_size", "fm_limb_split", "fm_limb_gemm", "fm_gemm_modp_noalloc",
     "fm_autotune", "fm_autotune_lookup", "fm_autotune_save", "fm_autotune_load", "fm_autotune_clear",
     "fm_pluq", "fm_gf2_pack", "fm_gf2_unpack", "fm_gf2_gemm", "fm_gf2_workspace_size",
-    "fm_gf2_plan_create", "fm_debug_expire_wait",
+    "fm_gf2_plan_create", "fm_debug_expire_wait", "fm_measure_peak", "fm_autotune_batch",
 )
 
 
@@ -137,6 +138,8 @@ def lib():
         "fm_autotune_save": ([ctypes.c_char_p], ctypes.c_int),
         "fm_autotune_load": ([ctypes.c_char_p], ctypes.c_int),
         "fm_autotune_clear": ([], ctypes.c_int),
+        "fm_autotune_batch": ([ctypes.POINTER(fm_gemm_call), I64, U32, I32, P, ctypes.POINTER(fm_tune_result)],
+                              ctypes.c_int),
         "fm_pluq": ([fm_matrix, I64, I64, U32, P, P, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
         "fm_gf2_pack": ([P, I64, I64, I64, fm_gf2_matrix, P], ctypes.c_int),
         "fm_gf2_unpack": ([fm_gf2_matrix, I64, I64, P, I64, P], ctypes.c_int),
@@ -146,6 +149,7 @@ def lib():
         "fm_gf2_plan_create": ([ctypes.POINTER(P), ctypes.POINTER(fm_gf2_call), I64,
                                 ctypes.POINTER(fm_opts)], ctypes.c_int),
         "fm_debug_expire_wait": ([I32, P], ctypes.c_int),
+        "fm_measure_peak": ([I32, I64, P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -403,6 +407,16 @@ def fm_autotune(M: int, N: int, K: int, p: int, flags: int = 0, stream=None) -> 
     return r
 
 
+def fm_autotune_batch(calls, p: int, flags: int = 0, stream=None) -> fm_tune_result:
+    """Times the candidate plan forms on the batch (scratch copies of C) and
+    remembers the fastest for its batch class."""
+    r = fm_tune_result()
+    arr = (fm_gemm_call * len(calls))(*calls)
+    _check(lib().fm_autotune_batch(arr, len(calls), int(p), int(flags), _stream(stream), ctypes.byref(r)),
+           "fm_autotune_batch")
+    return r
+
+
 def fm_autotune_lookup(M: int, N: int, K: int, p: int):
     r = fm_tune_result()
     hit = int(lib().fm_autotune_lookup(int(M), int(N), int(K), int(p), ctypes.byref(r)))
@@ -458,6 +472,13 @@ def fm_gf2_workspace_size(M: int, N: int, K: int) -> int:
 
 def fm_debug_expire_wait(which: int, stream=None):
     return _check(lib().fm_debug_expire_wait(int(which), _stream(stream)), "fm_debug_expire_wait")
+
+
+def fm_measure_peak(kind: int, iters: int = 1 << 14, stream=None) -> float:
+    """Multiply-adds per second of one arithmetic pipe (FM_PEAK_*), measured."""
+    out = ctypes.c_double(0.0)
+    _check(lib().fm_measure_peak(int(kind), int(iters), _stream(stream), ctypes.byref(out)), "fm_measure_peak")
+    return out.value
 
 
 def fm_get_last_device_status(stream=None) -> int:

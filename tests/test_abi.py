@@ -115,6 +115,30 @@ def test_autotune_table_roundtrip(fm, tmp_path):
     fm.fm_autotune_clear()
 
 
+def test_autotune_table_batch_lines_roundtrip(fm, tmp_path):
+    # host only: batch classes (calls, mean M, N, K, modulus class, T') save and
+    # load with the single-call classes; a malformed batch line is refused
+    fm.fm_autotune_clear()
+    table = tmp_path / "tune.txt"
+    table.write_text("# libfm autotune table v2\n"
+                     "13 13 13 1 2 7 256 960 0 2.500000 439804.651 1\n"
+                     "batch 12 9 9 9 1 6 2 128 960 0 0 4.780000 35100.000\n"
+                     "batch 6 5 5 5 2 5 1 0 0 0 0 0.300000 1000.000\n")
+    assert fm.fm_autotune_load(str(table)) == 3
+    out = tmp_path / "tune2.txt"
+    fm.fm_autotune_save(str(out))
+    lines = [x for x in out.read_text().splitlines() if x.startswith("batch ")]
+    assert lines == ["batch 6 5 5 5 2 5 1 0 0 0 0 0.300000 1000.000",
+                     "batch 12 9 9 9 1 6 2 128 960 0 0 4.780000 35100.000"]
+    fm.fm_autotune_clear()
+    assert fm.fm_autotune_load(str(out)) == 3
+    bad = tmp_path / "bad.txt"
+    bad.write_text("batch 12 9 9 9 1 6 3 128 960 0 0 4.78 35100\n")  # algo 3 is not a batch form
+    with pytest.raises(fm.FmError):
+        fm.fm_autotune_load(str(bad))
+    fm.fm_autotune_clear()
+
+
 def test_layout_calls_reject_bad_arguments_on_the_host(fm):
     # argument checks of the 32-bit and 16-bit layout calls run on the host,
     # before any device work (the matrices here are host-only fake bases)

@@ -54,7 +54,7 @@ def test_to_morton_permuted(env, orc, rows, cols, lg, lt):
 # grid, different T' on the two sides, several tiles), T' < 4 on either side
 # the entry-by-entry one
 PERMUTE_CASES = [(100, 90, 2, 5, 1, 6), (33, 47, 3, 3, 1, 5), (128, 128, 1, 6, 1, 6),
-                 (37, 53, 2, 4, 3, 2), (255, 250, 1, 7, 3, 5), (64, 61, 0, 6, 4, 2),
+                 (37, 53, 2, 4, 4, 2), (255, 250, 1, 7, 3, 5), (64, 61, 0, 6, 4, 2),
                  (20, 30, 5, 0, 3, 2), (17, 9, 2, 3, 4, 1), (1, 1, 0, 2, 0, 2), (0, 0, 1, 2, 1, 2)]
 
 
@@ -103,7 +103,7 @@ def _bad(perm, where, value):
     return out
 
 
-@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", [(100, 90, 2, 5, 1, 6), (37, 53, 2, 4, 3, 2),
+@pytest.mark.parametrize("rows,cols,lgs,lts,lgd,ltd", [(100, 90, 2, 5, 1, 6), (37, 53, 2, 4, 4, 2),
                                                         (20, 30, 5, 0, 3, 2)])
 def test_permute_out_of_range_entries(env, orc, rows, cols, lgs, lts, lgd, ltd):
     # a permutation entry outside [0, rows) / [0, cols) (too large, or
