@@ -65,6 +65,32 @@ def test_default_calls_special_cases():
     assert recursion.default_calls(T, 33, 1, 1) == 2
 
 
+def _leaves_per_dim(x):
+    # Closed form of the halving recursion along one dimension: for
+    # 2^k T' < x <= 2^(k+1) T', the pieces at depth k have sizes floor and ceil
+    # of x / 2^k (at most 2T'), and each piece longer than T' splits once more;
+    # x - 2^k T' of them are longer when that is below 2^k, all 2^k otherwise.
+    if x <= T:
+        return 1
+    k = 0
+    while (T << (k + 1)) < x:
+        k += 1
+    return (1 << k) + min(1 << k, x - (T << k))
+
+
+def test_default_calls_closed_form():
+    # the default recursion halves every dimension above T' independently, so
+    # its base-case count is the product of per-dimension leaf counts, each
+    # given by the closed form above (checked on every extent up to 2048 and
+    # on mixed triples)
+    from oracle import recursion
+    for x in range(1, 2049):
+        assert recursion.default_calls(T, x, 1, 1) == _leaves_per_dim(x), x
+    for M, N_, K in fm_inputs.integers(5, 3 * 100, 1, 1024, 3).reshape(100, 3):
+        M, N_, K = int(M), int(N_), int(K)
+        assert recursion.default_calls(T, M, N_, K) == _leaves_per_dim(M) * _leaves_per_dim(N_) * _leaves_per_dim(K)
+
+
 def test_table1_call_increase_distribution(fm):
     from oracle import recursion
     dc = functools.lru_cache(maxsize=None)(lambda M, N_, K: recursion.default_calls(T, M, N_, K))
