@@ -62,6 +62,45 @@ __device__ __forceinline__ uint64_t curve_encode(uint64_t i, uint64_t j, int lg,
     return CURVE == kHilbert ? fm_hilbert_encode(i, j, lg, lt) : fm_encode(i, j, lt);
 }
 
+// Offsets of the entries (i, j0), (i, j0 + kStride), (i, j0 + 2 kStride), ...
+// of one row of a curve-layout matrix (T' = 2^lt <= 1024 divides kStride, so
+// the offset inside a tile row is the same for all of them). On the Z curve the
+// tile index advances by dilated-integer addition: the column part of Z(I, J)
+// is spread(J) on the even bits, and spread(J + d) = ((spread(J) | odd) +
+// spread(d)) & even -- three operations per step instead of a full bit
+// interleave. The Hilbert curve recomputes the tile's position.
+constexpr uint32_t kStride = 4 * kThreads;
+constexpr uint64_t kEvenBits = 0x5555555555555555ull;
+
+template <int CURVE>
+struct RowWalk {
+    uint64_t rowz, sj, step, off;
+    uint64_t I, J, dJ;
+    int lg, lt;
+    __device__ __forceinline__ RowWalk(uint64_t i, uint64_t j0, int lg_, int lt_) : lg(lg_), lt(lt_)
+    {
+        const uint64_t t1 = (1ull << lt) - 1;
+        off = ((i & t1) << lt) | (j0 & t1);
+        I = i >> lt;
+        J = j0 >> lt;
+        dJ = (uint64_t)kStride >> lt;
+        rowz = fm_spread_bits(I) << 1;
+        sj = fm_spread_bits(J);
+        step = fm_spread_bits(dJ);
+    }
+    __device__ __forceinline__ uint64_t at() const
+    {
+        return CURVE == kHilbert ? (fm_hilbert_tile(I, J, lg) << (2 * lt)) | off : ((rowz | sj) << (2 * lt)) | off;
+    }
+    __device__ __forceinline__ void next()
+    {
+        if (CURVE == kHilbert)
+            J += dJ;
+        else
+            sj = ((sj | ~kEvenBits) + step) & kEvenBits;
+    }
+};
+
 // dst(i, j) = src[rp(i) * ld + cp(j)] (0 outside rows x cols), dst Morton.
 // A permutation entry outside [0, rows) / [0, cols) is not dereferenced: the
 // entries it would fill become 0 and FM_EINVAL is raised in *status.
@@ -156,56 +195,121 @@ __global__ void __launch_bounds__(kThreads) to_morton_kernel(const T* __restrict
     if (kPerm && __syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
-// Column-permuted conversion: dst(i, j) = src[rp(i) * ld + cp(j)]. Each CTA
-// stages a whole source row in shared memory with coalesced 16-byte loads,
-// gathers the permuted columns from shared memory and writes the destination
-// row as contiguous runs of T' entries (one per Morton tile it crosses), so
-// HBM sees one read and one write per element. Out-of-range permutation
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Permuted conversion: dst(i, j) = src[rp(i) * ld + cp(j)] (either permutation
+// may be the identity, NULL). Each CTA
+// walks destination rows i = blockIdx.x, + gridDim.x, ...: it stages the
+// source row rp(i) in shared memory (16-byte asynchronous copies of whole
+// vectors, entries past the last whole vector one by one) in its own entry
+// type, gathers the permuted columns from shared memory and writes the
+// destination row as contiguous runs of T' entries (one per Morton tile it
+// crosses), so HBM sees one read and one write per element. With NBUF = 2
+// (rows of 16-byte aligned vectors only) the copies of the CTA's next row are
+// in flight while it gathers the current one. Out-of-range permutation
 // entries are not dereferenced (0 and FM_EINVAL, as above).
-template <typename T>
+template <typename T, int NBUF>
 __global__ void __launch_bounds__(kThreads)
     to_morton_rowgather_kernel(const T* __restrict__ src, int64_t rows, int64_t cols,
                                int64_t ld, const int32_t* __restrict__ rp,
                                const int32_t* __restrict__ cp, uint32_t* __restrict__ dst, int lg,
                                int lt, int* status)
 {
-    extern __shared__ __align__(16) uint32_t srow[];
+    extern __shared__ __align__(16) uint8_t sraw[];
+    constexpr int kVec = 16 / sizeof(T);  // entries per 16-byte vector
     const int64_t n = (int64_t)1 << (lg + lt);
-    const bool vec = ((ld & 3) == 0) && (((uintptr_t)src & kVec4Align<T>) == 0);
+    const bool vec = ((ld % kVec) == 0) && (((uintptr_t)src & 15) == 0);
+    const int64_t cv = vec ? cols / kVec : 0;             // whole vectors of a row
+    const int64_t stride = (cols + kVec - 1) / kVec * kVec;  // entries per row buffer
+    T* sbuf = reinterpret_cast<T*>(sraw);
     bool bad = false;
-    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-        int64_t si = i < rows ? (rp ? (int64_t)__ldg(rp + i) : i) : -1;
-        if (i < rows && (si < 0 || si >= rows)) {
+
+    auto source_row = [&](int64_t i) -> int64_t {
+        if (i >= rows) return -1;
+        const int64_t si = rp ? (int64_t)__ldg(rp + i) : i;
+        if (si < 0 || si >= rows) {
             bad = true;
-            si = -1;
+            return -1;
         }
-        if (si >= 0) {
-            const T* sr = src + si * ld;
-            const int64_t c4 = vec ? cols / 4 : 0;
-            for (int64_t q = threadIdx.x; q < c4; q += kThreads)
-                *reinterpret_cast<uint4*>(srow + 4 * q) = ld4(sr + 4 * q);
-            for (int64_t j = 4 * c4 + threadIdx.x; j < cols; j += kThreads) srow[j] = (uint32_t)__ldg(sr + j);
-        }
-        __syncthreads();
-        for (int64_t j = 4 * (int64_t)threadIdx.x; j < n; j += 4 * kThreads) {
+        return si;
+    };
+    auto fetch = [&](int64_t si, T* row) {
+        if (si < 0) return;
+        const T* sr = src + si * ld;
+        for (int64_t q = threadIdx.x; q < cv; q += kThreads) cp_async16(row + kVec * q, sr + kVec * q);
+        for (int64_t j = kVec * cv + threadIdx.x; j < cols; j += kThreads) row[j] = __ldg(sr + j);
+    };
+    const bool cp_vec = cp != nullptr && (((uintptr_t)cp & 15) == 0);
+    const int ncols = (int)cols;
+    auto gather = [&](int64_t i, int64_t si, const T* row) {
+        RowWalk<kMorton> w_(i, 4 * threadIdx.x, lg, lt);
+        for (int j = 4 * (int)threadIdx.x; j < (int)n; j += (int)kStride, w_.next()) {
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (si >= 0) {
+            if (si >= 0 && j < ncols) {
+                int32_t sj[4];
+                if (cp_vec && j + 3 < ncols) {
+                    const int4 v = __ldg(reinterpret_cast<const int4*>(cp + j));
+                    sj[0] = v.x;
+                    sj[1] = v.y;
+                    sj[2] = v.z;
+                    sj[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) sj[q] = j + q < ncols ? (cp ? __ldg(cp + j + q) : j + q) : -1;
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (j + q < cols) {
-                        const int64_t sj = __ldg(cp + j + q);
-                        if (sj >= 0 && sj < cols)
-                            w[q] = srow[sj];
+                    if (j + q < ncols) {
+                        if ((unsigned)sj[q] < (unsigned)ncols)
+                            w[q] = (uint32_t)row[sj[q]];
                         else
                             bad = true;
                     }
                 }
             }
-            *reinterpret_cast<uint4*>(dst + fm_encode((uint64_t)i, (uint64_t)j, lt)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(dst + w_.at()) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    };
+
+    int64_t i = blockIdx.x;
+    int64_t si = i < n ? source_row(i) : -1;
+    if (NBUF == 2) {
+        fetch(si, sbuf);
+        cp_async_commit();
+    }
+    for (int k = 0; i < n; ++k, i += gridDim.x) {
+        T* cur = sbuf + (NBUF == 2 ? (int64_t)(k & 1) * stride : 0);
+        int64_t si_next = -1;
+        if (NBUF == 2) {
+            const int64_t inext = i + gridDim.x;
+            si_next = inext < n ? source_row(inext) : -1;
+            fetch(si_next, sbuf + (int64_t)((k + 1) & 1) * stride);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            fetch(si, cur);
+            cp_async_commit();
+            cp_async_wait<0>();
         }
         __syncthreads();
+        gather(i, si, cur);
+        __syncthreads();
+        if (NBUF == 2) si = si_next;
+        else if (i + gridDim.x < n) si = source_row(i + gridDim.x);
     }
+    cp_async_wait<0>();
     if (__syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
@@ -294,53 +398,53 @@ __global__ void __launch_bounds__(kThreads) permute_kernel(const uint32_t* __res
 }
 
 // The same permutation, row-staged, for layouts with T' >= 4 on both sides:
-// one CTA per destination row at a time. The source row rp[i] is read from
-// the tiles it crosses as runs of T'_src contiguous entries (16-byte vectors,
-// one curve index conversion per vector) into shared memory; the destination
-// row is written as runs of T'_dst contiguous entries (16-byte vectors), each
-// entry gathered from shared memory through cp. HBM sees each entry read once
-// and written once in whole 16-byte vectors, against one scattered 4-byte read
-// per entry in permute_kernel. The last vector of a source row may read past
-// cols, but not past the tile (T'_src is a multiple of 4), and those entries are
-// never gathered. Out-of-range permutation entries are not dereferenced (0 and
+// each CTA walks destination rows i = blockIdx.x, + gridDim.x, ... The source
+// row rp[i] is copied from the tiles it crosses, runs of T'_src contiguous
+// entries, into shared memory by 16-byte asynchronous copies (one curve index
+// conversion per vector); the destination row is written as runs of T'_dst
+// contiguous entries (16-byte vectors), each entry gathered from shared memory
+// through cp. With NBUF = 2 the copies of the CTA's next row are in flight
+// while it gathers the current one. HBM sees each entry read once and written
+// once in whole 16-byte vectors, against one scattered 4-byte read per entry
+// in permute_kernel. The last vector of a source row may read past cols, but
+// not past the tile (T'_src is a multiple of 4), and those entries are never
+// gathered. Out-of-range permutation entries are not dereferenced (0 and
 // FM_EINVAL).
-template <int CURVE = kMorton>
+template <int CURVE, int NBUF>
 __global__ void __launch_bounds__(kThreads)
     permute_staged_kernel(const uint32_t* __restrict__ src, int lgs, int lts, uint32_t* __restrict__ dst,
                           int lgd, int ltd, int64_t rows, int64_t cols, const int32_t* __restrict__ rp,
                           const int32_t* __restrict__ cp, int* status)
 {
-    extern __shared__ __align__(16) uint32_t srow[];
+    extern __shared__ __align__(16) uint32_t sbuf[];
     const int64_t nd = (int64_t)1 << (lgd + ltd);
-    const int64_t Ts = (int64_t)1 << lts, Td = (int64_t)1 << ltd;
     const int64_t c4 = (cols + 3) >> 2;
     const bool cp_vec = cp != nullptr && (((uintptr_t)cp & 15) == 0);
     bool bad = false;
-    for (int64_t i = blockIdx.x; i < nd; i += gridDim.x) {
-        int64_t si = i < rows ? (rp ? (int64_t)__ldg(rp + i) : i) : -1;
-        if (i < rows && (si < 0 || si >= rows)) {
+
+    // source row of destination row i, or -1 (a row past rows, or a bad entry)
+    auto source_row = [&](int64_t i) -> int64_t {
+        if (i >= rows) return -1;
+        const int64_t si = rp ? (int64_t)__ldg(rp + i) : i;
+        if (si < 0 || si >= rows) {
             bad = true;
-            si = -1;
+            return -1;
         }
-        if (si >= 0) {
-            const uint64_t I = (uint64_t)si >> lts;
-            const uint64_t off = (uint64_t)(si & (Ts - 1)) << lts;
-#pragma unroll 4
-            for (int64_t q = threadIdx.x; q < c4; q += kThreads) {
-                const int64_t j = 4 * q;
-                const uint64_t a = curve_tile_base<CURVE>(I, (uint64_t)j >> lts, lgs, lts) + off +
-                                   (uint64_t)(j & (Ts - 1));
-                *reinterpret_cast<uint4*>(srow + j) = __ldg(reinterpret_cast<const uint4*>(src + a));
-            }
-        }
-        __syncthreads();
-        const uint64_t Id = (uint64_t)i >> ltd;
-        const uint64_t doff = (uint64_t)(i & (Td - 1)) << ltd;
-        for (int64_t j = 4 * (int64_t)threadIdx.x; j < nd; j += 4 * kThreads) {
+        return si;
+    };
+    const int ncols = (int)cols, c4i = (int)c4;
+    auto fetch = [&](int64_t si, uint32_t* row) {
+        if (si < 0) return;
+        RowWalk<CURVE> w_(si, 4 * threadIdx.x, lgs, lts);
+        for (int q = threadIdx.x; q < c4i; q += kThreads, w_.next()) cp_async16(row + 4 * q, src + w_.at());
+    };
+    auto gather = [&](int64_t i, int64_t si, const uint32_t* row) {
+        RowWalk<CURVE> w_(i, 4 * threadIdx.x, lgd, ltd);
+        for (int j = 4 * (int)threadIdx.x; j < (int)nd; j += (int)kStride, w_.next()) {
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (si >= 0 && j < cols) {
+            if (si >= 0 && j < ncols) {
                 int32_t sj[4];
-                if (cp_vec && j + 3 < cols) {
+                if (cp_vec && j + 3 < ncols) {
                     const int4 v = __ldg(reinterpret_cast<const int4*>(cp + j));
                     sj[0] = v.x;
                     sj[1] = v.y;
@@ -349,24 +453,49 @@ __global__ void __launch_bounds__(kThreads)
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        sj[q] = j + q < cols ? (cp ? __ldg(cp + j + q) : (int32_t)(j + q)) : -1;
+                        sj[q] = j + q < ncols ? (cp ? __ldg(cp + j + q) : j + q) : -1;
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (j + q < cols) {
-                        if (sj[q] >= 0 && sj[q] < cols)
-                            w[q] = srow[sj[q]];
+                    if (j + q < ncols) {
+                        if ((unsigned)sj[q] < (unsigned)ncols)
+                            w[q] = row[sj[q]];
                         else
                             bad = true;
                     }
                 }
             }
-            const uint64_t a = curve_tile_base<CURVE>(Id, (uint64_t)j >> ltd, lgd, ltd) + doff +
-                               (uint64_t)(j & (Td - 1));
-            *reinterpret_cast<uint4*>(dst + a) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(dst + w_.at()) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    };
+
+    int64_t i = blockIdx.x;
+    int64_t si = i < nd ? source_row(i) : -1;
+    if (NBUF == 2) {
+        fetch(si, sbuf);
+        cp_async_commit();
+    }
+    for (int k = 0; i < nd; ++k, i += gridDim.x) {
+        uint32_t* cur = sbuf + (NBUF == 2 ? (int64_t)(k & 1) * 4 * c4 : 0);
+        int64_t si_next = -1;
+        if (NBUF == 2) {
+            const int64_t inext = i + gridDim.x;
+            si_next = inext < nd ? source_row(inext) : -1;
+            fetch(si_next, sbuf + (int64_t)((k + 1) & 1) * 4 * c4);
+            cp_async_commit();
+            cp_async_wait<1>();  // this thread's copies of the current row have landed
+        } else {
+            fetch(si, cur);
+            cp_async_commit();
+            cp_async_wait<0>();
         }
         __syncthreads();
+        gather(i, si, cur);
+        __syncthreads();  // the buffer is free before the next copies into it
+        if (NBUF == 2) si = si_next;
+        else if (i + gridDim.x < nd) si = source_row(i + gridDim.x);
     }
+    cp_async_wait<0>();
     if (__syncthreads_or(bad) && threadIdx.x == 0) fm_raise(status, FM_EINVAL);
 }
 
@@ -396,6 +525,9 @@ __global__ void __launch_bounds__(kThreads) validate_kernel(const uint32_t* __re
     if (__any_sync(0xffffffffu, bad) && lane == 0) fm_raise(status, FM_ERANGE);
 }
 
+// Shared memory the row-staged kernels may use: one or two source rows.
+constexpr size_t kStagedRowMax = 200 * 1024;
+
 int grid_for(int64_t tiles)
 {
     const int64_t cap = (int64_t)fm_sm_count() * 8;
@@ -416,13 +548,20 @@ int to_morton_impl(const T* src, int64_t rows, int64_t cols, int64_t ld, const i
         if (!status) return FM_ECUDA;
     }
     const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
-    const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
-    if (CURVE == kMorton && cp && dst.log2_T >= 2 && row_bytes <= 96 * 1024) {
-        const int grid = (int)std::min<int64_t>(n, (int64_t)fm_sm_count() * 8);
-        FM_CUDA_TRY(cudaFuncSetAttribute(to_morton_rowgather_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        to_morton_rowgather_kernel<T><<<grid, kThreads, row_bytes, (cudaStream_t)stream>>>(
-            src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T, status);
+    constexpr int kVec = 16 / sizeof(T);
+    const size_t row_bytes = (size_t)((cols + kVec - 1) / kVec * kVec) * sizeof(T);
+    if (CURVE == kMorton && (rp || cp) && dst.log2_T >= 2 && row_bytes <= kStagedRowMax) {
+        // two row buffers (the next row's copies overlap the gather) when the
+        // rows are whole 16-byte vectors and two fit, else one
+        const bool two = ((ld % kVec) == 0) && (((uintptr_t)src & 15) == 0) && 2 * row_bytes <= kStagedRowMax;
+        auto k = two ? to_morton_rowgather_kernel<T, 2> : to_morton_rowgather_kernel<T, 1>;
+        const size_t smem = two ? 2 * row_bytes : row_bytes;
+        FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedRowMax));
+        int per_sm = 0;
+        FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)fm_sm_count() * std::max(1, per_sm)));
+        k<<<grid, kThreads, smem, (cudaStream_t)stream>>>(src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid,
+                                                         dst.log2_T, status);
     } else if (rp || cp)
         to_morton_kernel<true, T, CURVE><<<grid_for(tiles), kThreads, 0, (cudaStream_t)stream>>>(
             src, rows, cols, ld, rp, cp, dst.base, dst.log2_grid, dst.log2_T, status);
@@ -514,10 +653,6 @@ extern "C" int fm_validate_residues(fm_sub X, uint32_t p, fm_stream stream)
 
 namespace {
 
-// Largest staged source row: the row-staged permutation keeps one source row of
-// up to this many bytes in shared memory.
-constexpr size_t kStagedRowMax = 200 * 1024;
-
 template <int CURVE>
 int permute_impl(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols, const int32_t* row_perm,
                  const int32_t* col_perm, fm_stream stream)
@@ -534,14 +669,18 @@ int permute_impl(fm_matrix src, fm_matrix dst, int64_t rows, int64_t cols, const
     cudaStream_t s = (cudaStream_t)stream;
     const size_t row_bytes = (size_t)((cols + 3) & ~(int64_t)3) * 4;
     if (src.log2_T >= 2 && dst.log2_T >= 2 && row_bytes <= kStagedRowMax) {
-        auto k = permute_staged_kernel<CURVE>;
+        // two row buffers (copies of the next row overlap the gather) when
+        // they fit, else one
+        const bool two = 2 * row_bytes <= kStagedRowMax;
+        auto k = two ? permute_staged_kernel<CURVE, 2> : permute_staged_kernel<CURVE, 1>;
+        const size_t smem = two ? 2 * row_bytes : row_bytes;
         FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedRowMax));
         int per_sm = 0;
-        FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, row_bytes));
+        FM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem));
         const int64_t cap = (int64_t)fm_sm_count() * std::max(1, per_sm);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nd, cap));
-        k<<<grid, kThreads, row_bytes, s>>>(src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid,
-                                            dst.log2_T, rows, cols, row_perm, col_perm, status);
+        k<<<grid, kThreads, smem, s>>>(src.base, src.log2_grid, src.log2_T, dst.base, dst.log2_grid,
+                                       dst.log2_T, rows, cols, row_perm, col_perm, status);
     } else {
         const int64_t tiles = (int64_t)1 << (2 * dst.log2_grid);
         permute_kernel<CURVE><<<grid_for(tiles), kThreads, 0, s>>>(
