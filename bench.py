@@ -447,8 +447,9 @@ def run_configs(fm, torch, dev, stream, peaks, seed=21):
                T' = 64, row-major inputs converted on the device with random row
                and column permutations of A, plain form (aligned/contained
                decomposition); checked against the limb form;
-    p31     -- C = A*B mod 2^31 - 1 at 4096^3, limb form (four limbs, 16 limb
-               products on the tensor cores); checked against the plain form."""
+    p31     -- C = A*B mod 2^31 - 1 at 4096^3, limb form (four limbs, 10 limb
+               products on the tensor cores: Karatsuba over every pair of
+               limbs); checked against the plain form."""
     import numpy as np
 
     import fm_inputs
@@ -566,9 +567,12 @@ def run_configs(fm, torch, dev, stream, peaks, seed=21):
     same = bool(torch.equal(res[0], res[1]))
     del xa, xb, res
     burst, _, _, src = measured_peaks()
-    mma = 16 * 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    # four limbs, Karatsuba over every pair: 4 + 6 = 10 limb products
+    mma = 10 * 2.0 * n ** 3 / (ms / 1e3) / 1e12
     out["p31"] = {"workload": "C = A*B mod 2^31-1, M=N=K=4096, Morton-hybrid T'=128, limb form (4 limbs, "
-                              "16 limb products)", "ms": ms, "value": 2.0 * n ** 3 / (ms / 1e3) / 1e9,
+                              "10 limb products: Karatsuba over every pair of limbs)", "ms": ms,
+                  "value": 2.0 * n ** 3 / (ms / 1e3) / 1e9,
+                  "ceiling_gops": 1e3 * burst / 10, "frac_of_ceiling": 2.0 * n ** 3 / (ms / 1e3) / 1e9 / (1e3 * burst / 10),
                   "unit": "Gop/s", "mma_tflops": mma, "frac_of_tensor_peak": mma / burst,
                   "peak_source": f"bf16 burst, {src}", "bit_identical_to_plain": same}
     torch.cuda.empty_cache()

@@ -128,7 +128,7 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
                     for (int pair : {-1, 1}) {
                         if (pair == 1 && bn != 256) continue;
                         limb(bn, kc, 0, pair);
-                        if (q.n_planes == 3) limb(bn, kc, 1, pair);
+                        if (q.n_planes > q.w) limb(bn, kc, 1, pair);
                     }
                 }
             }
@@ -297,10 +297,10 @@ extern "C" int fm_autotune_batch(const fm_gemm_call* calls, int64_t n, uint32_t 
                 for (int kc : {full, full / 2}) {
                     if (kc < 64 || kc % 64) continue;
                     add(FM_ALGO_LIMB_TC, bn, kc, 0, 0);
-                    if (q.n_planes == 3) add(FM_ALGO_LIMB_TC, bn, kc, 1, 0);
+                    if (q.n_planes > q.w) add(FM_ALGO_LIMB_TC, bn, kc, 1, 0);
                 }
             }
-            if (q.n_planes == 3) add(FM_ALGO_LIMB_TC, 128, 0, 0, 1);  // fused: Karatsuba, 128 wide
+            if (q.fold && q.n_planes == 3) add(FM_ALGO_LIMB_TC, 128, 0, 0, 1);  // fused: Karatsuba, 128 wide
         }
     }
     if (!(flags & FM_TUNE_NO_PLAIN) && plain_lt) add(FM_ALGO_PLAIN, 0, 0, 0, 0);

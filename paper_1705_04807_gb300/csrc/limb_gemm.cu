@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
                 const bool same_next = !last_on_buffer && idx2 == idx;
                 const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
-                if (FOLD) {
+                if constexpr (FOLD) {
                     const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
                     for (int g = 0; g < (n32 + 1) / 2; ++g) {  // two 32-column chunks in flight
@@ -944,7 +944,35 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
                             (uint32_t)(((uint64_t)65536 - 256) % p)};
     bool kara = w == 2 && q.fold && !(opts && opts->no_karatsuba == 1);
     for (int k = 0; kara && k < 3; ++k) kara = wk[k] != 0 && gcd_u64(wk[k], p) == 1;
-    if (kara) {
+    // Residue form (w >= 2, p >= 2^16 or even): Karatsuba over every pair of
+    // limbs, A_i B_j + A_j B_i = (A_i + A_j)(B_i + B_j) - A_i B_i - A_j B_j, so
+    //   A*B = sum_i w_ii A_i B_i + sum_{i<j} 256^(i+j) (A_i + A_j)(B_i + B_j)
+    // with w_ii = 256^(2i) - sum_{j != i} 256^(i+j): w + w (w - 1) / 2 products
+    // (6 for w = 3, 10 for w = 4) instead of w^2. The residue form reduces each
+    // product on its own, so the weights need not be invertible. Digit sums lie
+    // in [-256, 254]: a term of a pair product is at most 2^16 in magnitude.
+    const bool kara_res = !q.fold && w >= 2 && !(opts && opts->no_karatsuba == 1);
+    if (kara_res) {
+        const int cs_m = std::max(1, std::min(cs, (int)(((int64_t)1 << 24) / (256 * 256) / kBK)));
+        const int npairs = w * (w - 1) / 2;
+        q.n_planes = w + npairs;
+        q.n_products = w + npairs;
+        for (int i = 0; i < w; ++i) {
+            uint64_t wt = powmod(256, (uint64_t)(2 * i), p);
+            for (int j = 0; j < w; ++j)
+                if (j != i) wt = (wt + p - powmod(256, (uint64_t)(i + j), p)) % p;
+            q.prod_a[i] = q.prod_b[i] = i;
+            q.prod_cs[i] = cs;
+            q.prod_w[i] = (uint32_t)wt;
+        }
+        for (int u = 0; u < npairs; ++u) {
+            int i, j;
+            karatsuba_pair(u, i, j);
+            q.prod_a[w + u] = q.prod_b[w + u] = w + u;
+            q.prod_cs[w + u] = cs_m;
+            q.prod_w[w + u] = powmod(256, (uint64_t)(i + j), p);
+        }
+    } else if (kara) {
         // middle product: for p < 2^16 the representative is >= 32640 - p > -32896,
         // so d0 = d1 = -128 never occurs and |d0 + d1| <= 255; a term is at most
         // 255^2, and the value carried into a chunk is below p in magnitude (a

@@ -2,7 +2,8 @@
 //
 // Each residue x in [0, p) becomes w balanced digits in [-128, 127] (base 256)
 // of its representative r = x if x <= Hi else x - p, Hi = 127 * sum_{t<w} 256^t;
-// with Karatsuba (w = 2) a third plane holds d0 + d1. The kernels read the
+// with Karatsuba further planes hold the digit sums d_i + d_j, i < j < w (one
+// for w = 2, three for w = 3, six for w = 4). The kernels read the
 // (sub-)matrices from the Morton-hybrid layout (Sec. 1), re-base them to an
 // aligned grid and write the planes as tiles in the 128-byte-swizzled K-major
 // layout the tensor-core descriptors expect, so that every pipeline stage of
@@ -35,6 +36,16 @@ __device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, 
             d[t] = 0;
         }
     }
+}
+
+// Value of plane t for one residue's digits d: digit t for t < w, else the
+// Karatsuba digit sum d_i + d_j of pair t - w (|.| <= 256).
+__device__ __forceinline__ int plane_value(const int (&d)[4], int t, int w)
+{
+    if (t < w) return d[t & 3];
+    int i, j;
+    karatsuba_pair(t - w, i, j);
+    return d[i & 3] + d[j & 3];
 }
 
 // Two integers in [-512, 511] as a packed pair of IEEE halves, exactly: the
@@ -116,12 +127,11 @@ __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int
         for (int e = 0; e < 8; ++e) limb_digits(x[it][e], p, hi, w, d[e]);
         const uint32_t off = sw128_offset(r, kc);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kMaxPlanes; ++t) {
             if (t < n_planes) {
                 int q[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
-                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
+                for (int e = 0; e < 8; ++e) q[e] = plane_value(d[e], t, w);
                 uint4 v;
                 v.x = pack_half2(q[0], q[1]);
                 v.y = pack_half2(q[2], q[3]);
@@ -192,12 +202,11 @@ __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int
         }
         const uint32_t off = sw128_offset(n, kc);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kMaxPlanes; ++t) {
             if (t < n_planes) {
                 int q[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e)  // plane w (Karatsuba) holds d0 + d1, |.| <= 256
-                    q[e] = t == w ? d[e][0] + d[e][1] : d[e][t];
+                for (int e = 0; e < 8; ++e) q[e] = plane_value(d[e], t, w);
                 uint4 v;
                 v.x = pack_half2(q[0], q[1]);
                 v.y = pack_half2(q[2], q[3]);

@@ -160,6 +160,23 @@ def test_limb_accumulator_extremes_p31(env, orc, K):
     _constant_case(env, orc, P31, extremes[0], extremes[3], K, fm.FM_ALGO_LIMB_TC)
 
 
+@pytest.mark.parametrize("K", [256, 512, 1024, 2048])
+@pytest.mark.parametrize("p", [P31, 1000003, 65537])
+def test_limb_karatsuba_pair_extremes(env, orc, K, p):
+    # The residue form multiplies the digit sums d_i + d_j of every pair of
+    # limbs in chunks of 256 terms. Inputs whose pair digits are both -128 make
+    # those terms (-256)^2 = 2^16, so a 256-term chunk sums to exactly 2^24:
+    # x = 256^3 - 128 (1 + 256 + 256^2) = 8355712 has digits (-128, -128, -128, 1)
+    # for w = 4; x = 256^2 - 128 (1 + 256) = 32640 has digits (-128, -128, 1) for
+    # w = 3. Mixed with the +127 extremes (digit sums 254) as well.
+    fm = env[0]
+    w = 4 if p > (1 << 24) else 3
+    lo = 8355712 if w == 4 else 32640
+    hi = 127 * (1 + 256 + 65536) if w == 4 else 127 * 257
+    for a, b in ((lo, lo), (lo, hi), (hi, hi)):
+        _constant_case(env, orc, p, a, b, K, fm.FM_ALGO_LIMB_TC)
+
+
 def test_empty_and_degenerate(env, orc):
     fm, dev = env
     C = MortonMatrix(fm, dev, 2, 5, fill=fm_inputs.uniform_residues(1, (128, 128), P16))

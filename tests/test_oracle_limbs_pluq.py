@@ -108,3 +108,39 @@ def test_pluq_rank_deficient_against_library_rank(orc, p):
         dm = DomainMatrix([[GF(p)(int(v)) for v in row] for row in A.tolist()], (m, n), GF(p))
         assert rank == dm.rank()
         assert rank <= r
+
+
+@pytest.mark.parametrize("p", [65537, 1000003, 16777259, 2147483647, 65534])
+def test_pairwise_karatsuba_digit_sums_and_identity(orc, p):
+    # Karatsuba over every pair of limbs (the tensor-core residue form for w >= 2,
+    # p >= 2^16 or even): a digit sum d_i + d_j stays in [-256, 254], so a term of
+    # a pair product is at most 2^16 and a 256-term chunk at most 2^24 (exact in
+    # FP32); and sum_i w_ii A_i B_i + sum_{i<j} 256^(i+j) (A_i + A_j)(B_i + B_j)
+    # with w_ii = 256^(2i) - sum_{j != i} 256^(i+j) equals the product of the
+    # representatives over the integers, hence A*B mod p
+    from oracle import limbs
+    w = limbs.n_limbs(p)
+    _, hi = limbs.bounds(w)
+    x = np.concatenate([fm_inputs.uniform_residues(3, 100000, p).astype(np.int64),
+                        np.array([0, 1, 127, 128, hi, hi + 1, p - 2, p - 1], dtype=np.int64)])
+    x = x[x < p]
+    d = limbs.split(x, p).astype(np.int64)
+    for i in range(w):
+        for j in range(i + 1, w):
+            s = d[i] + d[j]
+            assert s.min() >= -256 and s.max() <= 254
+    assert 256 * 256 * 256 <= 1 << 24
+    A = fm_inputs.uniform_residues(4, (7, 40), p, 1)
+    B = fm_inputs.uniform_residues(4, (40, 5), p, 2)
+    dA, dB = limbs.split(A, p).astype(object), limbs.split(B, p).astype(object)
+    total = np.zeros((7, 5), dtype=object)
+    for i in range(w):
+        wii = 256 ** (2 * i) - sum(256 ** (i + j) for j in range(w) if j != i)
+        total = total + wii * (dA[i] @ dB[i])
+        for j in range(i + 1, w):
+            total = total + 256 ** (i + j) * ((dA[i] + dA[j]) @ (dB[i] + dB[j]))
+    rA = limbs.recombine(limbs.split(A, p)).astype(object)
+    rB = limbs.recombine(limbs.split(B, p)).astype(object)
+    assert np.array_equal(total, rA @ rB)
+    got = np.array([[int(v) % p for v in row] for row in total], dtype=np.uint32)
+    assert np.array_equal(got, orc.gemm_modp(None, A, B, p, 0))
