@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-gf2", action="store_true", help="skip the GF(2) measurements")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the small, Schur-update and 31-bit workloads")
+    ap.add_argument("--case", default=None, choices=["gemm", "gemm_p31", "permute", "to_morton_permuted"],
+                    help="profiling aid: run one kernel's call --steps times at --n (T' = --T) after "
+                         "--warmup calls, print nothing else, exit")
+    ap.add_argument("--T", type=int, default=128, help="T' of the --case matrices")
     return ap.parse_args()
 
 
@@ -539,7 +543,8 @@ def run_configs(fm, torch, dev, stream, peaks, seed=21):
                                 "row and column permutations of A in the conversion, plain form",
                     "layout_ms": lay_ms, "layout_gbs": lay_bytes / (lay_ms / 1e3) / 1e9, "gemm_ms": gemm_ms,
                     "value": ops / (gemm_ms / 1e3) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same,
-                    "gemm_frac_of_imad_wide": ops / 2 / (gemm_ms / 1e3) / 1e12 / peaks["imad_wide"]}
+                    "gemm_frac_of_imad_wide": (ops / 2 / (gemm_ms / 1e3) / 1e12 / peaks["imad_wide"]
+                                               if peaks else None)}
     del tA, tB, tC, dA, dB, dC, snap
 
     # p31: 4096^3 at p = 2^31 - 1, limb form (T' = 128); the plain form, which
@@ -961,7 +966,8 @@ def run_fm(args, world, rank, local):
         e2e_line = e2e_u32
 
     # ---- measured arithmetic rates of the non-tensor pipes (T multiply-adds/s) ----
-    peaks = {name: fm.fm_measure_peak(kind, 1 << 16, s) / 1e12 for name, kind in (
+    # (with the comparison forms only: the plain and DFMA rooflines use them)
+    peaks = {} if args.no_compare else {name: fm.fm_measure_peak(kind, 1 << 16, s) / 1e12 for name, kind in (
         ("imad_wide", fm.FM_PEAK_IMAD_WIDE), ("imad32", fm.FM_PEAK_IMAD32), ("dfma", fm.FM_PEAK_DFMA),
         ("ffma", fm.FM_PEAK_FFMA), ("mma_s8", fm.FM_PEAK_MMA_S8))}
 
@@ -1079,9 +1085,10 @@ def run_fm(args, world, rank, local):
     # accumulation but needs 4 limb products per modular multiply-add (the
     # Karatsuba digit sums do not fit in 8 bits); the f16 carrier on tcgen05
     # runs at the bf16 burst rate with 3 (Karatsuba).
-    line["peaks"] = dict(peaks, unit="T multiply-adds/s",
-                         modular_ceiling_gops={"mma_s8_4_products": 2e3 * peaks["mma_s8"] / 4,
-                                               "tcgen05_f16_3_products": 1e3 * burst / 3})
+    if peaks:
+        line["peaks"] = dict(peaks, unit="T multiply-adds/s",
+                             modular_ceiling_gops={"mma_s8_4_products": 2e3 * peaks["mma_s8"] / 4,
+                                                   "tcgen05_f16_3_products": 1e3 * burst / 3})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, secs = cpu_oracle_rate(n, p, target_s=12.0)
         line["cpu_baseline"] = {"value": v, "unit": "Gop/s", "cores": cores, "kind": "oracle",
@@ -1090,8 +1097,57 @@ def run_fm(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """One kernel's call, repeated, for an ncu capture of a small case: the limb
+    GEMM (C = A*B mod 65521 or mod 2^31 - 1, n^3), the Morton-to-Morton row and
+    column permutation, or the permuted row-major -> Morton conversion (n x n)."""
+    import numpy as np
+    import torch
+
+    import fm_inputs
+    import paper_1705_04807_gb300 as fm
+    from paper_1705_04807_gb300 import build as fmbuild
+    fmbuild.build()
+    fm.lib()
+    dev = torch.device("cuda", 0)
+    n, lt = args.n, args.T.bit_length() - 1
+    lg = (n >> lt).bit_length() - 1
+    p = 2147483647 if args.case == "gemm_p31" else P
+
+    def morton(seed, stream):
+        x = torch.from_numpy(fm_inputs.uniform_residues(seed, (n, n), p, stream).view(np.int32)).to(dev)
+        t = torch.empty(n * n, dtype=torch.int32, device=dev)
+        m = fm.matrix(t, lg, lt)
+        fm.fm_layout_to_morton(x, n, n, n, m)
+        return x, t, m
+
+    if args.case in ("gemm", "gemm_p31"):
+        mats = [morton(1, q) for q in range(3)]
+        subs = [fm.sub(m, 0, 0, n, n) for _, _, m in mats]
+        call = lambda: fm.fm_gemm_modp(subs[0], subs[1], subs[2], p, fm.FM_OP_SET,  # noqa: E731
+                                       fm.FM_ALGO_LIMB_TC)
+    else:
+        x, t0, m0 = morton(1, 0)
+        t1 = torch.empty_like(t0)
+        m1 = fm.matrix(t1, lg, lt)
+        rp = torch.from_numpy(fm_inputs.permutation(1, n, 1)).to(dev)
+        cp = torch.from_numpy(fm_inputs.permutation(1, n, 2)).to(dev)
+        if args.case == "permute":
+            call = lambda: fm.fm_permute_rows_cols(m0, m1, n, n, rp, cp)  # noqa: E731
+        else:
+            call = lambda: fm.fm_layout_to_morton_permuted(x, n, n, n, rp, cp, m1)  # noqa: E731
+    for _ in range(args.warmup + args.steps):
+        call()
+    torch.cuda.synchronize()
+    st = fm.fm_get_last_device_status()
+    assert st == 0, f"device status {st}"
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

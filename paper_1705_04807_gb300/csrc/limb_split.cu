@@ -23,12 +23,13 @@ using namespace fm_limb;
 constexpr int kSplitThreads = 256;
 
 // ---- limb digits ----------------------------------------------------------
-__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, int w, int (&d)[4])
+template <int W>
+__device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, int (&d)[4])
 {
     int32_t r = (x <= (uint32_t)hi) ? (int32_t)x : (int32_t)((int64_t)x - (int64_t)p);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        if (t < w) {
+        if (t < W) {
             const int32_t dt = ((r + 128) & 255) - 128;
             d[t] = dt;
             r = (r - dt) >> 8;
@@ -36,16 +37,6 @@ __device__ __forceinline__ void limb_digits(uint32_t x, uint32_t p, int32_t hi, 
             d[t] = 0;
         }
     }
-}
-
-// Value of plane t for one residue's digits d: digit t for t < w, else the
-// Karatsuba digit sum d_i + d_j of pair t - w (|.| <= 256).
-__device__ __forceinline__ int plane_value(const int (&d)[4], int t, int w)
-{
-    if (t < w) return d[t & 3];
-    int i, j;
-    karatsuba_pair(t - w, i, j);
-    return d[i & 3] + d[j & 3];
 }
 
 // Two integers in [-512, 511] as a packed pair of IEEE halves, exactly: the
@@ -57,6 +48,47 @@ __device__ __forceinline__ uint32_t pack_half2(int lo, int hi)
     const uint32_t bits = (0x6400u + (uint32_t)(lo + 512)) | ((0x6400u + (uint32_t)(hi + 512)) << 16);
     const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&bits), __float2half2_rn(1536.0f));
     return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Planes per operand: W digits, plus the digit sums of every pair of them
+// with Karatsuba.
+template <int W, bool KARA>
+constexpr int kPlanes = W + (KARA ? W * (W - 1) / 2 : 0);
+
+// Value of plane T for one residue's digits d: digit T for T < W, else the
+// Karatsuba digit sum d_i + d_j of pair T - W (|.| <= 256; the pair order of
+// karatsuba_pair). T and W are compile-time, so d stays in registers.
+template <int T, int W>
+__device__ __forceinline__ int plane_value(const int (&d)[4])
+{
+    if constexpr (T < W) {
+        return d[T];
+    } else {
+        constexpr int u = T - W;
+        constexpr int j = u < 1 ? 1 : (u < 3 ? 2 : 3);
+        constexpr int i = u - j * (j - 1) / 2;
+        return d[i] + d[j];
+    }
+}
+
+// Writes planes T.. of 8 consecutive entries (digits d) as f16 at out + off of
+// each plane.
+template <int W, bool KARA, int T = 0>
+__device__ __forceinline__ void store_planes(const int (&d)[8][4], uint8_t* out, size_t plane_bytes,
+                                             uint32_t off)
+{
+    if constexpr (T < kPlanes<W, KARA>) {
+        int q[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) q[e] = plane_value<T, W>(d[e]);
+        uint4 v;
+        v.x = pack_half2(q[0], q[1]);
+        v.y = pack_half2(q[2], q[3]);
+        v.z = pack_half2(q[4], q[5]);
+        v.w = pack_half2(q[6], q[7]);
+        *reinterpret_cast<uint4*>(out + (size_t)T * plane_bytes + off) = v;
+        store_planes<W, KARA, T + 1>(d, out, plane_bytes, off);
+    }
 }
 
 // Byte offset of the 16-byte chunk kc (8 f16 values) of row r inside a tile
@@ -102,10 +134,10 @@ __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, 
 
 // A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
 // One CTA writes tile (mb, kb) of every plane.
+template <int W, bool KARA>
 __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int lt, int64_t row0,
-                                             int64_t col0, int64_t M, int64_t K, int KB, int tile, int w,
-                                             int n_planes, uint32_t p, int32_t hi,
-                                             uint8_t* __restrict__ planes, size_t plane_bytes)
+                                             int64_t col0, int64_t M, int64_t K, int KB, int tile, uint32_t p,
+                                             int32_t hi, uint8_t* __restrict__ planes, size_t plane_bytes)
 {
     const int mb = tile / KB, kb = tile % KB;
     uint8_t* out = planes + (size_t)tile * kATileBytes;
@@ -124,22 +156,8 @@ __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int
         const int r = c >> 3, kc = c & 7;
         int d[8][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) limb_digits(x[it][e], p, hi, w, d[e]);
-        const uint32_t off = sw128_offset(r, kc);
-#pragma unroll
-        for (int t = 0; t < kMaxPlanes; ++t) {
-            if (t < n_planes) {
-                int q[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) q[e] = plane_value(d[e], t, w);
-                uint4 v;
-                v.x = pack_half2(q[0], q[1]);
-                v.y = pack_half2(q[2], q[3]);
-                v.z = pack_half2(q[4], q[5]);
-                v.w = pack_half2(q[6], q[7]);
-                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
-            }
-        }
+        for (int e = 0; e < 8; ++e) limb_digits<W>(x[it][e], p, hi, d[e]);
+        store_planes<W, KARA>(d, out, plane_bytes, sw128_offset(r, kc));
     }
 }
 
@@ -147,10 +165,10 @@ __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int
 // transposed to K-major), swizzled. Staged through shared memory so that both
 // the Morton reads (along n, 16-byte vectors) and the tile writes (along k)
 // are coalesced. One CTA writes tile (nb, kb) of every plane.
-template <int BN>
+template <int BN, int W, bool KARA>
 __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int lt, int64_t row0,
-                                             int64_t col0, int64_t K, int64_t N, int KB, int tile, int w,
-                                             int n_planes, uint32_t p, int32_t hi,
+                                             int64_t col0, int64_t K, int64_t N, int KB, int tile, uint32_t p,
+                                             int32_t hi,
                                              uint8_t* __restrict__ planes, size_t plane_bytes,
                                              uint32_t* sb)
 {
@@ -198,66 +216,93 @@ __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int kk = kc * 8 + e;
-            limb_digits(sb[kk * BN + (n ^ ((kk >> 3) << 2))], p, hi, w, d[e]);
+            limb_digits<W>(sb[kk * BN + (n ^ ((kk >> 3) << 2))], p, hi, d[e]);
         }
-        const uint32_t off = sw128_offset(n, kc);
-#pragma unroll
-        for (int t = 0; t < kMaxPlanes; ++t) {
-            if (t < n_planes) {
-                int q[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) q[e] = plane_value(d[e], t, w);
-                uint4 v;
-                v.x = pack_half2(q[0], q[1]);
-                v.y = pack_half2(q[2], q[3]);
-                v.z = pack_half2(q[4], q[5]);
-                v.w = pack_half2(q[6], q[7]);
-                *reinterpret_cast<uint4*>(out + (size_t)t * plane_bytes + off) = v;
-            }
-        }
+        store_planes<W, KARA>(d, out, plane_bytes, sw128_offset(n, kc));
     }
 }
 
+template <int W, bool KARA>
 __global__ void __launch_bounds__(kSplitThreads)
     split_a_kernel(const uint32_t* __restrict__ A, int lt, int64_t row0, int64_t col0, int64_t M,
-                   int64_t K, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
+                   int64_t K, int KB, uint32_t p, int32_t hi, uint8_t* __restrict__ planes, size_t plane_bytes)
 {
-    split_a_tile(A, lt, row0, col0, M, K, KB, blockIdx.x, w, n_planes, p, hi, planes, plane_bytes);
+    split_a_tile<W, KARA>(A, lt, row0, col0, M, K, KB, blockIdx.x, p, hi, planes, plane_bytes);
 }
 
-template <int BN>
+template <int BN, int W, bool KARA>
 __global__ void __launch_bounds__(kSplitThreads)
     split_b_kernel(const uint32_t* __restrict__ B, int lt, int64_t row0, int64_t col0, int64_t K,
-                   int64_t N, int KB, int w, int n_planes, uint32_t p, int32_t hi,
-                   uint8_t* __restrict__ planes, size_t plane_bytes)
+                   int64_t N, int KB, uint32_t p, int32_t hi, uint8_t* __restrict__ planes, size_t plane_bytes)
 {
     extern __shared__ __align__(16) uint32_t sb[];
-    split_b_tile<BN>(B, lt, row0, col0, K, N, KB, blockIdx.x, w, n_planes, p, hi, planes, plane_bytes, sb);
+    split_b_tile<BN, W, KARA>(B, lt, row0, col0, K, N, KB, blockIdx.x, p, hi, planes, plane_bytes, sb);
 }
 
 // Batched: CTA b splits tile jobs[b].y of operand jobs[b].x (one launch for the
 // A (or B) operands of every call of a plan).
+template <int W, bool KARA>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_a_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, int w,
-                         int n_planes, uint32_t p, int32_t hi)
+    split_a_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, uint32_t p,
+                         int32_t hi)
 {
     const int2 j = jobs[blockIdx.x];
     const FmSplitDesc d = descs[j.x];
-    split_a_tile(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, w, n_planes, p, hi, d.out,
-                 d.plane_bytes);
+    split_a_tile<W, KARA>(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, p, hi, d.out, d.plane_bytes);
 }
 
-template <int BN>
+template <int BN, int W, bool KARA>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_b_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, int w,
-                         int n_planes, uint32_t p, int32_t hi)
+    split_b_batch_kernel(const FmSplitDesc* __restrict__ descs, const int2* __restrict__ jobs, uint32_t p,
+                         int32_t hi)
 {
     extern __shared__ __align__(16) uint32_t sb[];
     const int2 j = jobs[blockIdx.x];
     const FmSplitDesc d = descs[j.x];
-    split_b_tile<BN>(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, w, n_planes, p, hi, d.out,
-                     d.plane_bytes, sb);
+    split_b_tile<BN, W, KARA>(d.src, d.lt, d.row0, d.col0, d.rows, d.cols, d.KB, j.y, p, hi, d.out,
+                              d.plane_bytes, sb);
+}
+
+// The split kernels for a plan's limb count and Karatsuba choice.
+template <int W, bool KARA>
+struct SplitKernels {
+    static constexpr auto a = split_a_kernel<W, KARA>;
+    static constexpr auto b128 = split_b_kernel<128, W, KARA>;
+    static constexpr auto b256 = split_b_kernel<256, W, KARA>;
+    static constexpr auto ab = split_a_batch_kernel<W, KARA>;
+    static constexpr auto bb128 = split_b_batch_kernel<128, W, KARA>;
+    static constexpr auto bb256 = split_b_batch_kernel<256, W, KARA>;
+};
+
+struct SplitSet {
+    decltype(&split_a_kernel<1, false>) a;
+    decltype(&split_b_kernel<128, 1, false>) b128, b256;
+    decltype(&split_a_batch_kernel<1, false>) ab;
+    decltype(&split_b_batch_kernel<128, 1, false>) bb128, bb256;
+};
+
+template <int W, bool KARA>
+SplitSet split_set()
+{
+    return SplitSet{SplitKernels<W, KARA>::a,  SplitKernels<W, KARA>::b128, SplitKernels<W, KARA>::b256,
+                    SplitKernels<W, KARA>::ab, SplitKernels<W, KARA>::bb128, SplitKernels<W, KARA>::bb256};
+}
+
+// Kernels for plan q: w digits, Karatsuba when the plan carries pair planes.
+int split_kernels(const FmLimbPlan& q, SplitSet* out)
+{
+    const bool kara = q.n_planes > q.w;
+    if (kara && q.n_planes != q.w + q.w * (q.w - 1) / 2) return FM_EINVAL;
+    switch (q.w * 2 + (kara ? 1 : 0)) {
+    case 2: *out = split_set<1, false>(); return FM_OK;
+    case 4: *out = split_set<2, false>(); return FM_OK;
+    case 5: *out = split_set<2, true>(); return FM_OK;
+    case 6: *out = split_set<3, false>(); return FM_OK;
+    case 7: *out = split_set<3, true>(); return FM_OK;
+    case 8: *out = split_set<4, false>(); return FM_OK;
+    case 9: *out = split_set<4, true>(); return FM_OK;
+    default: return FM_EINVAL;
+    }
 }
 
 }  // namespace
@@ -276,19 +321,19 @@ int fm_limb_split_run(const FmLimbPlan& q, fm_sub X, int role, uint32_t p, void*
 {
     uint8_t* out = static_cast<uint8_t*>(planes);
     const int32_t hi = limb_hi(q.w);
+    SplitSet ks;
+    FM_TRY(split_kernels(q, &ks));
     if (role == FM_LIMB_A) {
         if (q.MB * q.KB == 0) return FM_OK;
-        split_a_kernel<<<q.MB * q.KB, kSplitThreads, 0, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0,
-                                                             q.M, q.K, q.KB, q.w, q.n_planes, p, hi,
-                                                             out, q.a_plane_bytes);
+        ks.a<<<q.MB * q.KB, kSplitThreads, 0, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.M, q.K, q.KB, p, hi,
+                                                   out, q.a_plane_bytes);
     } else {
         if (q.NB * q.KB == 0) return FM_OK;
         const size_t sb_smem = (size_t)kBK * q.block_n * 4;
-        auto k = q.block_n == 256 ? split_b_kernel<256> : split_b_kernel<128>;
+        auto k = q.block_n == 256 ? ks.b256 : ks.b128;
         FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
-        k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N,
-                                                      q.KB, q.w, q.n_planes, p, hi, out,
-                                                      q.b_plane_bytes);
+        k<<<q.NB * q.KB, kSplitThreads, sb_smem, s>>>(X.m.base, X.m.log2_T, X.row0, X.col0, q.K, q.N, q.KB, p,
+                                                      hi, out, q.b_plane_bytes);
     }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
@@ -300,13 +345,15 @@ int fm_limb_split_batch_run(const FmLimbPlan& q, int role, const FmSplitDesc* d_
     if (n_jobs == 0) return FM_OK;
     if (n_jobs > 0x7fffffff) return FM_EINVAL;
     const int32_t hi = limb_hi(q.w);
+    SplitSet ks;
+    FM_TRY(split_kernels(q, &ks));
     if (role == FM_LIMB_A) {
-        split_a_batch_kernel<<<(unsigned)n_jobs, kSplitThreads, 0, s>>>(d_descs, d_jobs, q.w, q.n_planes, p, hi);
+        ks.ab<<<(unsigned)n_jobs, kSplitThreads, 0, s>>>(d_descs, d_jobs, p, hi);
     } else {
         const size_t sb_smem = (size_t)kBK * q.block_n * 4;
-        auto k = q.block_n == 256 ? split_b_batch_kernel<256> : split_b_batch_kernel<128>;
+        auto k = q.block_n == 256 ? ks.bb256 : ks.bb128;
         FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem));
-        k<<<(unsigned)n_jobs, kSplitThreads, sb_smem, s>>>(d_descs, d_jobs, q.w, q.n_planes, p, hi);
+        k<<<(unsigned)n_jobs, kSplitThreads, sb_smem, s>>>(d_descs, d_jobs, p, hi);
     }
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
