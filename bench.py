@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-gf2", action="store_true", help="skip the GF(2) measurements")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the small, Schur-update and 31-bit workloads")
-    ap.add_argument("--case", default=None, choices=["gemm", "gemm_p31", "permute", "to_morton_permuted"],
+    ap.add_argument("--case", default=None, choices=["gemm", "gemm_p31", "permute", "to_morton_permuted", "tu"],
                     help="profiling aid: run one kernel's call --steps times at --n (T' = --T) after "
                          "--warmup calls, print nothing else, exit")
     ap.add_argument("--T", type=int, default=128, help="T' of the --case matrices")
@@ -1110,6 +1110,10 @@ def run_case(args):
     fmbuild.build()
     fm.lib()
     dev = torch.device("cuda", 0)
+    if args.case == "tu":  # the TU workload (16384 x 12288, rank 10000), one factorization
+        r = run_tu(fm, torch, dev, torch.cuda.current_stream())
+        assert r["rank"] == r["rank_expected"], r
+        return
     n, lt = args.n, args.T.bit_length() - 1
     lg = (n >> lt).bit_length() - 1
     p = 2147483647 if args.case == "gemm_p31" else P
@@ -1124,7 +1128,7 @@ def run_case(args):
     if args.case in ("gemm", "gemm_p31"):
         mats = [morton(1, q) for q in range(3)]
         subs = [fm.sub(m, 0, 0, n, n) for _, _, m in mats]
-        call = lambda: fm.fm_gemm_modp(subs[0], subs[1], subs[2], p, fm.FM_OP_SET,  # noqa: E731
+        call = lambda: fm.fm_gemm_modp(subs[0], subs[1], subs[2], p, fm.FM_OP_SUB,  # noqa: E731
                                        fm.FM_ALGO_LIMB_TC)
     else:
         x, t0, m0 = morton(1, 0)

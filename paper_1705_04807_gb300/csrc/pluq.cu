@@ -158,6 +158,29 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const PanelArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.n_piv = found;
 }
 
+// *nz = 1 if rows [r0, m) x columns [c0, c0 + w) hold a nonzero (left at 0
+// otherwise): a panel with no nonzero has no pivot, and all its columns are
+// skipped without a search. One warp per row, contiguous runs inside tile rows.
+__global__ void panel_nonzero_kernel(const uint32_t* __restrict__ A, int lt, int64_t r0, int64_t m, int64_t c0,
+                                     int w, int* nz)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t T = (int64_t)1 << lt;
+    bool any = false;
+    for (int64_t i = r0 + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < m && !any; i += warps) {
+        for (int64_t j = 0; j < w;) {
+            const uint64_t gj = (uint64_t)(c0 + j);
+            const int64_t run = min((int64_t)w - j, T - (int64_t)(gj & (uint64_t)(T - 1)));
+            const uint32_t* seg = A + fm_encode((uint64_t)i, gj, lt);
+            for (int64_t e = lane; e < run; e += 32) any |= __ldg(seg + e) != 0u;
+            j += run;
+        }
+        any = __any_sync(0xffffffffu, any);
+    }
+    if (any && lane == 0) atomicOr(nz, 1);
+}
+
 // Columns [c0, c0 + w) of rows [0, m) reordered: new column t = old order[t].
 __global__ void permute_panel_cols_kernel(uint32_t* A, int lt, int64_t m, int64_t c0, int w,
                                           const int* __restrict__ order)
@@ -532,9 +555,14 @@ __device__ __forceinline__ uint32_t neg_mod(uint64_t acc, uint32_t p)
     return r == 0 ? 0u : p - r;
 }
 
-__global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
-                                                              int k, uint32_t* X, int xlt, uint32_t p,
-                                                              uint64_t mu)
+// UPPER = false: X = L^-1 for the unit lower triangle L of A (as above).
+// UPPER = true: X = U^-1 for the upper triangle U of A rows [r0, r0+k) x
+// columns [c0, c0+k) with dinv[t] = 1 / U(t, t): U = diag(U) V with V unit
+// upper, so the same inversion runs on the unit lower V^T, and
+// U^-1 (i, j) = (V^T)^-1 (j, i) / U(j, j).
+template <bool UPPER>
+__device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t r0, int64_t c0, int k, uint32_t* X,
+                                             int xlt, uint32_t p, uint64_t mu, const uint32_t* dinv)
 {
     extern __shared__ uint32_t smx[];
     constexpr int K = kNb;                 // padded size, 4 blocks of 32
@@ -544,7 +572,14 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A,
     const int nb = (k + 31) / 32;
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
         const int i = e / K, t = e % K;
-        L[e] = (t < i && i < k) ? A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)] : 0u;
+        uint32_t v = 0;
+        if (t < i && i < k) {
+            if (UPPER)
+                v = mulmod(A[fm_encode((uint64_t)(r0 + t), (uint64_t)(c0 + i), lt)], dinv[t], p, mu);
+            else
+                v = A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)];
+        }
+        L[e] = v;
         Xs[e] = i == t ? 1u : 0u;
     }
     __syncthreads();
@@ -580,8 +615,126 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A,
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x)
-        X[fm_encode((uint64_t)(e / k), (uint64_t)(e % k), xlt)] = Xs[(e / k) * K + (e % k)];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e % k;
+        X[fm_encode((uint64_t)i, (uint64_t)j, xlt)] =
+            UPPER ? mulmod(Xs[j * K + i], dinv[j], p, mu) : Xs[i * K + j];
+    }
+}
+
+__global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
+                                                              int k, uint32_t* X, int xlt, uint32_t p,
+                                                              uint64_t mu)
+{
+    tri_inv_body<false>(A, lt, r0, c0, k, X, xlt, p, mu, nullptr);
+}
+
+// Both inverses of a diagonal block factored by diag_lu_kernel: CTA 0 writes
+// X = L11^-1, CTA 1 writes Y = U11^-1.
+__global__ void __launch_bounds__(kInvThreads) tri_inv2_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
+                                                               uint32_t* X, uint32_t* Y, int xlt, uint32_t p,
+                                                               uint64_t mu, const uint32_t* dinv)
+{
+    if (blockIdx.x == 0)
+        tri_inv_body<false>(A, lt, r0, c0, kNb, X, xlt, p, mu, nullptr);
+    else
+        tri_inv_body<true>(A, lt, r0, c0, kNb, Y, xlt, p, mu, dinv);
+}
+
+// ---- diagonal-block fast path -------------------------------------------------
+// In a panel whose 128 diagonal entries are all nonzero when elimination
+// reaches them, the first-nonzero rule picks row r + t for column t: no row
+// exchanges, and the panel factors as [L11; L21] U11 with L21 = A21 U11^-1.
+// diag_lu_kernel factors the 128 x 128 diagonal block in one CTA, in shared
+// memory, without divisions: step t replaces row i > t by c_t S_i - S_i[t] S_t
+// (c_t = S_t[t]), which keeps every row a multiple sigma_t = c_0 ... c_{t-1} of
+// the row the division form computes; afterwards l_it = S_i[t] / c_t and
+// U row t = S_t / sigma_t, with all 2 x 128 inverses taken at once. A zero c_t
+// means the rule would search below the block: *flag = 1 and the block is left
+// unchanged (the column-by-column kernel then factors the panel). On success
+// L11 (strictly lower) and U11 (upper) are written into A and dinv[t] =
+// 1 / U11(t, t).
+constexpr int kDiagThreads = 1024;
+
+__device__ __forceinline__ uint32_t powmod_dev(uint32_t a, uint32_t e, uint32_t p, uint64_t mu)
+{
+    uint32_t r = 1 % p, b = a;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, p, mu);
+        b = mulmod(b, b, p, mu);
+        e >>= 1;
+    }
+    return r;
+}
+
+// a * b mod p for p < 2^16 (a, b < p): the product fits 32 bits; one Barrett
+// step with mu32 = floor(2^32 / p) leaves it below 2p
+__device__ __forceinline__ uint32_t mulmod16(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32)
+{
+    const uint32_t x = a * b;
+    uint32_t r = x - __umulhi(x, mu32) * p;
+    return r >= p ? r - p : r;
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(kDiagThreads) diag_lu_kernel(uint32_t* A, int lt, int64_t r0, int64_t c0,
+                                                               uint32_t p, uint64_t mu, uint32_t* dinv, int* flag)
+{
+    const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
+    extern __shared__ uint32_t D[];  // [kNb][kNb]
+    __shared__ uint32_t cpiv[kNb], cinv[kNb], sig[kNb], sinv[kNb];
+    __shared__ int s_zero;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < kNb * kNb; e += kDiagThreads)
+        D[e] = A[fm_encode((uint64_t)(r0 + e / kNb), (uint64_t)(c0 + e % kNb), lt)];
+    if (threadIdx.x == 0) s_zero = 0;
+    for (int t = 0; t < kNb; ++t) {
+        __syncthreads();
+        const uint32_t ct = D[t * kNb + t];
+        if (ct == 0) {
+            if (threadIdx.x == 0) s_zero = 1;
+            break;
+        }
+        if (threadIdx.x == 0) cpiv[t] = ct;
+        for (int i = t + 1 + ty; i < kNb; i += 32) {
+            const uint32_t sit = D[i * kNb + t];
+            for (int j = t + 1 + tx; j < kNb; j += 32) {
+                const uint32_t x = D[i * kNb + j], y = D[t * kNb + j];
+                D[i * kNb + j] = SMALL ? submod(mulmod16(ct, x, p, mu32), mulmod16(sit, y, p, mu32), p)
+                                       : submod(mulmod(ct, x, p, mu), mulmod(sit, y, p, mu), p);
+            }
+        }
+    }
+    __syncthreads();
+    if (s_zero) {
+        if (threadIdx.x == 0) *flag = 1;
+        return;
+    }
+    // sigma_t = c_0 ... c_{t-1}; the inverses of every c_t and sigma_t at once
+    if (threadIdx.x == 0) {
+        uint32_t sg = 1 % p;
+        for (int t = 0; t < kNb; ++t) {
+            sig[t] = sg;
+            sg = mulmod(sg, cpiv[t], p, mu);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNb) {
+        cinv[threadIdx.x] = powmod_dev(cpiv[threadIdx.x], p - 2, p, mu);
+    } else if (threadIdx.x < 2 * kNb) {
+        const int t = threadIdx.x - kNb;
+        sinv[t] = powmod_dev(sig[t], p - 2, p, mu);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kNb * kNb; e += kDiagThreads) {
+        const int i = e / kNb, j = e % kNb;
+        const uint32_t v = D[e];
+        const uint32_t out = j < i ? mulmod(v, cinv[j], p, mu) : mulmod(v, sinv[i], p, mu);
+        A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + j), lt)] = out;
+    }
+    // 1 / U11(t, t) = sigma_t / c_t
+    if (threadIdx.x < kNb) dinv[threadIdx.x] = mulmod(sig[threadIdx.x], cinv[threadIdx.x], p, mu);
+    if (threadIdx.x == 0) *flag = 0;
 }
 
 }  // namespace
@@ -635,16 +788,99 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     const int grid_g = sms * std::min(per_sm, 2);  // global-memory panel kernel
     const uint64_t mu = ~0ull / p;
 
+    // After a panel with k pivots in rows [r, r + k) and columns [c0, c0 + k):
+    // U12 <- L11^-1 A12 as a product (Sec. 2: S_A = S_B * S_C) with X = L11^-1
+    // (written into A12 itself: the limb product splits A12 into planes before
+    // A12 is written), then A22 <- A22 - L21 U12 by fm_gemm_modp on three
+    // disjoint sub-matrices of A.
+    int64_t c0 = 0;
+    int fast_panels = 0, searched_panels = 0, zero_panels = 0;
+    auto update_right = [&](int64_t r_, int k_, fm_matrix Xm) -> int {
+        const int64_t cl = c0 + std::min<int64_t>(kNb, n - c0);
+        if (cl >= n || k_ == 0) return FM_OK;
+        const int64_t cols = n - cl;
+        const fm_sub A12{Am, r_, cl, k_, cols};
+        FmLimbPlan lq;
+        FM_TRY(fm_limb_plan(k_, cols, k_, p, nullptr, &lq));
+        void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
+        if (!lws) return FM_ENOMEM;
+        FM_TRY(fm_limb_run(lq, A12, fm_sub{Xm, 0, 0, k_, k_}, A12, p, FM_OP_SET, lws, status, s));
+        if (r_ + k_ < m) {
+            const fm_sub C{Am, r_ + k_, cl, m - r_ - k_, cols};
+            const fm_sub L21{Am, r_ + k_, c0, m - r_ - k_, k_};
+            const fm_sub U12{Am, r_, cl, k_, cols};
+            FM_TRY(fm_gemm_modp(C, L21, U12, p, FM_OP_SUB, FM_ALGO_AUTO, nullptr, stream));
+        }
+        return FM_OK;
+    };
     std::vector<int> colid((size_t)n);  // original column at each storage position
     for (int64_t j = 0; j < n; ++j) colid[(size_t)j] = (int)j;
     std::vector<int> pivot_pos, skipped_pos;
     int64_t r = 0;
-    for (int64_t c0 = 0; c0 < n; c0 += kNb) {
+    for (c0 = 0; c0 < n; c0 += kNb) {
         const int w = (int)std::min<int64_t>(kNb, n - c0);
         if (r >= m) {
             for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
             continue;
         }
+        // X = L11^-1, Y = U11^-1 (the fast path), 1 / U11(t, t), and its flags
+        uint32_t* xs = static_cast<uint32_t*>(fm_workspace(4, (size_t)(2 * kNb * kNb + kNb + 4) * 4));
+        if (!xs) return FM_ENOMEM;
+        uint32_t* ys = xs + kNb * kNb;
+        uint32_t* dinv = ys + kNb * kNb;
+        int* d_flag = reinterpret_cast<int*>(dinv + kNb);
+        // a panel without a nonzero in rows [r, m) has no pivot: skip it
+        {
+            FM_CUDA_TRY(cudaMemsetAsync(d_flag + 1, 0, sizeof(int), s));
+            const int64_t ctas = (m - r + 7) / 8;  // one warp per row, 8 warps a CTA
+            panel_nonzero_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)sms * 8)), 256, 0, s>>>(
+                Am.base, Am.log2_T, r, m, c0, w, d_flag + 1);
+            FM_CUDA_TRY(cudaGetLastError());
+            int nz = 1;
+            FM_CUDA_TRY(cudaMemcpyAsync(&nz, d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (!nz) {
+                ++zero_panels;
+                for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
+                continue;
+            }
+        }
+        const size_t ismem = ((size_t)2 * kNb * kNb + 3 * 32 * 32) * 4;
+        // diagonal-block fast path: a full panel whose 128 diagonal pivots are
+        // nonzero (the rows the first-nonzero rule picks) factors without the
+        // column-by-column search
+        if (w == kNb && r + kNb <= m) {
+            const size_t dsmem = (size_t)kNb * kNb * 4;
+            auto dk = p < (1u << 16) ? diag_lu_kernel<true> : diag_lu_kernel<false>;
+            FM_CUDA_TRY(cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+            dk<<<1, kDiagThreads, dsmem, s>>>(Am.base, Am.log2_T, r, c0, p, mu, dinv, d_flag);
+            FM_CUDA_TRY(cudaGetLastError());
+            int flag = 1;
+            FM_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (flag == 0) {
+                ++fast_panels;
+                for (int t = 0; t < kNb; ++t) pivot_pos.push_back((int)(c0 + t));
+                FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)ismem));
+                tri_inv2_kernel<<<2, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv);
+                FM_CUDA_TRY(cudaGetLastError());
+                const fm_matrix Xm{xs, 0, 7}, Ym{ys, 0, 7};
+                if (r + kNb < m) {
+                    // L21 <- A21 U11^-1, over A21 itself (its planes are split before it is written)
+                    const fm_sub A21{Am, r + kNb, c0, m - r - kNb, kNb};
+                    FmLimbPlan lq;
+                    FM_TRY(fm_limb_plan(m - r - kNb, kNb, kNb, p, nullptr, &lq));
+                    void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
+                    if (!lws) return FM_ENOMEM;
+                    FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
+                }
+                FM_TRY(update_right(r, kNb, Xm));
+                r += kNb;
+                continue;
+            }
+        }
+        ++searched_panels;
         std::vector<int> slots(kNb, INT_MAX);
         FM_CUDA_TRY(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int) * kNb, cudaMemcpyHostToDevice, s));
         // panel rows resident in shared memory when a CTA's share fits
@@ -763,32 +999,12 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
                 FM_CUDA_TRY(cudaGetLastError());
             }
-            const int64_t cl = c0 + w;
-            if (cl < n) {
-                const int64_t cols = n - cl;
-                // U12 <- L11^-1 A12 as a product (Sec. 2: S_A = S_B * S_C): X = L11^-1
-                // in one CTA, then the limb product into A12 itself (it multiplies
-                // limb planes split from A12 before A12 is written)
-                uint32_t* xs = static_cast<uint32_t*>(fm_workspace(4, (size_t)kNb * kNb * 4));
-                if (!xs) return FM_ENOMEM;
-                const size_t ismem = ((size_t)2 * kNb * kNb + 3 * 32 * 32) * 4;
+            if (c0 + w < n) {
                 FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)ismem));
                 tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
                 FM_CUDA_TRY(cudaGetLastError());
-                const fm_matrix Xm{xs, 0, 7};
-                const fm_sub A12{Am, r, cl, k, cols};
-                FmLimbPlan lq;
-                FM_TRY(fm_limb_plan(k, cols, k, p, nullptr, &lq));
-                void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
-                if (!lws) return FM_ENOMEM;
-                FM_TRY(fm_limb_run(lq, A12, fm_sub{Xm, 0, 0, k, k}, A12, p, FM_OP_SET, lws, status, s));
-                if (r + k < m) {
-                    const fm_sub C{Am, r + k, cl, m - r - k, cols};
-                    const fm_sub L21{Am, r + k, c0, m - r - k, k};
-                    const fm_sub U12{Am, r, cl, k, cols};
-                    FM_TRY(fm_gemm_modp(C, L21, U12, p, FM_OP_SUB, FM_ALGO_AUTO, nullptr, stream));
-                }
+                FM_TRY(update_right(r, k, fm_matrix{xs, 0, 7}));
             }
         }
         r += k;
@@ -816,7 +1032,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     }
     FM_CUDA_TRY(cudaStreamSynchronize(s));
     *rank = r;
-    fm_trace("pluq m=%lld n=%lld p=%u rank=%lld panels of %d columns", (long long)m, (long long)n, p,
-             (long long)r, kNb);
+    fm_trace("pluq m=%lld n=%lld p=%u rank=%lld panels of %d columns: %d diagonal-block, %d searched, %d zero",
+             (long long)m, (long long)n, p, (long long)r, kNb, fast_panels, searched_panels, zero_panels);
     return FM_OK;
 }

@@ -114,3 +114,53 @@ def test_config5_tu_16384x12288_rank_10000(env, orc):
         lhs = orc.matvec_modp(PAQ, x, p)
         rhs = orc.matvec_modp(Lfac.astype(np.uint32), orc.matvec_modp(Ufac.astype(np.uint32), x, p), p)
         assert np.array_equal(lhs, rhs)
+
+
+def _trace_pluq(env, A, p, lt, tmp_path):
+    import os
+    log = tmp_path / "pluq_trace.txt"
+    os.environ["FM_TRACE"] = str(log)
+    try:
+        out = run_pluq(env, A, p, lt)
+    finally:
+        del os.environ["FM_TRACE"]
+    line = [x for x in log.read_text().splitlines() if "pluq m=" in x][-1]
+    fast = int(line.split("columns: ")[1].split(" diagonal-block")[0])
+    searched = int(line.split("diagonal-block, ")[1].split(" searched")[0])
+    zero = int(line.split("searched, ")[1].split(" zero")[0])
+    return out, fast, searched, zero
+
+
+@pytest.mark.parametrize("case", ["dense", "zero_first_pivot", "zero_mid_pivot", "tiny_field", "low_rank"])
+def test_pluq_diagonal_block_and_search_paths(env, orc, tmp_path, case):
+    # A full panel whose 128 diagonal pivots are nonzero factors by the
+    # diagonal-block path (one-CTA LU of the 128 x 128 block, L21 = A21 U11^-1);
+    # a zero pivot on the diagonal -- at its first column, in the middle of the
+    # block (row 70 of the leading 71 columns repeats row 3 there), or often in
+    # GF(3) -- sends the panel to the column-by-column search; a panel with no
+    # nonzero left (rank 200 of 384 columns: the third panel) is skipped. All
+    # give a valid P A Q = L U with the oracle's rank.
+    p, lt, m, n = P16, 6, 400, 384
+    A = fm_inputs.uniform_residues(11, (m, n), p)
+    if case == "zero_first_pivot":
+        A[0, 0] = 0
+    elif case == "zero_mid_pivot":
+        A[70, :71] = A[3, :71]
+    elif case == "tiny_field":
+        p = 3
+        A = A % 3
+    elif case == "low_rank":  # rank 200: the last panel holds no nonzero once 200 pivots are out
+        X, Y = low_rank(12, m, n, 200, p)
+        A = orc.gemm_modp(None, X, Y, p, 0)
+    (r, F, rp, cp), fast, searched, zero = _trace_pluq(env, A, p, lt, tmp_path)
+    _, _, _, _, r_oracle = orc.pluq(A, p)
+    assert r == r_oracle
+    check_factors(orc, A, p, r, F, rp, cp)
+    if case == "dense":
+        assert fast == 3 and searched == 0 and zero == 0
+    elif case in ("zero_first_pivot", "zero_mid_pivot"):
+        assert searched >= 1 and fast >= 1
+    elif case == "low_rank":
+        assert (fast, searched, zero) == (1, 1, 1)
+    else:
+        assert searched >= 1
