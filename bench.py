@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--no-gf2", action="store_true", help="skip the GF(2) measurements")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the small, Schur-update and 31-bit workloads")
-    ap.add_argument("--case", default=None, choices=["gemm", "gemm_p31", "permute", "to_morton_permuted", "tu"],
+    ap.add_argument("--case", default=None,
+                    choices=["gemm", "gemm_p31", "permute", "to_morton_permuted", "tu", "batch"],
                     help="profiling aid: run one kernel's call --steps times at --n (T' = --T) after "
                          "--warmup calls, print nothing else, exit")
     ap.add_argument("--T", type=int, default=128, help="T' of the --case matrices")
@@ -1113,6 +1114,37 @@ def run_case(args):
     if args.case == "tu":  # the TU workload (16384 x 12288, rank 10000), one factorization
         r = run_tu(fm, torch, dev, torch.cuda.current_stream())
         assert r["rank"] == r["rank_expected"], r
+        return
+    if args.case == "batch":  # the 4096-call workload at T' = --T, limb plan with planes
+        lt = args.T.bit_length() - 1
+        big, hi = 16384, 512
+        rows, cells = fm_inputs.batch_workload(5, 4096, 32, hi, big)
+        nC = cells * hi
+        mats = []
+        for q, side in ((1, big), (2, big)):
+            x = torch.from_numpy(fm_inputs.uniform_residues(5, (side, side), P, q).view(np.int32)).to(dev)
+            t = torch.empty(side * side, dtype=torch.int32, device=dev)
+            m = fm.matrix(t, (side >> lt).bit_length() - 1, lt)
+            fm.fm_layout_to_morton(x, side, side, side, m)
+            mats.append((t, m))
+            del x
+        tC = torch.zeros(nC * nC, dtype=torch.int32, device=dev)
+        mC = fm.matrix(tC, (nC >> lt).bit_length() - 1, lt)
+        calls = []
+        for c in range(len(rows)):
+            M, N, K, rC, cC, rA, cA, rB, cB = (int(x) for x in rows[c])
+            call = fm.fm_gemm_call()
+            call.C, call.A, call.B = fm.sub(mC, rC, cC, M, N), fm.sub(mats[0][1], rA, cA, M, K), \
+                fm.sub(mats[1][1], rB, cB, K, N)
+            call.op = fm.FM_OP_SUB
+            calls.append(call)
+        plan = fm.fm_plan_create(calls, P, fm.FM_ALGO_LIMB_TC)
+        for _ in range(args.warmup + args.steps):
+            plan.run()
+        torch.cuda.synchronize()
+        st = fm.fm_get_last_device_status()
+        assert st == 0, f"device status {st}"
+        plan.close()
         return
     n, lt = args.n, args.T.bit_length() - 1
     lg = (n >> lt).bit_length() - 1
