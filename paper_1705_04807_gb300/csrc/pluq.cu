@@ -793,25 +793,78 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     // (written into A12 itself: the limb product splits A12 into planes before
     // A12 is written), then A22 <- A22 - L21 U12 by fm_gemm_modp on three
     // disjoint sub-matrices of A.
-    int64_t c0 = 0;
+    // Two-level blocking: up to kOuter consecutive panels form an outer block.
+    // Inside it each panel's update reaches only the block's own columns; the
+    // columns behind the block receive the whole block's update at once, as
+    // U12 <- L11^-1 A12 by block forward substitution over its panels and one
+    // product A22 <- A22 - L21 U12 with K = the block's pivots (up to 512),
+    // which has a quarter of the epilogue work of four K = 128 updates. A block
+    // ends after a panel with fewer than 128 pivots (its pivot columns stay
+    // contiguous: a panel moves its pivot columns in front of its skipped ones).
+    constexpr int kOuter = 4;
+    int64_t c0 = 0, c_out = 0, r_out = 0;
+    int nbk = 0;           // panels in the open outer block
+    int bk[kOuter] = {0};  // pivots of each
     int fast_panels = 0, searched_panels = 0, zero_panels = 0;
-    auto update_right = [&](int64_t r_, int k_, fm_matrix Xm) -> int {
-        const int64_t cl = c0 + std::min<int64_t>(kNb, n - c0);
-        if (cl >= n || k_ == 0) return FM_OK;
-        const int64_t cols = n - cl;
-        const fm_sub A12{Am, r_, cl, k_, cols};
-        FmLimbPlan lq;
-        FM_TRY(fm_limb_plan(k_, cols, k_, p, nullptr, &lq));
-        void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
-        if (!lws) return FM_ENOMEM;
-        FM_TRY(fm_limb_run(lq, A12, fm_sub{Xm, 0, 0, k_, k_}, A12, p, FM_OP_SET, lws, status, s));
-        if (r_ + k_ < m) {
-            const fm_sub C{Am, r_ + k_, cl, m - r_ - k_, cols};
-            const fm_sub L21{Am, r_ + k_, c0, m - r_ - k_, k_};
-            const fm_sub U12{Am, r_, cl, k_, cols};
-            FM_TRY(fm_gemm_modp(C, L21, U12, p, FM_OP_SUB, FM_ALGO_AUTO, nullptr, stream));
+    // C op A * B with every operand a sub-matrix of A (the limb product writes
+    // C over the B operand when they are the same part: it splits B first)
+    auto product = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
+        if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
+        if (op == FM_OP_SET) {
+            FmLimbPlan lq;
+            FM_TRY(fm_limb_plan(C.rows, C.cols, Aop.cols, p, nullptr, &lq));
+            void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
+            if (!lws) return FM_ENOMEM;
+            return fm_limb_run(lq, C, Aop, Bop, p, FM_OP_SET, lws, status, s);
         }
-        return FM_OK;
+        return fm_gemm_modp(C, Aop, Bop, p, op, FM_ALGO_AUTO, nullptr, stream);
+    };
+    // After a panel with k pivots in rows [r_, r_ + k) and columns [c0, c0 + k):
+    // U12 <- L11^-1 A12 (X = L11^-1) and A22 <- A22 - L21 U12 on columns
+    // [c_from, c_to).
+    auto update_cols = [&](int64_t r_, int k_, fm_matrix Xm, int64_t c_from, int64_t c_to) -> int {
+        if (c_from >= c_to || k_ == 0) return FM_OK;
+        const int64_t cols = c_to - c_from;
+        const fm_sub A12{Am, r_, c_from, k_, cols};
+        FM_TRY(product(A12, fm_sub{Xm, 0, 0, k_, k_}, A12, FM_OP_SET));
+        return product(fm_sub{Am, r_ + k_, c_from, m - r_ - k_, cols}, fm_sub{Am, r_ + k_, c0, m - r_ - k_, k_},
+                       A12, FM_OP_SUB);
+    };
+    uint32_t* xs_base = nullptr;  // X of each panel of the open block (set per panel below)
+    // Closes the open block after its last panel (ending at column c_end, rows
+    // up to r_now). Columns [c_end, c_lim) -- the block's own columns behind
+    // that panel, when the block ended early -- already hold the updates of
+    // the block's earlier panels and take only the last panel's; columns
+    // [c_lim, n) take the whole block's.
+    auto finish_outer = [&](int64_t c_end, int64_t c_lim, int64_t r_now) -> int {
+        const int n_bk = nbk;
+        nbk = 0;
+        const int64_t k_out = r_now - r_out;
+        if (k_out == 0) return FM_OK;
+        const int k_last = bk[n_bk - 1];
+        if (n_bk == 1) {  // a block of one panel: no column has any of its update yet
+            const fm_matrix X0{xs_base, 0, 7};
+            return update_cols(r_out, k_last, X0, c_end, n);
+        }
+        if (c_end < c_lim && k_last > 0) {
+            const fm_matrix Xl{xs_base + (size_t)(n_bk - 1) * kNb * kNb, 0, 7};
+            FM_TRY(update_cols(r_now - k_last, k_last, Xl, c_end, c_lim));
+        }
+        c_end = std::max(c_end, c_lim);
+        if (c_end >= n) return FM_OK;
+        const int64_t cols = n - c_end;
+        for (int i = 0; i < n_bk; ++i) {
+            if (bk[i] == 0) continue;
+            const int64_t ri = r_out + (int64_t)kNb * i;
+            const fm_sub Ai{Am, ri, c_end, bk[i], cols};
+            if (i > 0)
+                FM_TRY(product(Ai, fm_sub{Am, ri, c_out, bk[i], (int64_t)kNb * i},
+                               fm_sub{Am, r_out, c_end, (int64_t)kNb * i, cols}, FM_OP_SUB));
+            const fm_matrix Xi{xs_base + (size_t)i * kNb * kNb, 0, 7};
+            FM_TRY(product(Ai, fm_sub{Xi, 0, 0, bk[i], bk[i]}, Ai, FM_OP_SET));
+        }
+        return product(fm_sub{Am, r_now, c_end, m - r_now, cols}, fm_sub{Am, r_now, c_out, m - r_now, k_out},
+                       fm_sub{Am, r_out, c_end, k_out, cols}, FM_OP_SUB);
     };
     std::vector<int> colid((size_t)n);  // original column at each storage position
     for (int64_t j = 0; j < n; ++j) colid[(size_t)j] = (int)j;
@@ -823,12 +876,27 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
             continue;
         }
-        // X = L11^-1, Y = U11^-1 (the fast path), 1 / U11(t, t), and its flags
-        uint32_t* xs = static_cast<uint32_t*>(fm_workspace(4, (size_t)(2 * kNb * kNb + kNb + 4) * 4));
-        if (!xs) return FM_ENOMEM;
-        uint32_t* ys = xs + kNb * kNb;
+        // X = L11^-1 of each panel of the open block, Y = U11^-1 (the fast
+        // path), 1 / U11(t, t), and the flags
+        xs_base = static_cast<uint32_t*>(fm_workspace(4, (size_t)((kOuter + 1) * kNb * kNb + kNb + 4) * 4));
+        if (!xs_base) return FM_ENOMEM;
+        if (nbk == 0) {
+            c_out = c0;
+            r_out = r;
+        }
+        uint32_t* xs = xs_base + (size_t)nbk * kNb * kNb;
+        uint32_t* ys = xs_base + (size_t)kOuter * kNb * kNb;
         uint32_t* dinv = ys + kNb * kNb;
         int* d_flag = reinterpret_cast<int*>(dinv + kNb);
+        const int64_t c_lim = std::min<int64_t>(c_out + (int64_t)kOuter * kNb, n);
+        // after a panel with k pivots: the rest of the block's columns now, or,
+        // when the panel ends the block, everything behind it
+        auto after_panel = [&](int k, fm_matrix Xm) -> int {
+            bk[nbk++] = k;
+            const bool ends = k < kNb || nbk == kOuter || c0 + w >= n || r + k >= m;
+            if (!ends) return update_cols(r, k, Xm, c0 + w, c_lim);
+            return finish_outer(c0 + w, c_lim, r + k);
+        };
         // a panel without a nonzero in rows [r, m) has no pivot: skip it
         {
             FM_CUDA_TRY(cudaMemsetAsync(d_flag + 1, 0, sizeof(int), s));
@@ -842,6 +910,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             if (!nz) {
                 ++zero_panels;
                 for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
+                FM_TRY(after_panel(0, fm_matrix{xs, 0, 7}));
                 continue;
             }
         }
@@ -875,7 +944,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                     if (!lws) return FM_ENOMEM;
                     FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
                 }
-                FM_TRY(update_right(r, kNb, Xm));
+                FM_TRY(after_panel(kNb, Xm));
                 r += kNb;
                 continue;
             }
@@ -999,14 +1068,12 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
                 FM_CUDA_TRY(cudaGetLastError());
             }
-            if (c0 + w < n) {
-                FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)ismem));
-                tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
-                FM_CUDA_TRY(cudaGetLastError());
-                FM_TRY(update_right(r, k, fm_matrix{xs, 0, 7}));
-            }
+            FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ismem));
+            tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
+            FM_CUDA_TRY(cudaGetLastError());
         }
+        FM_TRY(after_panel(k, fm_matrix{xs, 0, 7}));
         r += k;
     }
     // move every skipped column behind all pivot columns

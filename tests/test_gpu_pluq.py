@@ -164,3 +164,19 @@ def test_pluq_diagonal_block_and_search_paths(env, orc, tmp_path, case):
         assert (fast, searched, zero) == (1, 1, 1)
     else:
         assert searched >= 1
+
+
+@pytest.mark.parametrize("m,n,rk,lt,p", [(700, 900, 700, 6, P16), (1100, 700, 700, 7, P16), (900, 1300, 450, 6, P16),
+                                         (600, 640, 600, 5, 2147483647), (700, 900, 700, 6, 3)])
+def test_pluq_outer_blocks(env, orc, m, n, rk, lt, p):
+    # Panels grouped in blocks of four (columns behind a block updated once
+    # with K = its pivots; inside the block panel by panel): full-rank wide and
+    # tall matrices (blocks of four full panels, a last block of fewer),
+    # rank 450 (a block that ends early on a panel with 66 pivots), p = 2^31 - 1,
+    # and GF(3) (searched panels, blocks ending on short panels)
+    X, Y = low_rank(m * 3 + n + rk, m, n, rk, p)
+    A = orc.gemm_modp(None, X, Y, p, 0)
+    r, F, rp, cp = run_pluq(env, A, p, lt)
+    _, _, _, _, r_oracle = orc.pluq(A, p)
+    assert r == r_oracle
+    check_factors(orc, A, p, r, F, rp, cp)
