@@ -1111,8 +1111,9 @@ def run_case(args):
     fmbuild.build()
     fm.lib()
     dev = torch.device("cuda", 0)
-    if args.case == "tu":  # the TU workload (16384 x 12288, rank 10000), one factorization
-        r = run_tu(fm, torch, dev, torch.cuda.current_stream())
+    if args.case == "tu":  # the TU workload (16384 x 12288, rank 10000; --n = 12288), one factorization
+        n = args.n if args.n != N_DEFAULT else 12288
+        r = run_tu(fm, torch, dev, torch.cuda.current_stream(), m=(n * 4) // 3, n=n, k=(n * 625) // 768)
         assert r["rank"] == r["rank_expected"], r
         return
     if args.case == "batch":  # the 4096-call workload at T' = --T, limb plan with planes

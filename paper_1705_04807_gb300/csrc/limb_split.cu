@@ -191,10 +191,15 @@ __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int
             if (gn + 4 <= N && (gj & mask) + 4 <= mask + 1 && (a & 3) == 0) {
                 v[it] = __ldg(reinterpret_cast<const uint4*>(B + a));
             } else {
+                // misaligned or ragged: entries along the tile row follow one
+                // another, a new encode only where the run crosses into the next tile
                 uint32_t t[4];
+                uint64_t aq = a;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    t[q] = gn + q < N ? __ldg(B + fm_encode(gi, gj + q, lt)) : 0u;
+                for (int q = 0; q < 4; ++q) {
+                    if (q > 0) aq = ((gj + q) & mask) == 0 ? fm_encode(gi, gj + q, lt) : aq + 1;
+                    t[q] = gn + q < N ? __ldg(B + aq) : 0u;
+                }
                 v[it] = make_uint4(t[0], t[1], t[2], t[3]);
             }
         }

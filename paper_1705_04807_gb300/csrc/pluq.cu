@@ -549,9 +549,17 @@ __device__ __forceinline__ uint64_t mac_p(uint64_t acc, uint32_t a, uint32_t b, 
     return acc + (p < 65536u ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
 }
 
-__device__ __forceinline__ uint32_t neg_mod(uint64_t acc, uint32_t p)
+// x mod p for x < 2^40 (sums of at most 256 products below 2^32): Barrett with
+// mu = floor((2^64 - 1) / p) leaves the remainder below 2p
+__device__ __forceinline__ uint32_t red64(uint64_t x, uint32_t p, uint64_t mu)
 {
-    const uint32_t r = (uint32_t)(acc % p);
+    const uint64_t r = x - __umul64hi(x, mu) * p;
+    return (uint32_t)(r >= p ? r - p : r);
+}
+
+__device__ __forceinline__ uint32_t neg_mod(uint64_t acc, uint32_t p, uint64_t mu)
+{
+    const uint32_t r = red64(acc, p, mu);
     return r == 0 ? 0u : p - r;
 }
 
@@ -592,7 +600,7 @@ __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t 
             if (lane < r) {
                 uint64_t acc = 0;
                 for (int t = j; t < i; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + j], p, mu);
-                Xs[i * K + j] = neg_mod(acc, p);
+                Xs[i * K + j] = neg_mod(acc, p, mu);
             }
             __syncwarp();
         }
@@ -604,14 +612,14 @@ __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t 
         for (int bj = 0; bj < bi; ++bj) {
             uint64_t acc = 0;
             for (int t = 32 * bj; t < 32 * bi; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + 32 * bj + lane], p, mu);
-            T[(bj * 32 + warp) * 32 + lane] = (uint32_t)(acc % p);
+            T[(bj * 32 + warp) * 32 + lane] = red64(acc, p, mu);
         }
         __syncthreads();
         for (int bj = 0; bj < bi; ++bj) {
             uint64_t acc = 0;
             for (int s2 = 0; s2 < 32; ++s2)
                 acc = mac_p(acc, Xs[i * K + 32 * bi + s2], T[(bj * 32 + s2) * 32 + lane], p, mu);
-            Xs[i * K + 32 * bj + lane] = neg_mod(acc, p);
+            Xs[i * K + 32 * bj + lane] = neg_mod(acc, p, mu);
         }
         __syncthreads();
     }
@@ -676,65 +684,162 @@ __device__ __forceinline__ uint32_t mulmod16(uint32_t a, uint32_t b, uint32_t p,
     return r >= p ? r - p : r;
 }
 
+// a * b mod p, products of residues below 2^16 in 32 bits, else 64-bit Barrett
+template <bool SMALL>
+__device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32, uint64_t mu)
+{
+    return SMALL ? mulmod16(a, b, p, mu32) : mulmod(a, b, p, mu);
+}
+
+// sum of a * b over 32 terms, reduced once: raw products below 2^32 when
+// p < 2^16, reduced products otherwise (the sum stays below 2^37 either way)
+template <bool SMALL>
+__device__ __forceinline__ uint64_t mac(uint64_t acc, uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
+{
+    return acc + (SMALL ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
+}
+
+// Blocked in 32-wide block columns o = 0, 32, 64, 96 (the same L and U as the
+// unblocked elimination without row exchanges, which are unique):
+//   1. the 32 x 32 diagonal block by the division-free steps above, one entry
+//      per thread per step (rows on warps, columns on lanes), then its 32
+//      inverses at once; L_kk and U_kk written back;
+//   2. L_kk^-1 (warp 0) and U_kk^-1 (warp 1, as (V^T)^-1 transposed with
+//      U_kk = diag(U_kk) V), row by row;
+//   3. the panel below, L_ik = A_ik U_kk^-1, and the row to the right,
+//      U_kj = L_kk^-1 A_kj, as 32-term dot products reduced once;
+//   4. the trailing update A_ij -= L_ik U_kj, likewise.
 template <bool SMALL>
 __global__ void __launch_bounds__(kDiagThreads) diag_lu_kernel(uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                                uint32_t p, uint64_t mu, uint32_t* dinv, int* flag)
 {
-    const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
-    extern __shared__ uint32_t D[];  // [kNb][kNb]
-    __shared__ uint32_t cpiv[kNb], cinv[kNb], sig[kNb], sinv[kNb];
+    constexpr int K = kNb, B = 32;
+    extern __shared__ uint32_t sm[];
+    uint32_t* D = sm;                 // [K][K]
+    uint32_t* Li = D + K * K;         // [B][B]  L_kk^-1
+    uint32_t* Ui = Li + B * B;        // [B][B]  U_kk^-1
+    uint32_t* Z = Ui + B * B;         // [B][B]  (V^T)^-1
+    uint32_t* TL = Z + B * B;         // [K - B][B]  new panel below
+    uint32_t* TU = TL + (K - B) * B;  // [B][K - B]  new row to the right
+    __shared__ uint32_t cpiv[B], cinv[B], sinv[B], sig[B], dv[K];
     __shared__ int s_zero;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < kNb * kNb; e += kDiagThreads)
-        D[e] = A[fm_encode((uint64_t)(r0 + e / kNb), (uint64_t)(c0 + e % kNb), lt)];
-    if (threadIdx.x == 0) s_zero = 0;
-    for (int t = 0; t < kNb; ++t) {
-        __syncthreads();
-        const uint32_t ct = D[t * kNb + t];
-        if (ct == 0) {
-            if (threadIdx.x == 0) s_zero = 1;
-            break;
+    const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < K * K; e += kDiagThreads)
+        D[e] = A[fm_encode((uint64_t)(r0 + e / K), (uint64_t)(c0 + e % K), lt)];
+    if (tid == 0) s_zero = 0;
+    for (int o = 0; o < K; o += B) {
+        // 1. division-free LU of the diagonal block
+        for (int t = 0; t < B; ++t) {
+            __syncthreads();
+            const uint32_t c = D[(o + t) * K + o + t];
+            if (c == 0) {
+                if (tid == 0) s_zero = 1;
+                break;
+            }
+            if (tid == 0) cpiv[t] = c;
+            if (warp < B - 1 - t && lane < B - 1 - t) {
+                const int i = o + t + 1 + warp, j = o + t + 1 + lane;
+                D[i * K + j] = submod(mulm<SMALL>(c, D[i * K + j], p, mu32, mu),
+                                      mulm<SMALL>(D[i * K + o + t], D[(o + t) * K + j], p, mu32, mu), p);
+            }
         }
-        if (threadIdx.x == 0) cpiv[t] = ct;
-        for (int i = t + 1 + ty; i < kNb; i += 32) {
-            const uint32_t sit = D[i * kNb + t];
-            for (int j = t + 1 + tx; j < kNb; j += 32) {
-                const uint32_t x = D[i * kNb + j], y = D[t * kNb + j];
-                D[i * kNb + j] = SMALL ? submod(mulmod16(ct, x, p, mu32), mulmod16(sit, y, p, mu32), p)
-                                       : submod(mulmod(ct, x, p, mu), mulmod(sit, y, p, mu), p);
+        __syncthreads();
+        if (s_zero) {
+            if (tid == 0) *flag = 1;
+            return;
+        }
+        if (tid == 0) {
+            uint32_t g = 1 % p;
+            for (int t = 0; t < B; ++t) {
+                sig[t] = g;
+                g = mulm<SMALL>(g, cpiv[t], p, mu32, mu);
+            }
+        }
+        __syncthreads();
+        if (warp == 0)
+            cinv[lane] = powmod_dev(cpiv[lane], p - 2, p, mu);
+        else if (warp == 1)
+            sinv[lane] = powmod_dev(sig[lane], p - 2, p, mu);
+        __syncthreads();
+        {  // normalise: l_it = S_i[t] / c_t below the diagonal, U row t = S_t / sigma_t
+            const int i = warp, j = lane;
+            uint32_t& v = D[(o + i) * K + o + j];
+            v = i > j ? mulmod(v, cinv[j], p, mu) : mulmod(v, sinv[i], p, mu);
+            if (i == 0) dv[o + j] = mulmod(sig[j], cinv[j], p, mu);  // 1 / u_jj
+        }
+        __syncthreads();
+        // 2. L_kk^-1 and (V^T)^-1 with V^T(i, t) = U(t, i) / u_tt, both unit
+        //    lower: with M = -(X - I) strictly lower, M^32 = 0 and
+        //    X^-1 = (I + M)(I + M^2)(I + M^4)(I + M^8)(I + M^16), built by four
+        //    squarings of M and four products, every entry on its own thread
+        //    (warp = row, lane = column); TL and TU are free until step 3.
+        for (int which = 0; which < 2; ++which) {
+            uint32_t* X = which == 0 ? Li : Z;  // the inverse
+            uint32_t* Q = TL;                   // M^(2^s)
+            uint32_t* T = TL + B * B;           // product scratch
+            {
+                const int i = warp, j = lane;
+                uint32_t m = 0;
+                if (j < i) {
+                    const uint32_t x = which == 0 ? D[(o + i) * K + o + j]
+                                                  : mulm<SMALL>(D[(o + j) * K + o + i], dv[o + j], p, mu32, mu);
+                    m = x == 0 ? 0u : p - x;
+                }
+                Q[i * B + j] = m;
+                X[i * B + j] = i == j ? 1u : m;
+            }
+            for (int sq = 1; sq < 5; ++sq) {
+                __syncthreads();
+                const int i = warp, j = lane;
+                uint64_t acc = 0;
+                for (int t = j; t < i; ++t) acc = mac<SMALL>(acc, Q[i * B + t], Q[t * B + j], p, mu);
+                T[i * B + j] = red64(acc, p, mu);  // M^(2^sq)
+                __syncthreads();
+                Q[i * B + j] = T[i * B + j];
+                __syncthreads();
+                acc = 0;
+                for (int t = j; t <= i; ++t) acc = mac<SMALL>(acc, X[i * B + t], Q[t * B + j], p, mu);
+                T[i * B + j] = red64(acc, p, mu);  // X M^(2^sq)
+                __syncthreads();
+                const uint32_t xv = X[i * B + j] + T[i * B + j];
+                X[i * B + j] = xv >= p ? xv - p : xv;
+            }
+            __syncthreads();
+        }
+        Ui[warp * B + lane] = warp <= lane ? mulmod(Z[lane * B + warp], dv[o + lane], p, mu) : 0u;
+        __syncthreads();
+        if (o + B >= K) break;
+        // 3. the panel below and the row to the right
+        for (int i = o + B + warp; i < K; i += 32) {
+            uint64_t acc = 0;
+            for (int t = 0; t <= lane; ++t) acc = mac<SMALL>(acc, D[i * K + o + t], Ui[t * B + lane], p, mu);
+            TL[(i - o - B) * B + lane] = red64(acc, p, mu);
+        }
+        for (int j = o + B + lane; j < K; j += 32) {
+            uint64_t acc = 0;
+            for (int t = 0; t <= warp; ++t) acc = mac<SMALL>(acc, Li[warp * B + t], D[(o + t) * K + j], p, mu);
+            TU[warp * (K - B) + (j - o - B)] = red64(acc, p, mu);
+        }
+        __syncthreads();
+        for (int i = o + B + warp; i < K; i += 32) D[i * K + o + lane] = TL[(i - o - B) * B + lane];
+        for (int j = o + B + lane; j < K; j += 32) D[(o + warp) * K + j] = TU[warp * (K - B) + (j - o - B)];
+        __syncthreads();
+        // 4. trailing update
+        for (int i = o + B + warp; i < K; i += 32) {
+            for (int j = o + B + lane; j < K; j += 32) {
+                uint64_t acc = 0;
+#pragma unroll 8
+                for (int t = 0; t < B; ++t) acc = mac<SMALL>(acc, D[i * K + o + t], D[(o + t) * K + j], p, mu);
+                D[i * K + j] = submod(D[i * K + j], red64(acc, p, mu), p);
             }
         }
     }
     __syncthreads();
-    if (s_zero) {
-        if (threadIdx.x == 0) *flag = 1;
-        return;
-    }
-    // sigma_t = c_0 ... c_{t-1}; the inverses of every c_t and sigma_t at once
-    if (threadIdx.x == 0) {
-        uint32_t sg = 1 % p;
-        for (int t = 0; t < kNb; ++t) {
-            sig[t] = sg;
-            sg = mulmod(sg, cpiv[t], p, mu);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < kNb) {
-        cinv[threadIdx.x] = powmod_dev(cpiv[threadIdx.x], p - 2, p, mu);
-    } else if (threadIdx.x < 2 * kNb) {
-        const int t = threadIdx.x - kNb;
-        sinv[t] = powmod_dev(sig[t], p - 2, p, mu);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kNb * kNb; e += kDiagThreads) {
-        const int i = e / kNb, j = e % kNb;
-        const uint32_t v = D[e];
-        const uint32_t out = j < i ? mulmod(v, cinv[j], p, mu) : mulmod(v, sinv[i], p, mu);
-        A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + j), lt)] = out;
-    }
-    // 1 / U11(t, t) = sigma_t / c_t
-    if (threadIdx.x < kNb) dinv[threadIdx.x] = mulmod(sig[threadIdx.x], cinv[threadIdx.x], p, mu);
-    if (threadIdx.x == 0) *flag = 0;
+    for (int e = tid; e < K * K; e += kDiagThreads)
+        A[fm_encode((uint64_t)(r0 + e / K), (uint64_t)(c0 + e % K), lt)] = D[e];
+    if (tid < K) dinv[tid] = dv[tid];
+    if (tid == 0) *flag = 0;
 }
 
 }  // namespace
@@ -919,7 +1024,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         // nonzero (the rows the first-nonzero rule picks) factors without the
         // column-by-column search
         if (w == kNb && r + kNb <= m) {
-            const size_t dsmem = (size_t)kNb * kNb * 4;
+            const size_t dsmem = ((size_t)kNb * kNb + 3 * 32 * 32 + 2 * (kNb - 32) * 32) * 4;
             auto dk = p < (1u << 16) ? diag_lu_kernel<true> : diag_lu_kernel<false>;
             FM_CUDA_TRY(cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
             dk<<<1, kDiagThreads, dsmem, s>>>(Am.base, Am.log2_T, r, c0, p, mu, dinv, d_flag);
