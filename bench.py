@@ -68,6 +68,7 @@ def parse():
                     help="profiling aid: run one kernel's call --steps times at --n (T' = --T) after "
                          "--warmup calls, print nothing else, exit")
     ap.add_argument("--T", type=int, default=128, help="T' of the --case matrices")
+    ap.add_argument("--calls", type=int, default=4096, help="calls of the --case batch workload")
     return ap.parse_args()
 
 
@@ -509,10 +510,25 @@ def run_configs(fm, torch, dev, stream, peaks, seed=21):
     us = timed(lambda: small(fm.FM_ALGO_PLAIN), 200) * 1e3
     one = fm.sub(mA, 0, 0, 1, 1)
     floor_us = timed(lambda: fm.fm_validate_residues(one, p, s), 200) * 1e3
+    # where the time of a call goes: host submission (200 calls queued without
+    # waiting), and the device alone (the call replayed from a CUDA graph)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        small(fm.FM_ALGO_PLAIN)
+    host_us = (time.perf_counter() - t0) / 200 * 1e6
+    torch.cuda.synchronize()
+    gs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        fm.fm_gemm_modp(sub[0], sub[1], sub[2], p, fm.FM_OP_SET, fm.FM_ALGO_PLAIN, None, gs.cuda_stream)
+    graph_us = timed(lambda: graph.replay(), 200) * 1e3
+    del graph
     torch.cuda.synchronize()
     same = same_as(tC, tC.clone(), lambda: small(fm.FM_ALGO_LIMB_TC))
     out["small"] = {"workload": "C = A*B mod 65521, M=N=K=256, Morton-hybrid T'=32, plain form",
                     "us_per_call": us, "launch_floor_us": floor_us, "floor_frac": floor_us / us,
+                    "host_submit_us_per_call": host_us, "graph_replay_us_per_call": graph_us,
                     "value": 2.0 * n ** 3 / (us / 1e6) / 1e9, "unit": "Gop/s", "bit_identical_to_limb": same}
     del tA, tB, tC
 
@@ -1116,10 +1132,10 @@ def run_case(args):
         r = run_tu(fm, torch, dev, torch.cuda.current_stream(), m=(n * 4) // 3, n=n, k=(n * 625) // 768)
         assert r["rank"] == r["rank_expected"], r
         return
-    if args.case == "batch":  # the 4096-call workload at T' = --T, limb plan with planes
+    if args.case == "batch":  # the 4096-call workload at T' = --T (--calls fewer), limb plan with planes
         lt = args.T.bit_length() - 1
-        big, hi = 16384, 512
-        rows, cells = fm_inputs.batch_workload(5, 4096, 32, hi, big)
+        big, hi = (16384 if args.calls == 4096 else 8192), 512
+        rows, cells = fm_inputs.batch_workload(5, args.calls, 32, hi, big)
         nC = cells * hi
         mats = []
         for q, side in ((1, big), (2, big)):
