@@ -88,11 +88,13 @@ typedef struct fm_opts {
     int32_t k_chunk;        /* limb form: K elements per exact accumulation chunk  */
     int32_t block_n;        /* limb form: output tile width, 128 or 256            */
     int32_t no_karatsuba;   /* limb form: 1 = four limb products instead of three  */
-    int32_t cta_pair;       /* limb form, block_n 256, p < 2^16: 1 = a CTA pair
-                               (cta_group::2) per 256 x 256 output tile, -1 = one
-                               CTA per 128 x 256 tile, 0 = automatic (pairs for
-                               the fold form when M, N > 256 and K >= 1024;
-                               GF(2): one CTA)                                  */
+    int32_t cta_pair;       /* limb form: 1 = a CTA pair (cta_group::2) per
+                               256 x 256 output tile (fold form, block_n 256) or
+                               per 256 x 128 tile (residue form, block_n 128;
+                               FM_EINVAL with any other block_n), -1 = one CTA per
+                               128 x block_n tile, 0 = automatic (pairs for the
+                               fold form when M, N > 256 and K >= 1024; one CTA
+                               in the residue form and for GF(2))               */
     int32_t fused_batch;    /* limb batches: 1 = ONE launch that splits the
                                operands into limbs on the fly, instead of limb
                                planes of every call in a workspace and three

@@ -126,7 +126,7 @@ extern "C" int fm_autotune(int64_t M, int64_t N, int64_t K, uint32_t p, int32_t 
                 for (int kc : {full, full / 2}) {
                     if (kc < 64 || kc % 64) continue;
                     for (int pair : {-1, 1}) {
-                        if (pair == 1 && bn != 256) continue;
+                        if (pair == 1 && bn != (q.fold ? 256 : 128)) continue;  // pair tile widths
                         limb(bn, kc, 0, pair);
                         if (q.n_planes > q.w) limb(bn, kc, 1, pair);
                     }

@@ -45,12 +45,24 @@ using namespace fm_limb;
 constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 
-__device__ __forceinline__ uint32_t barrett64(uint64_t t, uint32_t p, uint64_t mu)
+// Residue-form fold of one product's sum into the running residue:
+// r + w * s mod p for an int32 sum s, a weight w < p and r in [0, p), p < 2^31,
+// all in 32-bit integer arithmetic. w * |s| mod p by Shoup's method: with
+// ws = floor(w 2^32 / p), q = floor(|s| ws / 2^32) falls short of w |s| / p by
+// less than 2, so w |s| - q p (exact mod 2^32) lies in [0, 2p) and one
+// conditional subtraction leaves y in [0, p). A negative s gives p - y, in
+// [1, p]; r plus that is below 2p and is reduced once more.
+__device__ __forceinline__ uint32_t umin_sub(uint32_t x, uint32_t p)
 {
-    const uint64_t q = __umul64hi(t, mu);
-    uint64_t r = t - q * (uint64_t)p;
-    while (r >= p) r -= p;
-    return (uint32_t)r;
+    return min(x, x - p);  // x - p when x >= p (otherwise x - p wraps above x)
+}
+
+__device__ __forceinline__ uint32_t fold_sum(int32_t s, uint32_t w, uint32_t ws, uint32_t r, uint32_t p)
+{
+    const uint32_t a = (uint32_t)abs(s);  // |s| < 2^31
+    const uint32_t q = __umulhi(a, ws);
+    const uint32_t y = umin_sub(a * w - q * p, p);
+    return umin_sub(r + (s < 0 ? p - y : y), p);
 }
 
 // Per-call part of a limb GEMM: its limb planes, K stages and jobs, and its C
@@ -75,11 +87,10 @@ struct LimbGemmArgs {
     int pa[16], pb[16];  // planes of A and B of product k
     int cs[16];          // 64-wide K stages per chunk of product k
     uint32_t p, mu32;
-    uint64_t mu64;
     uint32_t wt[16];  // weight of product k mod p
+    uint32_t wts[16]; // residue form: floor(wt[k] * 2^32 / p), Shoup's constant for wt[k]
     uint32_t cn[16];  // fold form: cn[k * 4 + k2] = wt[k] * wt[k2]^-1 mod p
     float invp, pf;   // fold form: 1/p and p as float
-    uint64_t offs64;  // residue form: multiple of p >= 2^31 (makes an int32 sum non-negative)
     int* status;
 };
 
@@ -404,15 +415,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                                 fm_tmem_ld32(rbase + cc * 32, v);
                                 fm_tmem_wait_ld();
                             }
-                            const uint32_t wt = args.wt[idx];
+                            const uint32_t wt = args.wt[idx], wts = args.wts[idx];
 #pragma unroll
-                            for (int e = 0; e < 32; ++e) {
-                                const uint64_t x =
-                                    (uint64_t)((int64_t)(int32_t)sv[e] + (int64_t)args.offs64);
-                                const uint32_t xm = barrett64(x, p, args.mu64);
-                                v[e] = barrett64((uint64_t)wt * xm + (r_fresh ? 0u : v[e]), p,
-                                                 args.mu64);
-                            }
+                            for (int e = 0; e < 32; ++e)
+                                v[e] = fold_sum((int32_t)sv[e], wt, wts, r_fresh ? 0u : v[e], p);
                             fm_tmem_st32(rbase + cc * 32, v);
                         } else {
                             fm_tmem_st32(sbase + cc * 32, sv);
@@ -496,24 +502,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// CTA-pair form (fold form only): a cluster of two CTAs computes a 256 x 256
-// output tile with tcgen05.mma.cta_group::2. CTA r of the pair stages A rows
-// [128 r, 128 r + 128) and B rows (n) [128 r, 128 r + 128) of the tile -- 32 KB
-// per 64-wide K stage instead of 48 KB -- and holds D rows [128 r, 128 r + 128)
-// in its tensor memory. The even CTA issues the MMAs; its commits are multicast
-// to both CTAs. Each CTA's bulk copies complete on its own full barrier; a
-// forwarder thread of the odd CTA then arrives on the even CTA's full barrier,
-// and the odd CTA's epilogue warps arrive on the even CTA's accumulator-empty
-// barriers.
-constexpr int kPairStages = 6;
-constexpr uint32_t kPairStageBytes = 2 * kATileBytes;  // A half + B half, 16 KB each
-constexpr size_t kPairSmem = (size_t)kPairStages * kPairStageBytes + 1024;
+// CTA-pair form: a cluster of two CTAs computes a 256 x BN output tile with
+// tcgen05.mma.cta_group::2 (fold form: BN = 256; residue form: BN = 128, whose
+// TMEM per CTA then holds the two accumulators, R and S as in the single-CTA
+// kernel). CTA r of the pair stages A rows [128 r, 128 r + 128) and B rows (n)
+// [BN/2 r, BN/2 r + BN/2) of the tile -- per 64-wide K stage 32 KB instead of
+// 48 KB (BN = 256) or 24 KB instead of 32 KB (BN = 128), which is also the
+// shared memory each MMA reads -- and holds D rows [128 r, 128 r + 128) in its
+// tensor memory. The even CTA issues the MMAs; its commits are multicast to both
+// CTAs. Each CTA's bulk copies complete on its own full barrier; a forwarder
+// thread of the odd CTA then arrives on the even CTA's full barrier, and the odd
+// CTA's epilogue warps arrive on the even CTA's accumulator-empty barriers.
+template <int BN>
+struct PairCfg {
+    static constexpr uint32_t kBHalfBytes = (uint32_t)BN * 64;  // BN/2 rows of 128 bytes
+    static constexpr uint32_t kStageBytes = kATileBytes + kBHalfBytes;
+    static constexpr int kStages = BN == 256 ? 6 : 8;
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;
+};
 
-template <int KIND>
+template <int KIND, bool FOLD>
 __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const __grid_constant__ LimbGemmArgs args)
 {
-    constexpr int BN = 256;
-    constexpr int S = kPairStages;
+    constexpr int BN = FOLD ? 256 : 128;
+    using Cfg = PairCfg<BN>;
+    constexpr int S = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
@@ -588,8 +601,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                     const uint8_t* a_src = cl.Ap + (size_t)args.pa[idx] * cl.a_plane_bytes +
                                            ((size_t)(2 * mb2 + rank) * cl.KB) * kATileBytes;
                     const uint8_t* b_src = cl.Bp + (size_t)args.pb[idx] * cl.b_plane_bytes +
-                                           ((size_t)nb * cl.KB) * (2 * kATileBytes) +
-                                           (size_t)rank * kATileBytes;
+                                           ((size_t)nb * cl.KB) * (2 * Cfg::kBHalfBytes) +
+                                           (size_t)rank * Cfg::kBHalfBytes;
                     for (int kb = kb0; kb < kb1; ++kb, ++g) {
                         const int s = g % S;
                         const uint32_t ph = (g / S) & 1;
@@ -597,11 +610,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                             ok = false;
                             break;
                         }
-                        uint8_t* sa = smem + (size_t)s * kPairStageBytes;
-                        fm_mbar_arrive_expect_tx(&full_bar[s], kPairStageBytes);
+                        uint8_t* sa = smem + (size_t)s * Cfg::kStageBytes;
+                        fm_mbar_arrive_expect_tx(&full_bar[s], Cfg::kStageBytes);
                         fm_bulk_g2s(sa, a_src + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
-                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * (2 * kATileBytes), kATileBytes,
-                                    &full_bar[s]);
+                        fm_bulk_g2s(sa + kATileBytes, b_src + (size_t)kb * (2 * Cfg::kBHalfBytes),
+                                    Cfg::kBHalfBytes, &full_bar[s]);
                     }
                 }
             }
@@ -636,13 +649,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                             break;
                         }
                         fm_tc_fence_after();
-                        const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * kPairStageBytes);
+                        const uint32_t a_addr = fm_smem_u32(smem + (size_t)s * Cfg::kStageBytes);
                         const uint32_t b_addr = a_addr + kATileBytes;
 #pragma unroll
                         for (int k = 0; k < kBK / 16; ++k) {
                             const uint64_t ad = fm_smem_desc_sw128(a_addr + k * 32);
                             const uint64_t bd = fm_smem_desc_sw128(b_addr + k * 32);
-                            const uint32_t acc = (t >= 2 || !first || k > 0) ? 1u : 0u;
+                            // fold form: from the third job of a tile on, each job
+                            // accumulates onto the residue folded back by the epilogue
+                            const uint32_t acc = ((FOLD && t >= 2) || !first || k > 0) ? 1u : 0u;
                             if (KIND == kE4M3Gf2)
                                 fm_mma_e4m3_pair(d_tmem, ad, bd, idesc, acc);
                             else
@@ -697,6 +712,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
         for (int tile = pair; tile < n_tiles && ok; tile += npairs) {
             int mb2, nb;
             coords(tile, mb2, nb);
+            const int64_t gi = (int64_t)(2 * mb2 + rank) * kBM + quarter * 32 + lane;
+            // C of this tile is read at its end: start moving it into L2 now
+            const int64_t live_cols = min((int64_t)kCols, cl.N - (int64_t)nb * BN - (int64_t)col0);
+            if (!FOLD && cl.op != FM_OP_SET && gi < cl.M && live_cols > 0)
+                prefetch_c_row(cl, gi, (int64_t)nb * BN + col0, live_cols);
             int idx = 0;
             for (int t = 0; t < njobs; ++t, ++T) {
                 const int b = T & 1;
@@ -707,64 +727,107 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                 fm_tc_fence_after();
                 while (t >= cl.first[idx + 1]) ++idx;
                 const bool last_on_buffer = (t + 2 >= njobs);
-                int idx2 = idx;
-                if (!last_on_buffer)
-                    while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
-                const bool same_next = !last_on_buffer && idx2 == idx;
                 const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
-                const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
+                if constexpr (FOLD) {
+                    int idx2 = idx;
+                    if (!last_on_buffer)
+                        while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
+                    const bool same_next = !last_on_buffer && idx2 == idx;
+                    const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
-                for (int g = 0; g < kCols / 64; ++g) {
-                    uint32_t v0[32], v1[32];
-                    fm_tmem_ld32(dbase + g * 64, v0);
-                    fm_tmem_ld32(dbase + g * 64 + 32, v1);
-                    fm_tmem_wait_ld();
-                    if (same_next) {
-                        fold_fp(v0, args.invp, args.pf);
-                        fold_fp(v1, args.invp, args.pf);
-                    } else {
-                        fold_int(v0, mul, !last_on_buffer, p, args.invp, args.pf);
-                        fold_int(v1, mul, !last_on_buffer, p, args.invp, args.pf);
+                    for (int g = 0; g < kCols / 64; ++g) {
+                        uint32_t v0[32], v1[32];
+                        fm_tmem_ld32(dbase + g * 64, v0);
+                        fm_tmem_ld32(dbase + g * 64 + 32, v1);
+                        fm_tmem_wait_ld();
+                        if (same_next) {
+                            fold_fp(v0, args.invp, args.pf);
+                            fold_fp(v1, args.invp, args.pf);
+                        } else {
+                            fold_int(v0, mul, !last_on_buffer, p, args.invp, args.pf);
+                            fold_int(v1, mul, !last_on_buffer, p, args.invp, args.pf);
+                        }
+                        fm_tmem_st32(dbase + g * 64, v0);
+                        fm_tmem_st32(dbase + g * 64 + 32, v1);
                     }
-                    fm_tmem_st32(dbase + g * 64, v0);
-                    fm_tmem_st32(dbase + g * 64 + 32, v1);
+                } else {
+                    // residue form: S (exact int32 sum of this product's chunks) is
+                    // folded into R at the product's last chunk and every 120 chunks
+                    const int c = t - cl.first[idx];
+                    const int n_chunks = cl.first[idx + 1] - cl.first[idx];
+                    const bool s_fresh = (c % 120) == 0;
+                    const bool fold_now = (c == n_chunks - 1) || ((c % 120) == 119);
+                    const bool r_fresh = (idx == 0 && c < 120);
+                    const uint32_t sbase = tmem + lane_base + (uint32_t)(3 * BN) + col0;
+                    const uint32_t rbase = tmem + lane_base + (uint32_t)(2 * BN) + col0;
+#pragma unroll 1
+                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                        uint32_t v[32], sv[32];
+                        fm_tmem_ld32(dbase + cc * 32, v);
+                        if (!s_fresh) fm_tmem_ld32(sbase + cc * 32, sv);
+                        fm_tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int32_t d = __float2int_rn(__uint_as_float(v[e]));
+                            sv[e] = (uint32_t)((s_fresh ? 0 : (int32_t)sv[e]) + d);
+                        }
+                        if (fold_now) {
+                            if (!r_fresh) {
+                                fm_tmem_ld32(rbase + cc * 32, v);
+                                fm_tmem_wait_ld();
+                            }
+                            const uint32_t wt = args.wt[idx], wts = args.wts[idx];
+#pragma unroll
+                            for (int e = 0; e < 32; ++e)
+                                v[e] = fold_sum((int32_t)sv[e], wt, wts, r_fresh ? 0u : v[e], p);
+                            fm_tmem_st32(rbase + cc * 32, v);
+                        } else {
+                            fm_tmem_st32(sbase + cc * 32, sv);
+                        }
+                    }
                 }
                 fm_tmem_wait_st();
                 fm_tc_fence_before();
                 __syncwarp();
-                if (!last_on_buffer && lane == 0)
+                // fold form: a buffer holding one of the tile's two final residues
+                // is released only after the tile end below has read it
+                if (!(FOLD && last_on_buffer) && lane == 0)
                     fm_mbar_arrive_remote(acce_leader + (uint32_t)(b * sizeof(uint64_t)));
             }
             if (!ok) break;
-            // tile end: merge the two final residues, release, write C
-            const int64_t gi = (int64_t)(2 * mb2 + rank) * kBM + quarter * 32 + lane;
+            // tile end: the final residue (fold form: the sum of the two buffers'
+            // residues; residue form: R) -> combine with C -> Morton-hybrid write
+            uint32_t rsrc = (uint32_t)(2 * BN);
             const int by = (T - 1) & 1, bx = by ^ 1;
-            if (njobs >= 2) {
-                const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
-                const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
+            if (FOLD) {
+                rsrc = (uint32_t)(by * BN);
+                if (njobs >= 2) {
+                    const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
+                    const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
 #pragma unroll 1
-                for (int cc = 0; cc < kCols / 32; ++cc) {
-                    uint32_t xv[32], yv[32];
-                    fm_tmem_ld32(xb + cc * 32, xv);
-                    fm_tmem_ld32(yb + cc * 32, yv);
-                    fm_tmem_wait_ld();
+                    for (int cc = 0; cc < kCols / 32; ++cc) {
+                        uint32_t xv[32], yv[32];
+                        fm_tmem_ld32(xb + cc * 32, xv);
+                        fm_tmem_ld32(yb + cc * 32, yv);
+                        fm_tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const uint32_t x = xv[e] + yv[e];
-                        yv[e] = x >= p ? x - p : x;
+                        for (int e = 0; e < 32; ++e) {
+                            const uint32_t x = xv[e] + yv[e];
+                            yv[e] = x >= p ? x - p : x;
+                        }
+                        fm_tmem_st32(yb + cc * 32, yv);
                     }
-                    fm_tmem_st32(yb + cc * 32, yv);
+                    fm_tmem_wait_st();
+                    fm_tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(bx * sizeof(uint64_t)));
                 }
-                fm_tmem_wait_st();
-                fm_tc_fence_before();
-                __syncwarp();
-                if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(bx * sizeof(uint64_t)));
             }
 #pragma unroll 1
             for (int cc = 0; cc < kCols / 32; ++cc) {
                 uint32_t sres[32];
                 const uint32_t col = col0 + cc * 32;
-                fm_tmem_ld32(tmem + lane_base + (uint32_t)(by * BN) + col, sres);
+                fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
                 fm_tmem_wait_ld();
                 if (gi < cl.M) {
                     if (KIND == kE4M3Gf2)
@@ -773,9 +836,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) limb_gemm_pair_kernel(const _
                         write_c_run<32>(cl, p, args.mu32, gi, (int64_t)nb * BN + col, cmask, sres);
                 }
             }
-            fm_tc_fence_before();
-            __syncwarp();
-            if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(by * sizeof(uint64_t)));
+            if (FOLD) {
+                fm_tc_fence_before();
+                __syncwarp();
+                if (lane == 0) fm_mbar_arrive_remote(acce_leader + (uint32_t)(by * sizeof(uint64_t)));
+            }
         }
     }
 
@@ -832,9 +897,9 @@ int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
     return FM_OK;
 }
 
-// How many CTA pairs of limb_gemm_pair_kernel<KIND> fit on the current device
-// at once; queried once per device and kind.
-template <int KIND>
+// How many CTA pairs of limb_gemm_pair_kernel<KIND, FOLD> fit on the current
+// device at once; queried once per device and variant.
+template <int KIND, bool FOLD>
 int pair_capacity(int* out)
 {
     static std::mutex mu;
@@ -846,8 +911,9 @@ int pair_capacity(int* out)
         *out = max_pairs[dev];
         return FM_OK;
     }
-    auto k = limb_gemm_pair_kernel<KIND>;
-    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
+    constexpr size_t smem = PairCfg<FOLD ? 256 : 128>::kSmem;
+    auto k = limb_gemm_pair_kernel<KIND, FOLD>;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -856,7 +922,7 @@ int pair_capacity(int* out)
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2 * fm_sm_count());
     cfg.blockDim = dim3(kGemmThreads);
-    cfg.dynamicSmemBytes = kPairSmem;
+    cfg.dynamicSmemBytes = smem;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
@@ -869,13 +935,14 @@ int pair_capacity(int* out)
 
 // Clusters of two CTAs, one per pair tile up to the number of pairs that fit
 // on the device at once (the kernel walks further tiles itself).
-template <int KIND>
+template <int KIND, bool FOLD>
 int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
 {
     int cap = 0;
-    FM_TRY(pair_capacity<KIND>(&cap));
-    auto k = limb_gemm_pair_kernel<KIND>;
-    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem));
+    FM_TRY((pair_capacity<KIND, FOLD>(&cap)));
+    constexpr size_t smem = PairCfg<FOLD ? 256 : 128>::kSmem;
+    auto k = limb_gemm_pair_kernel<KIND, FOLD>;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -883,7 +950,7 @@ int launch_gemm_pair(const LimbGemmArgs& a, int pair_tiles, cudaStream_t s)
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kGemmThreads);
-    cfg.dynamicSmemBytes = kPairSmem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -1002,7 +1069,8 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
             for (int k = 0; k < w * w; ++k)
                 if (gcd_u64(q.prod_w[k], p) != 1) return FM_EUNSUPPORTED;
     }
-    if (opts && opts->cta_pair == 1 && (!q.fold || bn != 256)) return FM_EINVAL;
+    // CTA pairs: 256 x 256 tiles in the fold form, 256 x 128 in the residue form
+    if (opts && opts->cta_pair == 1 && bn != (q.fold ? 256 : 128)) return FM_EINVAL;
     // automatic: CTA pairs for the fold form on 256-wide tiles of a product
     // with several tiles in each direction and a K loop long enough to hide
     // the pair's two-epilogue coupling
@@ -1010,7 +1078,9 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     if (pair == 0) pair = (q.fold && bn == 256 && M > 256 && N > 256 && K >= kPairMinK) ? 1 : -1;
     q.pair = pair == 1 ? 1 : 0;
     q.MB = (int)((M + kBM - 1) / kBM);
-    if (bn == 256) q.MB += q.MB & 1;  // the A plane layout depends on BN only
+    // an even number of A row blocks wherever a pair may run; the A plane
+    // layout depends on the form and BN only
+    if (bn == 256 || !q.fold) q.MB += q.MB & 1;
     q.NB = (int)((N + bn - 1) / bn);
     q.KB = (int)((K + kBK - 1) / kBK);
     q.a_plane_bytes = (size_t)q.MB * q.KB * kATileBytes;
@@ -1050,8 +1120,9 @@ int fm_gf2_plan(int64_t M, int64_t N, int64_t K, bool pair, FmLimbPlan* plan)
 int fm_limb_prepare_device()
 {
     int cap = 0;
-    FM_TRY(pair_capacity<kF16Res>(&cap));
-    return pair_capacity<kE4M3Gf2>(&cap);
+    FM_TRY((pair_capacity<kF16Res, true>(&cap)));
+    FM_TRY((pair_capacity<kF16Res, false>(&cap)));
+    return pair_capacity<kE4M3Gf2, true>(&cap);
 }
 
 size_t fm_limb_workspace_bytes(const FmLimbPlan& q)
@@ -1068,7 +1139,6 @@ void fill_common(const FmLimbPlan& q, uint32_t p, int* status, LimbGemmArgs& a)
     a.n_products = q.n_products;
     a.p = p;
     a.mu32 = (uint32_t)(((uint64_t)1 << 32) / p);
-    a.mu64 = ~0ull / p;
     for (int k = 0; k < q.n_products; ++k) {
         a.pa[k] = q.prod_a[k];
         a.pb[k] = q.prod_b[k];
@@ -1084,7 +1154,7 @@ void fill_common(const FmLimbPlan& q, uint32_t p, int* status, LimbGemmArgs& a)
     }
     a.invp = 1.0f / (float)p;
     a.pf = (float)p;
-    a.offs64 = ((((uint64_t)1 << 31) + p - 1) / p) * (uint64_t)p;
+    for (int k = 0; k < q.n_products; ++k) a.wts[k] = (uint32_t)(((uint64_t)a.wt[k] << 32) / p);
     a.status = status;
 }
 
@@ -1126,10 +1196,13 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     a.call.M = q.M;
     a.call.N = q.N;
     if (q.gf2) {
-        if (q.pair) return launch_gemm_pair<kE4M3Gf2>(a, q.MB / 2 * q.NB, s);
+        if (q.pair) return launch_gemm_pair<kE4M3Gf2, true>(a, q.MB / 2 * q.NB, s);
         return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
     }
-    if (q.pair) return launch_gemm_pair<kF16Res>(a, q.MB / 2 * q.NB, s);
+    if (q.pair) {
+        if (q.fold) return launch_gemm_pair<kF16Res, true>(a, q.MB / 2 * q.NB, s);
+        return launch_gemm_pair<kF16Res, false>(a, q.MB / 2 * q.NB, s);
+    }
     const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);

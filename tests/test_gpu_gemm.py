@@ -106,6 +106,39 @@ def test_limb_cta_pair_and_single_cta(env, orc, M, N, K):
             assert np.array_equal(got, want), (p, pair)
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (129, 130, 1000), (300, 520, 1000),
+                                   (2560, 2048, 128), (1000, 3000, 200), (513, 257, 2100)])
+def test_limb_residue_cta_pair_and_single_cta(env, orc, M, N, K):
+    # residue form (p >= 2^16 or even p): 256 x 128 tiles on CTA pairs against
+    # 128 x 128 tiles on single CTAs; one tile whose second half lies past M,
+    # ragged columns, more pair tiles than pairs resident on the device, and
+    # K spanning several chunks of every product
+    fm = env[0]
+    for p, op in ((P31, 2), (65537, 0), (65534, 1), (1000003, 2)):
+        for pair in (-1, 1):
+            got, want = run_case(env, orc, p, op, fm.FM_ALGO_LIMB_TC, M, N, K, (0, 3, 5, 0, 0, 7),
+                                 (7, 6, 7), seed=M + N + p % 997 + pair,
+                                 options=fm.opts(0, 128, 0, pair))
+            assert np.array_equal(got, want), (p, op, pair)
+
+
+@pytest.mark.parametrize("pair", [-1, 1])
+def test_limb_residue_sum_refresh(env, orc, pair):
+    # With 64-wide chunks a product at K = 8000 has 125 chunks: its int32 sum S
+    # is folded into the residue after chunk 119 and restarted at chunk 120
+    # (120 chunks of at most 2^24 stay inside int32). Random inputs, and the
+    # extremes whose every chunk sums to exactly 2^24.
+    fm = env[0]
+    o = fm.opts(64, 128, 0, pair)
+    got, want = run_case(env, orc, P31, 2, fm.FM_ALGO_LIMB_TC, 300, 200, 8000, (1, 2, 3, 4, 5, 6),
+                         (6, 6, 6), seed=120 + pair, options=o)
+    assert np.array_equal(got, want)
+    lo = 8355712  # digits (-128, -128, -128, 1)
+    hi = 127 * (1 + 256 + 65536)  # digits (127, 127, 127, 0): negative sums against lo
+    for a, b in ((P31 - 128, P31 - 128), (lo, lo), (lo, hi), (P31 - 128, 127)):
+        _constant_case(env, orc, P31, a, b, 8000, fm.FM_ALGO_LIMB_TC, o)
+
+
 def test_limb_rejects_unsafe_chunk(env):
     fm, dev = env
     M = MortonMatrix(fm, dev, 1, 7)
@@ -113,9 +146,12 @@ def test_limb_rejects_unsafe_chunk(env):
     with pytest.raises(fm.FmError):   # 1024 > the exact bound 960 when folding p = 65521
         fm.fm_gemm_modp(M.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), P16, 0,
                         fm.FM_ALGO_LIMB_TC, fm.opts(1024, 0))
-    with pytest.raises(fm.FmError):   # CTA pairs need the fold form on 256-wide tiles
+    with pytest.raises(fm.FmError):   # CTA pairs: 256-wide tiles in the fold form
         fm.fm_gemm_modp(M.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), P16, 0,
                         fm.FM_ALGO_LIMB_TC, fm.opts(0, 128, 0, 1))
+    with pytest.raises(fm.FmError):   # and 128-wide tiles in the residue form
+        fm.fm_gemm_modp(M.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), A.sub(0, 0, 64, 64), P31, 0,
+                        fm.FM_ALGO_LIMB_TC, fm.opts(0, 256, 0, 1))
 
 
 def _constant_case(env, orc, p, a, b, K, algo, options=None):
@@ -152,12 +188,13 @@ def test_limb_accumulator_extremes_p31(env, orc, K):
     # p = 2^31 - 1, chunk 1024 without folding: all limbs -128 sum to exactly
     # 2^24 per chunk. x = p - 128 * 256^t (t < 3) has limb t equal to -128; the
     # top limb of a representative lies in [-1, 127], so 127 * 256^3 is its
-    # extreme.
+    # extreme. On single CTAs and on CTA pairs.
     fm = env[0]
     extremes = [P31 - 128 * 256 ** t for t in range(3)] + [127 * 256 ** 3]
-    for a in extremes:
-        _constant_case(env, orc, P31, a, a, K, fm.FM_ALGO_LIMB_TC)
-    _constant_case(env, orc, P31, extremes[0], extremes[3], K, fm.FM_ALGO_LIMB_TC)
+    for o in (fm.opts(0, 128, 0, -1), fm.opts(0, 128, 0, 1)):
+        for a in extremes:
+            _constant_case(env, orc, P31, a, a, K, fm.FM_ALGO_LIMB_TC, o)
+        _constant_case(env, orc, P31, extremes[0], extremes[3], K, fm.FM_ALGO_LIMB_TC, o)
 
 
 @pytest.mark.parametrize("K", [256, 512, 1024, 2048])
@@ -173,8 +210,9 @@ def test_limb_karatsuba_pair_extremes(env, orc, K, p):
     w = 4 if p > (1 << 24) else 3
     lo = 8355712 if w == 4 else 32640
     hi = 127 * (1 + 256 + 65536) if w == 4 else 127 * 257
-    for a, b in ((lo, lo), (lo, hi), (hi, hi)):
-        _constant_case(env, orc, p, a, b, K, fm.FM_ALGO_LIMB_TC)
+    for o in (fm.opts(0, 128, 0, -1), fm.opts(0, 128, 0, 1)):
+        for a, b in ((lo, lo), (lo, hi), (hi, hi)):
+            _constant_case(env, orc, p, a, b, K, fm.FM_ALGO_LIMB_TC, o)
 
 
 def test_empty_and_degenerate(env, orc):
