@@ -534,20 +534,55 @@ __global__ void swap_pairs_kernel(uint32_t* A, int lt, int64_t n, const int* __r
     }
 }
 
+// a * b mod p for p < 2^16 (a, b < p): the product fits 32 bits; one Barrett
+// step with mu32 = floor(2^32 / p) leaves it below 2p
+__device__ __forceinline__ uint32_t mulmod16(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32)
+{
+    const uint32_t x = a * b;
+    uint32_t r = x - __umulhi(x, mu32) * p;
+    return r >= p ? r - p : r;
+}
+
+// a * b mod p, products of residues below 2^16 in 32 bits, else 64-bit Barrett
+template <bool SMALL>
+__device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32, uint64_t mu)
+{
+    return SMALL ? mulmod16(a, b, p, mu32) : mulmod(a, b, p, mu);
+}
+
+// a^e mod p by square-and-multiply
+template <bool SMALL>
+__device__ __forceinline__ uint32_t powm(uint32_t a, uint32_t e, uint32_t p, uint32_t mu32, uint64_t mu)
+{
+    uint32_t r = 1 % p, b = a;
+    while (e) {
+        if (e & 1) r = mulm<SMALL>(r, b, p, mu32, mu);
+        b = mulm<SMALL>(b, b, p, mu32, mu);
+        e >>= 1;
+    }
+    return r;
+}
+
+// sum of a * b over 32 terms, reduced once: raw products below 2^32 when
+// p < 2^16, reduced products otherwise (the sum stays below 2^37 either way)
+template <bool SMALL>
+__device__ __forceinline__ uint64_t mac(uint64_t acc, uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
+{
+    return acc + (SMALL ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
+}
+
 // X <- L11^-1 (k x k, k <= 128), L11 the unit lower triangle of rows
 // [r0, r0+k) x columns [c0, c0+k); X is written to the Morton-hybrid matrix Xm
 // (zero above the diagonal, ones on it). Blocked in 32 x 32 blocks (the
-// identity pads k to a multiple of 32): one warp inverts each diagonal block
-// row by row (X(i, j) = -sum_{j <= t < i} L(i, t) X(t, j)); then block row bi
-// follows from the rows above it, X(bi, bj) = -X(bi, bi) sum_{bj <= m < bi}
+// identity pads k to a multiple of 32): the diagonal blocks by forward
+// substitution, one column of each per warp (unit_lower_inv_cols); then block
+// row bi follows from the rows above it, X(bi, bj) = -X(bi, bi) sum_{bj <= m < bi}
 // L(bi, m) X(m, bj), for all bj at once. Sums accumulate in 64 bits: raw
 // products below p^2 < 2^32 when p < 2^16, products reduced mod p otherwise.
+// L and X live in shared memory with a row stride of K + 1 words, so that a
+// warp reading one column touches 32 different banks.
 constexpr int kInvThreads = 1024;
-
-__device__ __forceinline__ uint64_t mac_p(uint64_t acc, uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
-{
-    return acc + (p < 65536u ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
-}
+constexpr int kInvStride = kNb + 1;
 
 // x mod p for x < 2^40 (sums of at most 256 products below 2^32): Barrett with
 // mu = floor((2^64 - 1) / p) leaves the remainder below 2p
@@ -563,47 +598,104 @@ __device__ __forceinline__ uint32_t neg_mod(uint64_t acc, uint32_t p, uint64_t m
     return r == 0 ? 0u : p - r;
 }
 
+// NC columns of inverses of unit lower 32 x 32 triangles, one warp, by forward
+// substitution: column c has index j[c] and its triangle's strictly lower part
+// W (W(i, t) = 0 for t >= i); lrow[c] points at row `lane` of W. Lane i ends
+// with X(i, j) in x[c]: X(i, j) = 0 for i < j, X(j, j) = 1 and
+// X(i, j) = -sum_{j <= t < i} W(i, t) X(t, j) for i > j. Step t broadcasts the
+// final X(t, j) from lane t, after which lane t + 1's sum is complete; the NC
+// columns interleave, so their dependency chains overlap. Every lane runs every
+// step, so the per-step work is what counts: for p < 2^16 each product is
+// reduced at once (32-bit Barrett) and the sum of at most 31 residues stays
+// below 2^21 in 32 bits; otherwise the sum of reduced products is kept in 64
+// bits.
+template <int NC, bool SMALL>
+__device__ __forceinline__ void unit_lower_inv_cols(const uint32_t* const (&lrow)[NC], const int (&j)[NC],
+                                                    uint32_t (&x)[NC], uint32_t p, uint32_t mu32, uint64_t mu,
+                                                    int lane)
+{
+    uint64_t acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        acc[c] = 0;
+        x[c] = lane == j[c] ? 1u : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 31; ++t) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const uint32_t xt = __shfl_sync(0xffffffffu, x[c], t);
+            if (SMALL) {
+                const uint32_t a = (uint32_t)acc[c] + mulmod16(lrow[c][t], xt, p, mu32);
+                acc[c] = a;
+                if (lane == t + 1 && t + 1 > j[c]) {
+                    const uint32_t r = mulmod16(a, 1u, p, mu32);  // a < 2^21
+                    x[c] = r == 0 ? 0u : p - r;
+                }
+            } else {
+                acc[c] += mulmod(lrow[c][t], xt, p, mu);
+                if (lane == t + 1 && t + 1 > j[c]) x[c] = neg_mod(acc[c], p, mu);
+            }
+        }
+    }
+}
+
 // UPPER = false: X = L^-1 for the unit lower triangle L of A (as above).
 // UPPER = true: X = U^-1 for the upper triangle U of A rows [r0, r0+k) x
 // columns [c0, c0+k) with dinv[t] = 1 / U(t, t): U = diag(U) V with V unit
 // upper, so the same inversion runs on the unit lower V^T, and
-// U^-1 (i, j) = (V^T)^-1 (j, i) / U(j, j).
-template <bool UPPER>
+// U^-1 (i, j) = (V^T)^-1 (j, i) / U(j, j). The diagonal blocks of the inverse
+// of a lower triangle are the inverses of its diagonal blocks: when dg is not
+// null (k = 128) they are taken from there (block b's inverse column-major at
+// dg + b * 2048 + (UPPER ? 1024 : 0), as diag_lu_kernel leaves them).
+template <bool UPPER, bool SMALL>
 __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t r0, int64_t c0, int k, uint32_t* X,
-                                             int xlt, uint32_t p, uint64_t mu, const uint32_t* dinv)
+                                             int xlt, uint32_t p, uint64_t mu, const uint32_t* dinv,
+                                             const uint32_t* dg)
 {
+    const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
     extern __shared__ uint32_t smx[];
-    constexpr int K = kNb;                 // padded size, 4 blocks of 32
-    uint32_t* L = smx;                     // [K][K], strictly lower part
-    uint32_t* Xs = smx + (size_t)K * K;    // [K][K]
-    uint32_t* T = Xs + (size_t)K * K;      // [3][32][32]
+    constexpr int K = kNb, S = kInvStride;  // padded size, 4 blocks of 32
+    uint32_t* L = smx;                      // [K][S], strictly lower part
+    uint32_t* Xs = smx + (size_t)K * S;     // [K][S]
+    uint32_t* T = Xs + (size_t)K * S;       // [3][32][32]
     const int nb = (k + 31) / 32;
-    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-        const int i = e / K, t = e % K;
+    // element e = (a, b) with b the fastest: a row of A is read along its
+    // columns in both cases (UPPER: W(b, a) = U(a, b) / U(a, a))
+#pragma unroll
+    for (int q = 0; q < K * K / kInvThreads; ++q) {
+        const int e = (int)threadIdx.x + q * kInvThreads;
+        const int a = e / K, b = e % K;
         uint32_t v = 0;
-        if (t < i && i < k) {
-            if (UPPER)
-                v = mulmod(A[fm_encode((uint64_t)(r0 + t), (uint64_t)(c0 + i), lt)], dinv[t], p, mu);
-            else
-                v = A[fm_encode((uint64_t)(r0 + i), (uint64_t)(c0 + t), lt)];
+        if (UPPER) {
+            if (a < b && b < k) v = mulmod(A[fm_encode((uint64_t)(r0 + a), (uint64_t)(c0 + b), lt)], dinv[a], p, mu);
+            L[b * S + a] = v;
+        } else {
+            if (b < a && a < k) v = A[fm_encode((uint64_t)(r0 + a), (uint64_t)(c0 + b), lt)];
+            L[a * S + b] = v;
         }
-        L[e] = v;
-        Xs[e] = i == t ? 1u : 0u;
+        Xs[a * S + b] = a == b ? 1u : 0u;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // 1. the diagonal blocks, one warp each
-    if (warp < nb) {
-        const int base = 32 * warp, j = base + lane;
-        for (int r = 1; r < 32; ++r) {
-            const int i = base + r;
-            if (lane < r) {
-                uint64_t acc = 0;
-                for (int t = j; t < i; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + j], p, mu);
-                Xs[i * K + j] = neg_mod(acc, p, mu);
-            }
-            __syncwarp();
+    // 1. the diagonal blocks: column `warp` of each, one warp (or loaded)
+    if (dg) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            Xs[(32 * b + lane) * S + 32 * b + warp] = dg[b * 2048 + (UPPER ? 1024 : 0) + warp * 32 + lane];
+    } else {
+        const uint32_t* lrow[4];
+        int jj[4];
+        uint32_t x[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            lrow[b] = L + (size_t)(32 * b + lane) * S + 32 * b;
+            jj[b] = warp;
         }
+        unit_lower_inv_cols<4, SMALL>(lrow, jj, x, p, mu32, mu, lane);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (b < nb) Xs[(32 * b + lane) * S + 32 * b + warp] = x[b];
     }
     __syncthreads();
     // 2. block rows below the first: thread (r, c) = (warp, lane) of each 32 x 32 block
@@ -611,42 +703,50 @@ __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t 
         const int i = 32 * bi + warp;
         for (int bj = 0; bj < bi; ++bj) {
             uint64_t acc = 0;
-            for (int t = 32 * bj; t < 32 * bi; ++t) acc = mac_p(acc, L[i * K + t], Xs[t * K + 32 * bj + lane], p, mu);
+#pragma unroll 8
+            for (int t = 32 * bj; t < 32 * bi; ++t) acc = mac<SMALL>(acc, L[i * S + t], Xs[t * S + 32 * bj + lane], p, mu);
             T[(bj * 32 + warp) * 32 + lane] = red64(acc, p, mu);
         }
         __syncthreads();
         for (int bj = 0; bj < bi; ++bj) {
             uint64_t acc = 0;
+#pragma unroll 8
             for (int s2 = 0; s2 < 32; ++s2)
-                acc = mac_p(acc, Xs[i * K + 32 * bi + s2], T[(bj * 32 + s2) * 32 + lane], p, mu);
-            Xs[i * K + 32 * bj + lane] = neg_mod(acc, p, mu);
+                acc = mac<SMALL>(acc, Xs[i * S + 32 * bi + s2], T[(bj * 32 + s2) * 32 + lane], p, mu);
+            Xs[i * S + 32 * bj + lane] = neg_mod(acc, p, mu);
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
         X[fm_encode((uint64_t)i, (uint64_t)j, xlt)] =
-            UPPER ? mulmod(Xs[j * K + i], dinv[j], p, mu) : Xs[i * K + j];
+            UPPER ? mulmod(Xs[j * S + i], dinv[j], p, mu) : Xs[i * S + j];
     }
 }
 
+template <bool SMALL>
 __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                               int k, uint32_t* X, int xlt, uint32_t p,
                                                               uint64_t mu)
 {
-    tri_inv_body<false>(A, lt, r0, c0, k, X, xlt, p, mu, nullptr);
+    tri_inv_body<false, SMALL>(A, lt, r0, c0, k, X, xlt, p, mu, nullptr, nullptr);
 }
 
 // Both inverses of a diagonal block factored by diag_lu_kernel: CTA 0 writes
-// X = L11^-1, CTA 1 writes Y = U11^-1.
+// X = L11^-1, CTA 1 writes Y = U11^-1. Launched right behind diag_lu_kernel,
+// before the host has read its flag: when the fast path failed (*flag != 0)
+// it returns at once.
+template <bool SMALL>
 __global__ void __launch_bounds__(kInvThreads) tri_inv2_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                                uint32_t* X, uint32_t* Y, int xlt, uint32_t p,
-                                                               uint64_t mu, const uint32_t* dinv)
+                                                               uint64_t mu, const uint32_t* dinv, const int* flag,
+                                                               const uint32_t* dg)
 {
+    if (*flag != 0) return;
     if (blockIdx.x == 0)
-        tri_inv_body<false>(A, lt, r0, c0, kNb, X, xlt, p, mu, nullptr);
+        tri_inv_body<false, SMALL>(A, lt, r0, c0, kNb, X, xlt, p, mu, nullptr, dg);
     else
-        tri_inv_body<true>(A, lt, r0, c0, kNb, Y, xlt, p, mu, dinv);
+        tri_inv_body<true, SMALL>(A, lt, r0, c0, kNb, Y, xlt, p, mu, dinv, dg);
 }
 
 // ---- diagonal-block fast path -------------------------------------------------
@@ -664,69 +764,40 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv2_kernel(const uint32_t* A
 // 1 / U11(t, t).
 constexpr int kDiagThreads = 1024;
 
-__device__ __forceinline__ uint32_t powmod_dev(uint32_t a, uint32_t e, uint32_t p, uint64_t mu)
-{
-    uint32_t r = 1 % p, b = a;
-    while (e) {
-        if (e & 1) r = mulmod(r, b, p, mu);
-        b = mulmod(b, b, p, mu);
-        e >>= 1;
-    }
-    return r;
-}
-
-// a * b mod p for p < 2^16 (a, b < p): the product fits 32 bits; one Barrett
-// step with mu32 = floor(2^32 / p) leaves it below 2p
-__device__ __forceinline__ uint32_t mulmod16(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32)
-{
-    const uint32_t x = a * b;
-    uint32_t r = x - __umulhi(x, mu32) * p;
-    return r >= p ? r - p : r;
-}
-
-// a * b mod p, products of residues below 2^16 in 32 bits, else 64-bit Barrett
-template <bool SMALL>
-__device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uint32_t mu32, uint64_t mu)
-{
-    return SMALL ? mulmod16(a, b, p, mu32) : mulmod(a, b, p, mu);
-}
-
-// sum of a * b over 32 terms, reduced once: raw products below 2^32 when
-// p < 2^16, reduced products otherwise (the sum stays below 2^37 either way)
-template <bool SMALL>
-__device__ __forceinline__ uint64_t mac(uint64_t acc, uint32_t a, uint32_t b, uint32_t p, uint64_t mu)
-{
-    return acc + (SMALL ? (uint64_t)a * b : (uint64_t)mulmod(a, b, p, mu));
-}
-
 // Blocked in 32-wide block columns o = 0, 32, 64, 96 (the same L and U as the
 // unblocked elimination without row exchanges, which are unique):
 //   1. the 32 x 32 diagonal block by the division-free steps above, one entry
 //      per thread per step (rows on warps, columns on lanes), then its 32
 //      inverses at once; L_kk and U_kk written back;
-//   2. L_kk^-1 (warp 0) and U_kk^-1 (warp 1, as (V^T)^-1 transposed with
-//      U_kk = diag(U_kk) V), row by row;
+//   2. L_kk^-1 and U_kk^-1 (as (V^T)^-1 transposed, U_kk = diag(U_kk) V) by
+//      forward substitution, one column of each per warp; both inverses are
+//      also left in dg for tri_inv2_kernel;
 //   3. the panel below, L_ik = A_ik U_kk^-1, and the row to the right,
 //      U_kj = L_kk^-1 A_kj, as 32-term dot products reduced once;
 //   4. the trailing update A_ij -= L_ik U_kj, likewise.
 template <bool SMALL>
 __global__ void __launch_bounds__(kDiagThreads) diag_lu_kernel(uint32_t* A, int lt, int64_t r0, int64_t c0,
-                                                               uint32_t p, uint64_t mu, uint32_t* dinv, int* flag)
+                                                               uint32_t p, uint64_t mu, uint32_t* dinv, int* flag,
+                                                               uint32_t* dg)
 {
     constexpr int K = kNb, B = 32;
     extern __shared__ uint32_t sm[];
+    constexpr int S = B + 1;          // padded row stride: a column read hits 32 banks
     uint32_t* D = sm;                 // [K][K]
-    uint32_t* Li = D + K * K;         // [B][B]  L_kk^-1
-    uint32_t* Ui = Li + B * B;        // [B][B]  U_kk^-1
-    uint32_t* Z = Ui + B * B;         // [B][B]  (V^T)^-1
-    uint32_t* TL = Z + B * B;         // [K - B][B]  new panel below
+    uint32_t* Li = D + K * K;         // [B][S]  L_kk^-1
+    uint32_t* Ui = Li + B * S;        // [B][B]  U_kk^-1
+    uint32_t* Z = Ui + B * B;         // [B][S]  (V^T)^-1
+    uint32_t* TL = Z + B * S;         // [K - B][B]  new panel below
     uint32_t* TU = TL + (K - B) * B;  // [B][K - B]  new row to the right
     __shared__ uint32_t cpiv[B], cinv[B], sinv[B], sig[B], dv[K];
     __shared__ int s_zero;
     const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < K * K; e += kDiagThreads)
+#pragma unroll
+    for (int q = 0; q < K * K / kDiagThreads; ++q) {
+        const int e = tid + q * kDiagThreads;
         D[e] = A[fm_encode((uint64_t)(r0 + e / K), (uint64_t)(c0 + e % K), lt)];
+    }
     if (tid == 0) s_zero = 0;
     for (int o = 0; o < K; o += B) {
         // 1. division-free LU of the diagonal block
@@ -749,76 +820,71 @@ __global__ void __launch_bounds__(kDiagThreads) diag_lu_kernel(uint32_t* A, int 
             if (tid == 0) *flag = 1;
             return;
         }
-        if (tid == 0) {
-            uint32_t g = 1 % p;
-            for (int t = 0; t < B; ++t) {
-                sig[t] = g;
-                g = mulm<SMALL>(g, cpiv[t], p, mu32, mu);
+        if (warp == 0) {
+            // sigma_t = c_0 ... c_{t-1}: an exclusive prefix product (warp scan),
+            // then 1 / sigma_t
+            uint32_t v = cpiv[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v = mulm<SMALL>(v, u, p, mu32, mu);
             }
+            const uint32_t ex = __shfl_up_sync(0xffffffffu, v, 1);
+            const uint32_t g = lane == 0 ? 1 % p : ex;
+            sig[lane] = g;
+            sinv[lane] = powm<SMALL>(g, p - 2, p, mu32, mu);
+        } else if (warp == 1) {
+            cinv[lane] = powm<SMALL>(cpiv[lane], p - 2, p, mu32, mu);
         }
-        __syncthreads();
-        if (warp == 0)
-            cinv[lane] = powmod_dev(cpiv[lane], p - 2, p, mu);
-        else if (warp == 1)
-            sinv[lane] = powmod_dev(sig[lane], p - 2, p, mu);
         __syncthreads();
         {  // normalise: l_it = S_i[t] / c_t below the diagonal, U row t = S_t / sigma_t
             const int i = warp, j = lane;
             uint32_t& v = D[(o + i) * K + o + j];
-            v = i > j ? mulmod(v, cinv[j], p, mu) : mulmod(v, sinv[i], p, mu);
-            if (i == 0) dv[o + j] = mulmod(sig[j], cinv[j], p, mu);  // 1 / u_jj
+            v = mulm<SMALL>(v, i > j ? cinv[j] : sinv[i], p, mu32, mu);
+            if (i == 0) dv[o + j] = mulm<SMALL>(sig[j], cinv[j], p, mu32, mu);  // 1 / u_jj
         }
         __syncthreads();
         // 2. L_kk^-1 and (V^T)^-1 with V^T(i, t) = U(t, i) / u_tt, both unit
-        //    lower: with M = -(X - I) strictly lower, M^32 = 0 and
-        //    X^-1 = (I + M)(I + M^2)(I + M^4)(I + M^8)(I + M^16), built by four
-        //    squarings of M and four products, every entry on its own thread
-        //    (warp = row, lane = column); TL and TU are free until step 3.
-        for (int which = 0; which < 2; ++which) {
-            uint32_t* X = which == 0 ? Li : Z;  // the inverse
-            uint32_t* Q = TL;                   // M^(2^s)
-            uint32_t* T = TL + B * B;           // product scratch
-            {
-                const int i = warp, j = lane;
-                uint32_t m = 0;
-                if (j < i) {
-                    const uint32_t x = which == 0 ? D[(o + i) * K + o + j]
-                                                  : mulm<SMALL>(D[(o + j) * K + o + i], dv[o + j], p, mu32, mu);
-                    m = x == 0 ? 0u : p - x;
-                }
-                Q[i * B + j] = m;
-                X[i * B + j] = i == j ? 1u : m;
-            }
-            for (int sq = 1; sq < 5; ++sq) {
-                __syncthreads();
-                const int i = warp, j = lane;
-                uint64_t acc = 0;
-                for (int t = j; t < i; ++t) acc = mac<SMALL>(acc, Q[i * B + t], Q[t * B + j], p, mu);
-                T[i * B + j] = red64(acc, p, mu);  // M^(2^sq)
-                __syncthreads();
-                Q[i * B + j] = T[i * B + j];
-                __syncthreads();
-                acc = 0;
-                for (int t = j; t <= i; ++t) acc = mac<SMALL>(acc, X[i * B + t], Q[t * B + j], p, mu);
-                T[i * B + j] = red64(acc, p, mu);  // X M^(2^sq)
-                __syncthreads();
-                const uint32_t xv = X[i * B + j] + T[i * B + j];
-                X[i * B + j] = xv >= p ? xv - p : xv;
-            }
-            __syncthreads();
+        //    lower: their strictly lower parts W1, W2 are copied to padded
+        //    [B][S] arrays in TL (free until step 3), then warp w solves for
+        //    column w of both inverses by forward substitution
+        {
+            uint32_t* W1 = TL;
+            uint32_t* W2 = TL + B * S;
+            const int i = warp, t = lane;
+            W1[i * S + t] = t < i ? D[(o + i) * K + o + t] : 0u;
+            // thread (warp, lane) = (t', i'): reads row t' of U along its columns
+            W2[lane * S + warp] = warp < lane ? mulm<SMALL>(D[(o + warp) * K + o + lane], dv[o + warp], p, mu32, mu) : 0u;
         }
-        Ui[warp * B + lane] = warp <= lane ? mulmod(Z[lane * B + warp], dv[o + lane], p, mu) : 0u;
+        __syncthreads();
+        {
+            const uint32_t* lrow[2] = {TL + lane * S, TL + B * S + lane * S};
+            const int jj[2] = {warp, warp};
+            uint32_t x[2];
+            unit_lower_inv_cols<2, SMALL>(lrow, jj, x, p, mu32, mu, lane);
+            Li[lane * S + warp] = x[0];
+            Z[lane * S + warp] = x[1];
+            // both, column-major, for tri_inv2_kernel (the diagonal blocks of
+            // L11^-1 and of (V^T)^-1)
+            dg[(o / B) * 2048 + warp * 32 + lane] = x[0];
+            dg[(o / B) * 2048 + 1024 + warp * 32 + lane] = x[1];
+        }
+        __syncthreads();
+        Ui[warp * B + lane] = warp <= lane ? mulm<SMALL>(Z[lane * S + warp], dv[o + lane], p, mu32, mu) : 0u;
         __syncthreads();
         if (o + B >= K) break;
         // 3. the panel below and the row to the right
+        //    (all 32 terms: U_kk^-1 is zero below its diagonal, L_kk^-1 above)
         for (int i = o + B + warp; i < K; i += 32) {
             uint64_t acc = 0;
-            for (int t = 0; t <= lane; ++t) acc = mac<SMALL>(acc, D[i * K + o + t], Ui[t * B + lane], p, mu);
+#pragma unroll 8
+            for (int t = 0; t < B; ++t) acc = mac<SMALL>(acc, D[i * K + o + t], Ui[t * B + lane], p, mu);
             TL[(i - o - B) * B + lane] = red64(acc, p, mu);
         }
         for (int j = o + B + lane; j < K; j += 32) {
             uint64_t acc = 0;
-            for (int t = 0; t <= warp; ++t) acc = mac<SMALL>(acc, Li[warp * B + t], D[(o + t) * K + j], p, mu);
+#pragma unroll 8
+            for (int t = 0; t < B; ++t) acc = mac<SMALL>(acc, Li[warp * S + t], D[(o + t) * K + j], p, mu);
             TU[warp * (K - B) + (j - o - B)] = red64(acc, p, mu);
         }
         __syncthreads();
@@ -836,8 +902,11 @@ __global__ void __launch_bounds__(kDiagThreads) diag_lu_kernel(uint32_t* A, int 
         }
     }
     __syncthreads();
-    for (int e = tid; e < K * K; e += kDiagThreads)
+#pragma unroll
+    for (int q = 0; q < K * K / kDiagThreads; ++q) {
+        const int e = tid + q * kDiagThreads;
         A[fm_encode((uint64_t)(r0 + e / K), (uint64_t)(c0 + e % K), lt)] = D[e];
+    }
     if (tid < K) dinv[tid] = dv[tid];
     if (tid == 0) *flag = 0;
 }
@@ -983,7 +1052,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         }
         // X = L11^-1 of each panel of the open block, Y = U11^-1 (the fast
         // path), 1 / U11(t, t), and the flags
-        xs_base = static_cast<uint32_t*>(fm_workspace(4, (size_t)((kOuter + 1) * kNb * kNb + kNb + 4) * 4));
+        xs_base = static_cast<uint32_t*>(fm_workspace(4, (size_t)((kOuter + 1) * kNb * kNb + kNb + 4 + 8 * 1024) * 4));
         if (!xs_base) return FM_ENOMEM;
         if (nbk == 0) {
             c_out = c0;
@@ -993,6 +1062,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         uint32_t* ys = xs_base + (size_t)kOuter * kNb * kNb;
         uint32_t* dinv = ys + kNb * kNb;
         int* d_flag = reinterpret_cast<int*>(dinv + kNb);
+        uint32_t* dgs = reinterpret_cast<uint32_t*>(d_flag + 4);  // diagonal 32 x 32 inverses
         const int64_t c_lim = std::min<int64_t>(c_out + (int64_t)kOuter * kNb, n);
         // after a panel with k pivots: the rest of the block's columns now, or,
         // when the panel ends the block, everything behind it
@@ -1002,7 +1072,44 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             if (!ends) return update_cols(r, k, Xm, c0 + w, c_lim);
             return finish_outer(c0 + w, c_lim, r + k);
         };
-        // a panel without a nonzero in rows [r, m) has no pivot: skip it
+        const size_t ismem = ((size_t)2 * kNb * kInvStride + 3 * 32 * 32) * 4;
+        // diagonal-block fast path, tried first: a full panel whose 128 diagonal
+        // pivots are nonzero (the rows the first-nonzero rule picks) factors
+        // without the column-by-column search
+        if (w == kNb && r + kNb <= m) {
+            const size_t dsmem = ((size_t)kNb * kNb + 2 * 32 * 33 + 32 * 32 + 2 * (kNb - 32) * 32) * 4;
+            auto dk = p < (1u << 16) ? diag_lu_kernel<true> : diag_lu_kernel<false>;
+            FM_CUDA_TRY(cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+            dk<<<1, kDiagThreads, dsmem, s>>>(Am.base, Am.log2_T, r, c0, p, mu, dinv, d_flag, dgs);
+            FM_CUDA_TRY(cudaGetLastError());
+            // both inverses right away (they return at once if the fast path
+            // failed), so that the device works while the host reads the flag
+            auto ik = p < (1u << 16) ? tri_inv2_kernel<true> : tri_inv2_kernel<false>;
+            FM_CUDA_TRY(cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+            ik<<<2, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv, d_flag, dgs);
+            FM_CUDA_TRY(cudaGetLastError());
+            int flag = 1;
+            FM_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (flag == 0) {
+                ++fast_panels;
+                for (int t = 0; t < kNb; ++t) pivot_pos.push_back((int)(c0 + t));
+                const fm_matrix Xm{xs, 0, 7}, Ym{ys, 0, 7};
+                if (r + kNb < m) {
+                    // L21 <- A21 U11^-1, over A21 itself (its planes are split before it is written)
+                    const fm_sub A21{Am, r + kNb, c0, m - r - kNb, kNb};
+                    FmLimbPlan lq;
+                    FM_TRY(fm_limb_plan(m - r - kNb, kNb, kNb, p, nullptr, &lq));
+                    void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
+                    if (!lws) return FM_ENOMEM;
+                    FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
+                }
+                FM_TRY(after_panel(kNb, Xm));
+                r += kNb;
+                continue;
+            }
+        }
+        // otherwise: a panel without a nonzero in rows [r, m) has no pivot: skip it
         {
             FM_CUDA_TRY(cudaMemsetAsync(d_flag + 1, 0, sizeof(int), s));
             const int64_t ctas = (m - r + 7) / 8;  // one warp per row, 8 warps a CTA
@@ -1016,41 +1123,6 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 ++zero_panels;
                 for (int t = 0; t < w; ++t) skipped_pos.push_back((int)(c0 + t));
                 FM_TRY(after_panel(0, fm_matrix{xs, 0, 7}));
-                continue;
-            }
-        }
-        const size_t ismem = ((size_t)2 * kNb * kNb + 3 * 32 * 32) * 4;
-        // diagonal-block fast path: a full panel whose 128 diagonal pivots are
-        // nonzero (the rows the first-nonzero rule picks) factors without the
-        // column-by-column search
-        if (w == kNb && r + kNb <= m) {
-            const size_t dsmem = ((size_t)kNb * kNb + 3 * 32 * 32 + 2 * (kNb - 32) * 32) * 4;
-            auto dk = p < (1u << 16) ? diag_lu_kernel<true> : diag_lu_kernel<false>;
-            FM_CUDA_TRY(cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-            dk<<<1, kDiagThreads, dsmem, s>>>(Am.base, Am.log2_T, r, c0, p, mu, dinv, d_flag);
-            FM_CUDA_TRY(cudaGetLastError());
-            int flag = 1;
-            FM_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-            FM_CUDA_TRY(cudaStreamSynchronize(s));
-            if (flag == 0) {
-                ++fast_panels;
-                for (int t = 0; t < kNb; ++t) pivot_pos.push_back((int)(c0 + t));
-                FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)ismem));
-                tri_inv2_kernel<<<2, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv);
-                FM_CUDA_TRY(cudaGetLastError());
-                const fm_matrix Xm{xs, 0, 7}, Ym{ys, 0, 7};
-                if (r + kNb < m) {
-                    // L21 <- A21 U11^-1, over A21 itself (its planes are split before it is written)
-                    const fm_sub A21{Am, r + kNb, c0, m - r - kNb, kNb};
-                    FmLimbPlan lq;
-                    FM_TRY(fm_limb_plan(m - r - kNb, kNb, kNb, p, nullptr, &lq));
-                    void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
-                    if (!lws) return FM_ENOMEM;
-                    FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
-                }
-                FM_TRY(after_panel(kNb, Xm));
-                r += kNb;
                 continue;
             }
         }
@@ -1173,9 +1245,9 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 perm_swaps_kernel<<<1, 32, 0, s>>>(row_perm, r, d_piv, w);
                 FM_CUDA_TRY(cudaGetLastError());
             }
-            FM_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ismem));
-            tri_inv_kernel<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
+            auto ik = p < (1u << 16) ? tri_inv_kernel<true> : tri_inv_kernel<false>;
+            FM_CUDA_TRY(cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+            ik<<<1, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, k, xs, 7, p, mu);
             FM_CUDA_TRY(cudaGetLastError());
         }
         FM_TRY(after_panel(k, fm_matrix{xs, 0, 7}));
