@@ -286,7 +286,7 @@ extern "C" int fm_gemm_modp(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op
     if (algo == FM_ALGO_LIMB_MMA_S8) return FM_EUNSUPPORTED;
     if (algo == FM_ALGO_LIMB_TC) {
         FmLimbPlan plan;
-        FM_TRY(fm_limb_plan(M, N, K, p, opts, &plan));
+        FM_TRY(fm_limb_plan_shaped(M, N, K, p, opts, &plan));
         void* ws = fm_workspace(0, fm_limb_workspace_bytes(plan));
         if (!ws) return FM_ENOMEM;
         fm_trace("gemm_modp limb M=%lld N=%lld K=%lld p=%u op=%d products=%d tiles=%d jobs/tile=%d planes=%zu B",
@@ -324,7 +324,7 @@ extern "C" int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uin
     algo = resolve_algo(C, A, B, algo);
     if (algo != FM_ALGO_LIMB_TC) return 0;
     FmLimbPlan plan;
-    rc = fm_limb_plan(C.rows, C.cols, A.cols, p, opts, &plan);
+    rc = fm_limb_plan_shaped(C.rows, C.cols, A.cols, p, opts, &plan);
     if (rc != FM_OK) return rc;
     return (int64_t)fm_limb_workspace_bytes(plan);
 }

@@ -39,6 +39,10 @@ struct FmLimbPlan {
 };
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan);
+// fm_limb_plan with the output tile width chosen from the shape when opts
+// leave it open (for callers that split and multiply with the same plan).
+int fm_limb_plan_shaped(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
+                        FmLimbPlan* plan);
 // GF(2) product on bit-packed operands: one E4M3 0/1 plane per operand (tiles of
 // 128 rows x 128 k bytes), one product, parity folded over p = 2 (gf2.cu splits,
 // limb_gemm.cu multiplies).

@@ -1089,6 +1089,29 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
     return FM_OK;
 }
 
+// fm_limb_plan with the output tile width chosen from the shape when the
+// caller leaves it open (fold form; the residue form always takes 128): the
+// width whose tiles take fewer rounds of the persistent grid, a round of
+// 128-wide tiles counting half of a 256-wide one, times 1.1 for K <= 1024
+// (the epilogue dominates) or 1.5 beyond (128-wide tiles run their MMAs
+// slower). Thin products -- N <= 384, or a single row block -- then take 128:
+// a 256-wide tile over 128 valid columns leaves half the epilogue warps idle,
+// and more, smaller tiles reach more SMs. Only for paths that split and
+// multiply with the same plan (the step-by-step limb API keeps fm_limb_plan).
+int fm_limb_plan_shaped(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts, FmLimbPlan* plan)
+{
+    FM_TRY(fm_limb_plan(M, N, K, p, opts, plan));
+    if (!plan->fold || (opts && (opts->block_n != 0 || opts->cta_pair == 1))) return FM_OK;
+    const int64_t sms = fm_sm_count(), mb = (M + kBM - 1) / kBM;
+    auto rounds = [&](int64_t bn) { return (mb * ((N + bn - 1) / bn) + sms - 1) / sms; };
+    const double c256 = 2.0 * (double)rounds(256);
+    const double c128 = (double)rounds(128) * (K <= 1024 ? 1.1 : 1.5);
+    if (c128 >= c256) return FM_OK;
+    fm_opts o = opts ? *opts : fm_opts{};
+    o.block_n = 128;
+    return fm_limb_plan(M, N, K, p, &o, plan);
+}
+
 int fm_gf2_plan(int64_t M, int64_t N, int64_t K, bool pair, FmLimbPlan* plan)
 {
     FmLimbPlan q;

@@ -986,7 +986,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
         if (op == FM_OP_SET) {
             FmLimbPlan lq;
-            FM_TRY(fm_limb_plan(C.rows, C.cols, Aop.cols, p, nullptr, &lq));
+            FM_TRY(fm_limb_plan_shaped(C.rows, C.cols, Aop.cols, p, nullptr, &lq));
             void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
             if (!lws) return FM_ENOMEM;
             return fm_limb_run(lq, C, Aop, Bop, p, FM_OP_SET, lws, status, s);
@@ -1099,7 +1099,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                     // L21 <- A21 U11^-1, over A21 itself (its planes are split before it is written)
                     const fm_sub A21{Am, r + kNb, c0, m - r - kNb, kNb};
                     FmLimbPlan lq;
-                    FM_TRY(fm_limb_plan(m - r - kNb, kNb, kNb, p, nullptr, &lq));
+                    FM_TRY(fm_limb_plan_shaped(m - r - kNb, kNb, kNb, p, nullptr, &lq));
                     void* lws = fm_workspace(0, fm_limb_workspace_bytes(lq));
                     if (!lws) return FM_ENOMEM;
                     FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
