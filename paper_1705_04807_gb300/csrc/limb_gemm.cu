@@ -138,12 +138,18 @@ __device__ __forceinline__ void write_gf2_run(const CView& c, int64_t gi, int64_
     }
 }
 
-template <int BN>
+// TWO: two CTAs per SM (fold form, 128-wide tiles): each holds only its two
+// 128-column accumulators (256 TMEM columns) and three 32 KB stages, so that
+// two fit on one SM; for short K, where every tile is mostly epilogue, one
+// CTA's drains and C update then overlap the other's MMAs, and the SM has
+// twice the epilogue warps to hide their latency.
+template <int BN, bool TWO = false>
 struct GemmCfg {
-    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr int kStages = TWO ? 3 : (BN == 256 ? 4 : 6);
     static constexpr uint32_t kBTileBytes = BN * 128;
     static constexpr uint32_t kStageBytes = kATileBytes + kBTileBytes;
     static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
+    static constexpr uint32_t kTmemCols = TWO ? 2 * BN : 512;
 };
 
 // Persistent: one CTA per SM walks the output tiles blockIdx.x, + gridDim.x, ...
@@ -154,11 +160,12 @@ struct GemmCfg {
 // kE4M3Gf2 = E4M3 0/1 planes (GF(2)), parity bits written to a bit-packed C.
 enum { kF16Res = 0, kE4M3Gf2 = 1 };
 
-template <int BN, bool FOLD, int KIND, bool BATCH>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+template <int BN, bool FOLD, int KIND, bool BATCH, bool TWO = false>
+__global__ void __launch_bounds__(kGemmThreads, TWO ? 2 : 1)
     limb_gemm_kernel(const __grid_constant__ LimbGemmArgs args)
 {
-    using Cfg = GemmCfg<BN>;
+    static_assert(!TWO || (FOLD && BN == 128 && KIND == kF16Res), "two CTAs per SM: fold form, 128-wide tiles");
+    using Cfg = GemmCfg<BN, TWO>;
     constexpr int S = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         s_consumed = 0;
     }
     if (warp == 1) {
-        fm_tmem_alloc(&tmem_slot, 512);
+        fm_tmem_alloc(&tmem_slot, Cfg::kTmemCols);
         fm_tmem_relinquish();
     }
     fm_tc_fence_before();
@@ -373,7 +380,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     while (t + 2 >= cl.first[idx2 + 1]) ++idx2;
                 const bool same_next = !last_on_buffer && idx2 == idx;
                 const uint32_t dbase = tmem + lane_base + (uint32_t)(b * BN) + col0;
-                if constexpr (FOLD) {
+                if constexpr (FOLD && TWO) {
+                    // two CTAs per SM: one 32-column chunk at a time (register budget)
+                    const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
+#pragma unroll 1
+                    for (int g = 0; g < n32; ++g) {
+                        uint32_t v0[32];
+                        fm_tmem_ld32(dbase + g * 32, v0);
+                        fm_tmem_wait_ld();
+                        if (same_next)
+                            fold_fp(v0, args.invp, args.pf);
+                        else
+                            fold_int(v0, mul, !last_on_buffer, p, args.invp, args.pf);
+                        fm_tmem_st32(dbase + g * 32, v0);
+                    }
+                } else if constexpr (FOLD) {
                     const uint32_t mul = last_on_buffer ? args.wt[idx] : args.cn[idx * 4 + idx2];
 #pragma unroll 1
                     for (int g = 0; g < (n32 + 1) / 2; ++g) {  // two 32-column chunks in flight
@@ -445,18 +466,34 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     // y <- x + y mod p, then x is free for the next tile's first job
                     const uint32_t xb = tmem + lane_base + (uint32_t)(bx * BN) + col0;
                     const uint32_t yb = tmem + lane_base + (uint32_t)(by * BN) + col0;
+                    if constexpr (TWO) {
 #pragma unroll 1
-                    for (int cc = 0; cc < n32; ++cc) {
-                        uint32_t xv[32], yv[32];
-                        fm_tmem_ld32(xb + cc * 32, xv);
-                        fm_tmem_ld32(yb + cc * 32, yv);
-                        fm_tmem_wait_ld();
+                        for (int cc = 0; cc < 2 * n32; ++cc) {
+                            uint32_t xv[16], yv[16];
+                            fm_tmem_ld16(xb + cc * 16, xv);
+                            fm_tmem_ld16(yb + cc * 16, yv);
+                            fm_tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const uint32_t x = xv[e] + yv[e];
-                            yv[e] = x >= p ? x - p : x;
+                            for (int e = 0; e < 16; ++e) {
+                                const uint32_t x = xv[e] + yv[e];
+                                yv[e] = x >= p ? x - p : x;
+                            }
+                            fm_tmem_st16(yb + cc * 16, yv);
                         }
-                        fm_tmem_st32(yb + cc * 32, yv);
+                    } else {
+#pragma unroll 1
+                        for (int cc = 0; cc < n32; ++cc) {
+                            uint32_t xv[32], yv[32];
+                            fm_tmem_ld32(xb + cc * 32, xv);
+                            fm_tmem_ld32(yb + cc * 32, yv);
+                            fm_tmem_wait_ld();
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const uint32_t x = xv[e] + yv[e];
+                                yv[e] = x >= p ? x - p : x;
+                            }
+                            fm_tmem_st32(yb + cc * 32, yv);
+                        }
                     }
                     fm_tmem_wait_st();
                     fm_tc_fence_before();
@@ -466,18 +503,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             } else {
                 rsrc = (uint32_t)(2 * BN);
             }
+            if constexpr (TWO) {
 #pragma unroll 1
-            for (int cc = 0; cc < n32; ++cc) {
-                uint32_t sres[32];
-                const uint32_t col = col0 + cc * 32;
-                fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
-                fm_tmem_wait_ld();
-                if (gi < cv.M) {
-                    if (KIND == kE4M3Gf2)
-                        write_gf2_run(cv, gi, (int64_t)nb * BN + col, sres);
-                    else
-                        write_c_run<32>(cv, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cv.c_lt) - 1,
+                for (int cc = 0; cc < 2 * n32; ++cc) {
+                    uint32_t sres[16];
+                    const uint32_t col = col0 + cc * 16;
+                    fm_tmem_ld16(tmem + lane_base + rsrc + col, sres);
+                    fm_tmem_wait_ld();
+                    if (gi < cv.M)
+                        write_c_run<16>(cv, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cv.c_lt) - 1,
                                         sres);
+                }
+            } else {
+#pragma unroll 1
+                for (int cc = 0; cc < n32; ++cc) {
+                    uint32_t sres[32];
+                    const uint32_t col = col0 + cc * 32;
+                    fm_tmem_ld32(tmem + lane_base + rsrc + col, sres);
+                    fm_tmem_wait_ld();
+                    if (gi < cv.M) {
+                        if (KIND == kE4M3Gf2)
+                            write_gf2_run(cv, gi, (int64_t)nb * BN + col, sres);
+                        else
+                            write_c_run<32>(cv, p, args.mu32, gi, (int64_t)nb * BN + col, (1ull << cv.c_lt) - 1,
+                                            sres);
+                    }
                 }
             }
             if (FOLD) {
@@ -497,7 +547,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     if (warp == 1) {
         fm_tc_fence_after();
-        fm_tmem_dealloc(tmem, 512);
+        fm_tmem_dealloc(tmem, Cfg::kTmemCols);
     }
 }
 
@@ -886,11 +936,17 @@ uint32_t invmod(uint32_t a, uint32_t m)
     return (uint32_t)(t % m);
 }
 
-template <int BN, bool FOLD, int KIND = kF16Res, bool BATCH = false>
+// Products with K up to this run the fold form's 128-wide tiles two CTAs per
+// SM (measured 17-20 % ahead of one CTA per SM from K = 128 to 4096; beyond,
+// three stages might not keep the MMAs fed, and the default there is 256-wide
+// tiles anyway).
+constexpr int64_t kTwoMaxK = 4096;
+
+template <int BN, bool FOLD, int KIND = kF16Res, bool BATCH = false, bool TWO = false>
 int launch_gemm(const LimbGemmArgs& a, int grid, cudaStream_t s)
 {
-    auto k = limb_gemm_kernel<BN, FOLD, KIND, BATCH>;
-    const size_t smem = GemmCfg<BN>::kSmem;
+    auto k = limb_gemm_kernel<BN, FOLD, KIND, BATCH, TWO>;
+    const size_t smem = GemmCfg<BN, TWO>::kSmem;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, kGemmThreads, smem, s>>>(a);
     FM_CUDA_TRY(cudaGetLastError());
@@ -1090,14 +1146,16 @@ int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opt
 }
 
 // fm_limb_plan with the output tile width chosen from the shape when the
-// caller leaves it open (fold form; the residue form always takes 128): the
-// width whose tiles take fewer rounds of the persistent grid, a round of
-// 128-wide tiles counting half of a 256-wide one, times 1.1 for K <= 1024
-// (the epilogue dominates) or 1.5 beyond (128-wide tiles run their MMAs
-// slower). Thin products -- N <= 384, or a single row block -- then take 128:
-// a 256-wide tile over 128 valid columns leaves half the epilogue warps idle,
-// and more, smaller tiles reach more SMs. Only for paths that split and
-// multiply with the same plan (the step-by-step limb API keeps fm_limb_plan).
+// caller leaves it open (fold form; the residue form always takes 128). For
+// K <= 1024 the tiles are 128 wide: every tile is then mostly epilogue, and
+// 128-wide tiles run two CTAs per SM (measured ahead of 256-wide tiles on
+// 384- to 11776-wide products). Beyond, the width whose tiles take fewer
+// rounds of the persistent grid, a round of 128-wide tiles counting half of a
+// 256-wide one times 1.5 (they run their MMAs slower): thin products -- a few
+// hundred columns, or a single row block -- then take 128 as well, since a
+// 256-wide tile over 128 valid columns leaves half the epilogue warps idle and
+// more, smaller tiles reach more SMs. Only for paths that split and multiply
+// with the same plan (the step-by-step limb API keeps fm_limb_plan).
 int fm_limb_plan_shaped(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts, FmLimbPlan* plan)
 {
     FM_TRY(fm_limb_plan(M, N, K, p, opts, plan));
@@ -1105,8 +1163,8 @@ int fm_limb_plan_shaped(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_op
     const int64_t sms = fm_sm_count(), mb = (M + kBM - 1) / kBM;
     auto rounds = [&](int64_t bn) { return (mb * ((N + bn - 1) / bn) + sms - 1) / sms; };
     const double c256 = 2.0 * (double)rounds(256);
-    const double c128 = (double)rounds(128) * (K <= 1024 ? 1.1 : 1.5);
-    if (c128 >= c256) return FM_OK;
+    const double c128 = (double)rounds(128) * 1.5;
+    if (K > 1024 && c128 >= c256) return FM_OK;
     fm_opts o = opts ? *opts : fm_opts{};
     o.block_n = 128;
     return fm_limb_plan(M, N, K, p, &o, plan);
@@ -1229,6 +1287,7 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
     const int grid = std::min(q.MB * q.NB, fm_sm_count());
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);
+        if (q.K <= kTwoMaxK) return launch_gemm<128, true, kF16Res, false, true>(a, std::min(q.MB * q.NB, 2 * fm_sm_count()), s);
         return launch_gemm<128, true>(a, grid, s);
     }
     return launch_gemm<128, false>(a, grid, s);
@@ -1264,6 +1323,7 @@ struct FmLimbBatch {
     LimbCall* d_calls = nullptr;
     int4* d_tiles = nullptr;
     int n_tiles = 0;
+    int max_kb = 0;                        // the longest call's 64-wide K stages
     bool gf2 = false;                      // bit-packed GF(2) operands
     FmFusedBatch* fused = nullptr;         // one launch, operands split on the fly
     std::vector<fm_gemm_call> zero_calls;  // K = 0: only FM_OP_SET changes C
@@ -1374,6 +1434,8 @@ int build_batch(const std::vector<BatchCall>& in, int bn, int kt, FmLimbBatch* b
     FM_TRY(upload_vec(lc, &b->d_calls));
     FM_TRY(upload_vec(sorted, &b->d_tiles));
     b->n_ajobs = (int64_t)aj.size();
+    b->max_kb = 0;
+    for (const LimbCall& c : lc) b->max_kb = std::max(b->max_kb, c.KB);
     b->n_bjobs = (int64_t)bj.size();
     b->n_tiles = (int)sorted.size();
     return FM_OK;
@@ -1516,6 +1578,8 @@ int fm_limb_batch_run(FmLimbBatch* b, int* status, cudaStream_t s)
     if (b->gf2) return launch_gemm<256, true, kE4M3Gf2, true>(a, grid, s);
     if (b->q.fold) {
         if (b->q.block_n == 256) return launch_gemm<256, true, kF16Res, true>(a, grid, s);
+        if ((int64_t)b->max_kb * kBK <= kTwoMaxK)
+            return launch_gemm<128, true, kF16Res, true, true>(a, std::min(b->n_tiles, 2 * fm_sm_count()), s);
         return launch_gemm<128, true, kF16Res, true>(a, grid, s);
     }
     return launch_gemm<128, false, kF16Res, true>(a, grid, s);

@@ -106,6 +106,18 @@ def test_limb_cta_pair_and_single_cta(env, orc, M, N, K):
             assert np.array_equal(got, want), (p, pair)
 
 
+@pytest.mark.parametrize("M,N,K", [(300, 520, 4096), (300, 520, 4097), (2560, 2048, 128), (129, 1000, 64)])
+def test_limb_fold_two_ctas_per_sm(env, orc, M, N, K):
+    # fold form on 128-wide tiles: two CTAs per SM up to K = 4096, one beyond;
+    # both sides of that bound, more tiles than the 2 x 152 resident CTAs, and
+    # a single row block
+    fm = env[0]
+    for p, op in ((P16, 2), (257, 0), (2, 1)):
+        got, want = run_case(env, orc, p, op, fm.FM_ALGO_LIMB_TC, M, N, K, (3, 0, 0, 5, 7, 0),
+                             (7, 6, 7), seed=K + p, options=fm.opts(0, 128, 0, -1))
+        assert np.array_equal(got, want), (p, op)
+
+
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (129, 130, 1000), (300, 520, 1000),
                                    (2560, 2048, 128), (1000, 3000, 200), (513, 257, 2100)])
 def test_limb_residue_cta_pair_and_single_cta(env, orc, M, N, K):
