@@ -36,6 +36,7 @@ struct FmLimbPlan {
     int gf2 = 0;      // 1: GF(2), one E4M3 plane per operand, 128 elements per K stage
     int MB, NB, KB;
     size_t a_plane_bytes, b_plane_bytes;  // bytes of ONE plane
+    int max_ctas = 0; // > 0: at most this many GEMM CTAs resident (leaves SMs to other streams)
 };
 int fm_limb_plan(int64_t M, int64_t N, int64_t K, uint32_t p, const fm_opts* opts,
                  FmLimbPlan* plan);

@@ -30,6 +30,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -1280,14 +1281,18 @@ int fm_limb_gemm_run(const FmLimbPlan& q, fm_sub C, const void* a_planes, const 
         if (q.pair) return launch_gemm_pair<kE4M3Gf2, true>(a, q.MB / 2 * q.NB, s);
         return launch_gemm<256, true, kE4M3Gf2>(a, std::min(q.MB * q.NB, fm_sm_count()), s);
     }
+    // q.max_ctas caps the resident CTAs (a persistent grid then walks more tiles each)
+    auto cap = [&](int ctas) { return q.max_ctas > 0 ? std::max(1, std::min(ctas, q.max_ctas)) : ctas; };
     if (q.pair) {
-        if (q.fold) return launch_gemm_pair<kF16Res, true>(a, q.MB / 2 * q.NB, s);
-        return launch_gemm_pair<kF16Res, false>(a, q.MB / 2 * q.NB, s);
+        const int pt = std::min(q.MB / 2 * q.NB, q.max_ctas > 0 ? std::max(1, q.max_ctas / 2) : INT_MAX);
+        if (q.fold) return launch_gemm_pair<kF16Res, true>(a, pt, s);
+        return launch_gemm_pair<kF16Res, false>(a, pt, s);
     }
-    const int grid = std::min(q.MB * q.NB, fm_sm_count());
+    const int grid = cap(std::min(q.MB * q.NB, fm_sm_count()));
     if (q.fold) {
         if (q.block_n == 256) return launch_gemm<256, true>(a, grid, s);
-        if (q.K <= kTwoMaxK) return launch_gemm<128, true, kF16Res, false, true>(a, std::min(q.MB * q.NB, 2 * fm_sm_count()), s);
+        if (q.K <= kTwoMaxK)
+            return launch_gemm<128, true, kF16Res, false, true>(a, cap(std::min(q.MB * q.NB, 2 * fm_sm_count())), s);
         return launch_gemm<128, true>(a, grid, s);
     }
     return launch_gemm<128, false>(a, grid, s);

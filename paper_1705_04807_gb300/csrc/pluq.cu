@@ -975,13 +975,88 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     // which has a quarter of the epilogue work of four K = 128 updates. A block
     // ends after a panel with fewer than 128 pivots (its pivot columns stay
     // contiguous: a panel moves its pivot columns in front of its skipped ones).
+    // Look-ahead: at the end of a block, stream s (the caller's) updates only
+    // the next block's columns and goes on with its panels; the columns behind
+    // those take the block's update on a second stream u, which waits (an event)
+    // for the block's panels on s. s waits for u before it touches those columns
+    // itself (at the next block's end), before row swaps of a searched panel
+    // (they reach every column) and before the final column permutation. u's
+    // products run in their own plane workspace on a capped number of CTAs, so
+    // that the panels' one-CTA kernels and thin products find SMs free;
+    // the panels' inverses X alternate between two sets by block parity (u reads
+    // a block's set while the next block writes the other).
     constexpr int kOuter = 4;
     int64_t c0 = 0, c_out = 0, r_out = 0;
     int nbk = 0;           // panels in the open outer block
     int bk[kOuter] = {0};  // pivots of each
+    int blk = 0;           // outer blocks opened so far
+    int cur_set = 0;       // the open block's set of inverses
     int fast_panels = 0, searched_panels = 0, zero_panels = 0;
+    struct LookAhead {
+        cudaStream_t u = nullptr;
+        cudaEvent_t ev_s = nullptr, ev_u = nullptr;
+        bool pending = false;  // work enqueued on u since s last waited for it
+        int64_t lo = 0;        // while pending: u may still write columns [lo, n)
+        int set = 0;           // while pending: the set of inverses u reads
+        ~LookAhead()
+        {
+            if (u) {
+                cudaStreamSynchronize(u);
+                cudaStreamDestroy(u);
+            }
+            if (ev_s) cudaEventDestroy(ev_s);
+            if (ev_u) cudaEventDestroy(ev_u);
+        }
+    } la;
+    FM_CUDA_TRY(cudaStreamCreateWithFlags(&la.u, cudaStreamNonBlocking));
+    FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_s, cudaEventDisableTiming));
+    FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_u, cudaEventDisableTiming));
+    auto wait_u = [&]() -> int {  // s waits for everything enqueued on u so far
+        if (!la.pending) return FM_OK;
+        FM_CUDA_TRY(cudaEventRecord(la.ev_u, la.u));
+        FM_CUDA_TRY(cudaStreamWaitEvent(s, la.ev_u, 0));
+        la.pending = false;
+        return FM_OK;
+    };
+    // u waits for everything enqueued on s so far, then takes columns [lo, n)
+    // (s has waited for u's earlier work before every call)
+    auto start_u = [&](int64_t lo) -> int {
+        FM_CUDA_TRY(cudaEventRecord(la.ev_s, s));
+        FM_CUDA_TRY(cudaStreamWaitEvent(la.u, la.ev_s, 0));
+        la.pending = true;
+        la.lo = lo;
+        la.set = cur_set;
+        return FM_OK;
+    };
+    // u's GEMM CTAs: 4/5 of the SM count (config 5: 120 of 152 took 30.5 ms,
+    // 202 -- spread over every SM, so that the one-CTA panel kernels, which take
+    // a whole SM's registers, wait for it -- 31.9 ms, 76 or fewer starve u)
+    const int u_ctas = std::max(2, sms * 4 / 5);
+    // plane workspaces sized once for the largest product (K = a block's pivots),
+    // so that neither stream's workspace is reallocated while the other runs
+    {
+        size_t most = 0;
+        for (int bn : {128, 256}) {
+            fm_opts o{};
+            o.block_n = bn;
+            FmLimbPlan lq;
+            if (fm_limb_plan(m, n, (int64_t)kOuter * kNb, p, &o, &lq) == FM_OK)
+                most = std::max(most, fm_limb_workspace_bytes(lq));
+        }
+        if (most && (!fm_workspace(0, most) || !fm_workspace(5, most))) return FM_ENOMEM;
+    }
     // C op A * B with every operand a sub-matrix of A (the limb product writes
     // C over the B operand when they are the same part: it splits B first)
+    // the same on the look-ahead stream, in its own workspace, on capped CTAs
+    auto product_u = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
+        if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
+        FmLimbPlan lq;
+        FM_TRY(fm_limb_plan_shaped(C.rows, C.cols, Aop.cols, p, nullptr, &lq));
+        lq.max_ctas = u_ctas;
+        void* lws = fm_workspace(5, fm_limb_workspace_bytes(lq));
+        if (!lws) return FM_ENOMEM;
+        return fm_limb_run(lq, C, Aop, Bop, p, op, lws, status, la.u);
+    };
     auto product = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
         if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
         if (op == FM_OP_SET) {
@@ -996,49 +1071,71 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     // After a panel with k pivots in rows [r_, r_ + k) and columns [c0, c0 + k):
     // U12 <- L11^-1 A12 (X = L11^-1) and A22 <- A22 - L21 U12 on columns
     // [c_from, c_to).
-    auto update_cols = [&](int64_t r_, int k_, fm_matrix Xm, int64_t c_from, int64_t c_to) -> int {
+    auto update_cols = [&](int64_t r_, int k_, fm_matrix Xm, int64_t c_from, int64_t c_to, bool on_u = false) -> int {
         if (c_from >= c_to || k_ == 0) return FM_OK;
         const int64_t cols = c_to - c_from;
         const fm_sub A12{Am, r_, c_from, k_, cols};
-        FM_TRY(product(A12, fm_sub{Xm, 0, 0, k_, k_}, A12, FM_OP_SET));
-        return product(fm_sub{Am, r_ + k_, c_from, m - r_ - k_, cols}, fm_sub{Am, r_ + k_, c0, m - r_ - k_, k_},
-                       A12, FM_OP_SUB);
+        auto prod = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) {
+            return on_u ? product_u(C, Aop, Bop, op) : product(C, Aop, Bop, op);
+        };
+        FM_TRY(prod(A12, fm_sub{Xm, 0, 0, k_, k_}, A12, FM_OP_SET));
+        return prod(fm_sub{Am, r_ + k_, c_from, m - r_ - k_, cols}, fm_sub{Am, r_ + k_, c0, m - r_ - k_, k_}, A12,
+                    FM_OP_SUB);
     };
-    uint32_t* xs_base = nullptr;  // X of each panel of the open block (set per panel below)
+    uint32_t* xs_base = nullptr;  // X of each panel, two sets of kOuter (set per panel below)
     // Closes the open block after its last panel (ending at column c_end, rows
     // up to r_now). Columns [c_end, c_lim) -- the block's own columns behind
     // that panel, when the block ended early -- already hold the updates of
     // the block's earlier panels and take only the last panel's; columns
-    // [c_lim, n) take the whole block's.
+    // [c_lim, n) take the whole block's: on s up to la_end, the end of the next
+    // block's columns, and on u beyond.
     auto finish_outer = [&](int64_t c_end, int64_t c_lim, int64_t r_now) -> int {
         const int n_bk = nbk;
         nbk = 0;
         const int64_t k_out = r_now - r_out;
         if (k_out == 0) return FM_OK;
+        uint32_t* xset = xs_base + (size_t)cur_set * kOuter * kNb * kNb;
+        const int64_t la_end = std::min<int64_t>(n, c_end + (int64_t)kOuter * kNb);
+        FM_TRY(wait_u());  // u's columns of the previous block are about to be touched
         const int k_last = bk[n_bk - 1];
         if (n_bk == 1) {  // a block of one panel: no column has any of its update yet
-            const fm_matrix X0{xs_base, 0, 7};
-            return update_cols(r_out, k_last, X0, c_end, n);
+            const fm_matrix X0{xset, 0, 7};
+            FM_TRY(update_cols(r_out, k_last, X0, c_end, la_end));
+            if (la_end >= n) return FM_OK;
+            FM_TRY(start_u(la_end));
+            return update_cols(r_out, k_last, X0, la_end, n, true);
         }
         if (c_end < c_lim && k_last > 0) {
-            const fm_matrix Xl{xs_base + (size_t)(n_bk - 1) * kNb * kNb, 0, 7};
+            const fm_matrix Xl{xset + (size_t)(n_bk - 1) * kNb * kNb, 0, 7};
             FM_TRY(update_cols(r_now - k_last, k_last, Xl, c_end, c_lim));
         }
         c_end = std::max(c_end, c_lim);
-        if (c_end >= n) return FM_OK;
-        const int64_t cols = n - c_end;
-        for (int i = 0; i < n_bk; ++i) {
-            if (bk[i] == 0) continue;
-            const int64_t ri = r_out + (int64_t)kNb * i;
-            const fm_sub Ai{Am, ri, c_end, bk[i], cols};
-            if (i > 0)
-                FM_TRY(product(Ai, fm_sub{Am, ri, c_out, bk[i], (int64_t)kNb * i},
-                               fm_sub{Am, r_out, c_end, (int64_t)kNb * i, cols}, FM_OP_SUB));
-            const fm_matrix Xi{xs_base + (size_t)i * kNb * kNb, 0, 7};
-            FM_TRY(product(Ai, fm_sub{Xi, 0, 0, bk[i], bk[i]}, Ai, FM_OP_SET));
-        }
-        return product(fm_sub{Am, r_now, c_end, m - r_now, cols}, fm_sub{Am, r_now, c_out, m - r_now, k_out},
-                       fm_sub{Am, r_out, c_end, k_out, cols}, FM_OP_SUB);
+        // columns [lo, hi): U12 <- L11^-1 A12 by block forward substitution over
+        // the block's panels, then A22 <- A22 - L21 U12 with K = the block's pivots
+        auto block_cols = [&](int64_t lo, int64_t hi, bool on_u) -> int {
+            if (lo >= hi) return FM_OK;
+            auto prod = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) {
+                return on_u ? product_u(C, Aop, Bop, op) : product(C, Aop, Bop, op);
+            };
+            const int64_t cols = hi - lo;
+            for (int i = 0; i < n_bk; ++i) {
+                if (bk[i] == 0) continue;
+                const int64_t ri = r_out + (int64_t)kNb * i;
+                const fm_sub Ai{Am, ri, lo, bk[i], cols};
+                if (i > 0)
+                    FM_TRY(prod(Ai, fm_sub{Am, ri, c_out, bk[i], (int64_t)kNb * i},
+                                fm_sub{Am, r_out, lo, (int64_t)kNb * i, cols}, FM_OP_SUB));
+                const fm_matrix Xi{xset + (size_t)i * kNb * kNb, 0, 7};
+                FM_TRY(prod(Ai, fm_sub{Xi, 0, 0, bk[i], bk[i]}, Ai, FM_OP_SET));
+            }
+            return prod(fm_sub{Am, r_now, lo, m - r_now, cols}, fm_sub{Am, r_now, c_out, m - r_now, k_out},
+                        fm_sub{Am, r_out, lo, k_out, cols}, FM_OP_SUB);
+        };
+        const int64_t mid = std::max(c_end, la_end);
+        FM_TRY(block_cols(c_end, mid, false));
+        if (mid >= n) return FM_OK;
+        FM_TRY(start_u(mid));
+        return block_cols(mid, n, true);
     };
     std::vector<int> colid((size_t)n);  // original column at each storage position
     for (int64_t j = 0; j < n; ++j) colid[(size_t)j] = (int)j;
@@ -1052,18 +1149,25 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         }
         // X = L11^-1 of each panel of the open block, Y = U11^-1 (the fast
         // path), 1 / U11(t, t), and the flags
-        xs_base = static_cast<uint32_t*>(fm_workspace(4, (size_t)((kOuter + 1) * kNb * kNb + kNb + 4 + 8 * 1024) * 4));
+        xs_base = static_cast<uint32_t*>(
+            fm_workspace(4, (size_t)((2 * kOuter + 1) * kNb * kNb + kNb + 4 + 8 * 1024) * 4));
         if (!xs_base) return FM_ENOMEM;
         if (nbk == 0) {
             c_out = c0;
             r_out = r;
+            cur_set = (blk++) & 1;
+            if (la.pending && la.set == cur_set) FM_TRY(wait_u());  // u still reads this set
         }
-        uint32_t* xs = xs_base + (size_t)nbk * kNb * kNb;
-        uint32_t* ys = xs_base + (size_t)kOuter * kNb * kNb;
+        uint32_t* xs = xs_base + ((size_t)cur_set * kOuter + nbk) * kNb * kNb;
+        uint32_t* ys = xs_base + (size_t)2 * kOuter * kNb * kNb;
         uint32_t* dinv = ys + kNb * kNb;
         int* d_flag = reinterpret_cast<int*>(dinv + kNb);
         uint32_t* dgs = reinterpret_cast<uint32_t*>(d_flag + 4);  // diagonal 32 x 32 inverses
         const int64_t c_lim = std::min<int64_t>(c_out + (int64_t)kOuter * kNb, n);
+        // this panel and its block's updates touch columns [c0, c_lim): u must
+        // be done with them (a block that follows an all-zero one starts past
+        // the columns the previous block end left to s)
+        if (la.pending && c_lim > la.lo) FM_TRY(wait_u());
         // after a panel with k pivots: the rest of the block's columns now, or,
         // when the panel ends the block, everything behind it
         auto after_panel = [&](int k, fm_matrix Xm) -> int {
@@ -1127,6 +1231,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             }
         }
         ++searched_panels;
+        FM_TRY(wait_u());  // its row swaps reach every column
         std::vector<int> slots(kNb, INT_MAX);
         FM_CUDA_TRY(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int) * kNb, cudaMemcpyHostToDevice, s));
         // panel rows resident in shared memory when a CTA's share fits
@@ -1253,6 +1358,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         FM_TRY(after_panel(k, fm_matrix{xs, 0, 7}));
         r += k;
     }
+    FM_TRY(wait_u());
     // move every skipped column behind all pivot columns
     std::vector<int> final_order(pivot_pos);
     final_order.insert(final_order.end(), skipped_pos.begin(), skipped_pos.end());
