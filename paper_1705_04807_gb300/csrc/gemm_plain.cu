@@ -5,7 +5,8 @@
 // whole tiles of A and B that the piece touches -- each one a contiguous
 // T'^2 block of the Morton-hybrid array, thanks to the aligned/contained
 // decomposition (Prop. of Sec. 2.1) -- with one 1-D bulk copy (TMA) per tile
-// into shared memory, double-buffered on mbarriers. Inside a staged tile the
+// into shared memory, in a ring of kPlainStages<T'> stages on mbarriers (four
+// of 16 KB at T' = 32, two of 64 KB at T' = 64). Inside a staged tile the
 // element (u, v) is at u*T' + v (Sec. 2.1, P2), so the inner loop is a plain
 // row-major product.
 //
@@ -89,6 +90,15 @@ __device__ __forceinline__ uint32_t combine(uint32_t c, uint32_t s, uint32_t p, 
     return cc >= s ? cc - s : cc + (p - s);
 }
 
+// Stages of the copy ring: at T' = 32 a stage (up to four tiles) is 16 KB, so
+// four fit in 64 KB and keep three pieces' copies in flight behind the one
+// being multiplied; at T' = 64 two stages already take 128 KB.
+template <int LT>
+__host__ __device__ constexpr int plain_stages()
+{
+    return LT == 5 ? 4 : 2;
+}
+
 template <int LT, int ARITH>
 __global__ void __launch_bounds__(4 << LT)
     plain_kernel(const FmCallDesc* __restrict__ calls, const FmWorkItem* __restrict__ items,
@@ -102,10 +112,11 @@ __global__ void __launch_bounds__(4 << LT)
     constexpr int RPW = 8;                // output rows per warp
     constexpr int CPL = T / 32;           // output columns per lane
     constexpr uint32_t kTileBytes = TE * 4;
+    constexpr int S = plain_stages<LT>();
 
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    uint32_t* tiles = reinterpret_cast<uint32_t*>(smem_raw);  // [2 stages][4 tiles][TE]
-    __shared__ __align__(8) uint64_t full[2];
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(smem_raw);  // [S stages][4 tiles][TE]
+    __shared__ __align__(8) uint64_t full[S];
     __shared__ int s_item;
     __shared__ int s_abort;
 
@@ -113,8 +124,7 @@ __global__ void __launch_bounds__(4 << LT)
     const int warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        fm_mbar_init(&full[0], 1);
-        fm_mbar_init(&full[1], 1);
+        for (int s = 0; s < S; ++s) fm_mbar_init(&full[s], 1);
         fm_fence_mbar_init();
         s_abort = 0;
     }
@@ -150,10 +160,8 @@ __global__ void __launch_bounds__(4 << LT)
                             &full[buf]);
         };
 
-        if (tid == 0) {
-            if (n > 0) issue(0, g & 1);
-            if (n > 1) issue(1, (g + 1) & 1);
-        }
+        if (tid == 0)
+            for (int q = 0; q < n && q < S; ++q) issue(q, (g + q) % S);
 
         // my rows and columns inside the output part
         int my_r[RPW], my_c[CPL];
@@ -170,8 +178,8 @@ __global__ void __launch_bounds__(4 << LT)
 
         for (int q = 0; q < n; ++q) {
             const uint32_t gq = g + q;
-            const uint32_t buf = gq & 1;
-            if (!fm_mbar_wait(&full[buf], (gq >> 1) & 1, status, &s_abort)) break;
+            const uint32_t buf = gq % S;
+            if (!fm_mbar_wait(&full[buf], (gq / S) & 1, status, &s_abort)) break;
             const FmLPiece lp = lps[cd.lp_begin + q];
             const uint32_t* st = tiles + (size_t)buf * 4 * TE;
             // row pointers into A, column pointers into B (clamped for idle lanes)
@@ -238,13 +246,13 @@ __global__ void __launch_bounds__(4 << LT)
                 }
             }
             __syncthreads();  // every thread is done with this buffer
-            if (tid == 0 && q + 2 < n) issue(q + 2, buf);
+            if (tid == 0 && q + S < n) issue(q + S, buf);
         }
         if (s_abort) {
             // let copies still in flight land before the CTA exits
             if (tid == 0)
-                for (int q = 0; q < n && q < 2; ++q)
-                    fm_mbar_wait(&full[(g + q) & 1], ((g + q) >> 1) & 1, status, nullptr);
+                for (int q = 0; q < n && q < S; ++q)
+                    fm_mbar_wait(&full[(g + q) % S], ((g + q) / S) & 1, status, nullptr);
             break;
         }
         g += n;
@@ -273,7 +281,7 @@ int launch_t(const FmCallDesc* calls, const FmWorkItem* items, const FmLPiece* l
              int64_t n_items, uint32_t p, int* queue, int grid, int* status, cudaStream_t s)
 {
     constexpr int T = 1 << LT;
-    const size_t smem = (size_t)2 * 4 * T * T * 4;
+    const size_t smem = (size_t)plain_stages<LT>() * 4 * T * T * 4;
     auto k = plain_kernel<LT, ARITH>;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, 4 << LT, smem, s>>>(calls, items, lps, n_items, p, queue, status);
@@ -304,7 +312,7 @@ int fm_plain_occupancy(int lt, int arith)
 {
     int blocks = 1;
     const int T = 1 << lt;
-    const size_t smem = (size_t)2 * 4 * T * T * 4;
+    const size_t smem = (size_t)(lt == 5 ? plain_stages<5>() : plain_stages<6>()) * 4 * T * T * 4;
 #define FM_OCC(L, A)                                                                             \
     if (lt == L && arith == A) {                                                                 \
         cudaFuncSetAttribute(plain_kernel<L, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
