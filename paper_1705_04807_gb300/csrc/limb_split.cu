@@ -133,7 +133,11 @@ __device__ __forceinline__ void load8_morton(const uint32_t* __restrict__ base, 
 }
 
 // A (M x K) -> w planes of [MB][KB] tiles, each 128 rows x 64 k f16, swizzled.
-// One CTA writes tile (mb, kb) of every plane.
+// One CTA writes tile (mb, kb) of every plane. Rows at or past M are not
+// written: a row of the product depends on its own row of A only, and the
+// GEMM writes no output row past M (whatever such a plane row holds only
+// reaches accumulator rows that are never stored). Columns past K inside the
+// last K tile are written as zeros: they enter every row's sums.
 template <int W, bool KARA>
 __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int lt, int64_t row0,
                                              int64_t col0, int64_t M, int64_t K, int KB, int tile, uint32_t p,
@@ -154,6 +158,7 @@ __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int
     for (int it = 0; it < kIters; ++it) {
         const int c = threadIdx.x + it * kSplitThreads;
         const int r = c >> 3, kc = c & 7;
+        if ((int64_t)mb * kBM + r >= M) continue;
         int d[8][4];
 #pragma unroll
         for (int e = 0; e < 8; ++e) limb_digits<W>(x[it][e], p, hi, d[e]);
@@ -164,7 +169,9 @@ __device__ __forceinline__ void split_a_tile(const uint32_t* __restrict__ A, int
 // B (K x N) -> w planes of [NB][KB] tiles, each BN rows (n) x 64 k f16 (B
 // transposed to K-major), swizzled. Staged through shared memory so that both
 // the Morton reads (along n, 16-byte vectors) and the tile writes (along k)
-// are coalesced. One CTA writes tile (nb, kb) of every plane.
+// are coalesced. One CTA writes tile (nb, kb) of every plane; rows n at or
+// past N are not written (they reach only output columns that are never
+// stored), k past K is written as zeros.
 template <int BN, int W, bool KARA>
 __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int lt, int64_t row0,
                                              int64_t col0, int64_t K, int64_t N, int KB, int tile, uint32_t p,
@@ -216,7 +223,8 @@ __device__ __forceinline__ void split_b_tile(const uint32_t* __restrict__ B, int
     // store covers 512 contiguous bytes of the tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kc = lane & 7;
-    for (int n = warp * 4 + (lane >> 3); n < BN; n += kSplitThreads / 8) {
+    const int n_end = (int)min((int64_t)BN, N - (int64_t)nb * BN);
+    for (int n = warp * 4 + (lane >> 3); n < n_end; n += kSplitThreads / 8) {
         int d[8][4];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
