@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the small, Schur-update and 31-bit workloads")
     ap.add_argument("--case", default=None,
-                    choices=["gemm", "gemm_p31", "permute", "to_morton_permuted", "tu", "batch"],
+                    choices=["gemm", "gemm_p31", "gemm_plain", "permute", "to_morton_permuted", "tu", "batch"],
                     help="profiling aid: run one kernel's call --steps times at --n (T' = --T) after "
                          "--warmup calls, print nothing else, exit")
     ap.add_argument("--T", type=int, default=128, help="T' of the --case matrices")
@@ -1116,8 +1116,9 @@ def run_fm(args, world, rank, local):
 
 def run_case(args):
     """One kernel's call, repeated, for an ncu capture of a small case: the limb
-    GEMM (C = A*B mod 65521 or mod 2^31 - 1, n^3), the Morton-to-Morton row and
-    column permutation, or the permuted row-major -> Morton conversion (n x n)."""
+    GEMM (C = A*B mod 65521 or mod 2^31 - 1, n^3), the plain CUDA-core GEMM
+    (mod 65521, n^3, T' = --T), the Morton-to-Morton row and column permutation,
+    or the permuted row-major -> Morton conversion (n x n)."""
     import numpy as np
     import torch
 
@@ -1174,11 +1175,11 @@ def run_case(args):
         fm.fm_layout_to_morton(x, n, n, n, m)
         return x, t, m
 
-    if args.case in ("gemm", "gemm_p31"):
+    if args.case in ("gemm", "gemm_p31", "gemm_plain"):
         mats = [morton(1, q) for q in range(3)]
         subs = [fm.sub(m, 0, 0, n, n) for _, _, m in mats]
-        call = lambda: fm.fm_gemm_modp(subs[0], subs[1], subs[2], p, fm.FM_OP_SUB,  # noqa: E731
-                                       fm.FM_ALGO_LIMB_TC)
+        algo = fm.FM_ALGO_PLAIN if args.case == "gemm_plain" else fm.FM_ALGO_LIMB_TC
+        call = lambda: fm.fm_gemm_modp(subs[0], subs[1], subs[2], p, fm.FM_OP_SUB, algo)  # noqa: E731
     else:
         x, t0, m0 = morton(1, 0)
         t1 = torch.empty_like(t0)
