@@ -1088,7 +1088,15 @@ def run_fm(args, world, rank, local):
     if "batched" in out:
         line["batched"] = out["batched"]
     if "tu" in out:
-        line["tu"] = out["tu"]
+        # the elimination work against the limb GEMM's modular rate measured in
+        # this run (n^3 products at the step's size): the rate a factorization
+        # would reach if all of its work ran as that GEMM
+        tu = dict(out["tu"])
+        tu["roofline"] = {"bound": "limb GEMM rate", "achieved": tu["value"],
+                          "peak": roofline["modular_gops"], "unit": "Gop/s",
+                          "frac": tu["value"] / roofline["modular_gops"],
+                          "peak_source": f"limb GEMM in this run, n={n}, p={p}"}
+        line["tu"] = tu
     if "gf2" in out:
         line["gf2"] = out["gf2"]
     if "configs" in out:
