@@ -994,7 +994,8 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     int fast_panels = 0, searched_panels = 0, zero_panels = 0;
     struct LookAhead {
         cudaStream_t u = nullptr;
-        cudaEvent_t ev_s = nullptr, ev_u = nullptr;
+        cudaEvent_t ev_s = nullptr, ev_u = nullptr, ev_flag = nullptr;
+        int* h_flag = nullptr;  // pinned: the fast path's flag arrives without blocking the host
         bool pending = false;  // work enqueued on u since s last waited for it
         int64_t lo = 0;        // while pending: u may still write columns [lo, n)
         int set = 0;           // while pending: the set of inverses u reads
@@ -1006,11 +1007,15 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             }
             if (ev_s) cudaEventDestroy(ev_s);
             if (ev_u) cudaEventDestroy(ev_u);
+            if (ev_flag) cudaEventDestroy(ev_flag);
+            if (h_flag) cudaFreeHost(h_flag);
         }
     } la;
     FM_CUDA_TRY(cudaStreamCreateWithFlags(&la.u, cudaStreamNonBlocking));
     FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_s, cudaEventDisableTiming));
     FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_u, cudaEventDisableTiming));
+    FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_flag, cudaEventDisableTiming));
+    FM_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&la.h_flag), sizeof(int), cudaHostAllocDefault));
     auto wait_u = [&]() -> int {  // s waits for everything enqueued on u so far
         if (!la.pending) return FM_OK;
         FM_CUDA_TRY(cudaEventRecord(la.ev_u, la.u));
@@ -1186,15 +1191,18 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             FM_CUDA_TRY(cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
             dk<<<1, kDiagThreads, dsmem, s>>>(Am.base, Am.log2_T, r, c0, p, mu, dinv, d_flag, dgs);
             FM_CUDA_TRY(cudaGetLastError());
-            // both inverses right away (they return at once if the fast path
-            // failed), so that the device works while the host reads the flag
+            // the flag goes to the host right behind the block; both inverses
+            // run meanwhile (they return at once if the fast path failed), and
+            // the host, which waits for the flag only, queues what follows
+            // while they run
+            FM_CUDA_TRY(cudaMemcpyAsync(la.h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FM_CUDA_TRY(cudaEventRecord(la.ev_flag, s));
             auto ik = p < (1u << 16) ? tri_inv2_kernel<true> : tri_inv2_kernel<false>;
             FM_CUDA_TRY(cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
             ik<<<2, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv, d_flag, dgs);
             FM_CUDA_TRY(cudaGetLastError());
-            int flag = 1;
-            FM_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-            FM_CUDA_TRY(cudaStreamSynchronize(s));
+            FM_CUDA_TRY(cudaEventSynchronize(la.ev_flag));
+            const int flag = *la.h_flag;
             if (flag == 0) {
                 ++fast_panels;
                 for (int t = 0; t < kNb; ++t) pivot_pos.push_back((int)(c0 + t));
