@@ -131,6 +131,32 @@ def _trace_pluq(env, A, p, lt, tmp_path):
     return out, fast, searched, zero
 
 
+@pytest.mark.parametrize("case", ["searched_after_block", "low_rank_after_blocks"])
+def test_pluq_look_ahead_stream(env, orc, tmp_path, case):
+    # Behind the first outer block (columns 0..511) the look-ahead stream still
+    # updates columns 1024.. while the next block's panels factor. Then (a) a zero
+    # diagonal pivot at column 650 (row 650 repeats row 5 in the leading 651
+    # columns) sends panel 5 to the search, whose row swaps reach every column
+    # and must wait for that stream; (b) rank 700: after block 1 ends early the
+    # panels past the rank start blocks further right, whose columns the stream
+    # may still hold. Both against the oracle's rank and P A Q = L U.
+    p, lt, m, n = P16, 6, 1200, 1400
+    if case == "searched_after_block":
+        A = fm_inputs.uniform_residues(13, (m, n), p)
+        A[650, :651] = A[5, :651]
+    else:
+        X, Y = low_rank(14, m, n, 700, p)
+        A = orc.gemm_modp(None, X, Y, p, 0)
+    (r, F, rp, cp), fast, searched, zero = _trace_pluq(env, A, p, lt, tmp_path)
+    _, _, _, _, r_oracle = orc.pluq(A, p)
+    assert r == r_oracle
+    check_factors(orc, A, p, r, F, rp, cp)
+    if case == "searched_after_block":
+        assert searched >= 1 and fast >= 8
+    else:
+        assert zero >= 4
+
+
 @pytest.mark.parametrize("case", ["dense", "zero_first_pivot", "zero_mid_pivot", "tiny_field", "low_rank"])
 def test_pluq_diagonal_block_and_search_paths(env, orc, tmp_path, case):
     # A full panel whose 128 diagonal pivots are nonzero factors by the
