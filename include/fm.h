@@ -249,8 +249,8 @@ int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K
  * library (every GPU that loads it holds that array until the process exits).
  * A product whose limb planes need more than 64 MiB returns FM_ETOOBIG (e.g.
  * M = N = K = 2048 fits for p < 2^16; the planes take 6 * K * (M + N) bytes for
- * odd p < 2^16 with three planes, 8 * K * (M + N) for p = 2^31 - 1, rounded up
- * to whole tiles). Calls with M, N or K equal to 0 touch no scratch (K = 0
+ * odd p < 2^16 with three planes, 20 * K * (M + N) for p = 2^31 - 1 with ten
+ * (four limbs and their six pair sums), rounded up to whole tiles). Calls with M, N or K equal to 0 touch no scratch (K = 0
  * with FM_OP_SET zeroes the C sub-matrix; with ADD or SUB it leaves C as is).
  * The first call on a device that multiplies (K > 0) does that device's
  * one-time set-up: it looks up the array's device address and queries how
@@ -272,9 +272,13 @@ int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, f
  * >= r outside L are zero); row_perm (device, m) and col_perm (device, n) are
  * gathers: (P A Q)(i, j) = A_in(row_perm[i], col_perm[j]). *rank (host) gets r.
  * Blocked right-looking elimination with 128-column panels (first-nonzero
- * pivoting, zero columns moved behind the pivot columns); every trailing
- * update is one fm_gemm_modp call (C <- C - L21 * U12 on sub-matrices of A).
- * p must be prime; n <= 51200. Synchronous: returns after the factorisation.
+ * pivoting, zero columns moved behind the pivot columns) grouped four to an
+ * outer block; the trailing updates are limb products on sub-matrices of A
+ * (C <- C - L21 * U12). The bulk of each outer block's update runs on a second
+ * stream the call creates (ordered against `stream` by events) while the next
+ * block's panels factor on `stream`; the call also holds a 4-byte pinned host
+ * buffer for the panels' flags. p must be prime; n <= 51200. Synchronous:
+ * returns after the factorisation, with both streams idle.
  * The paper defers the TU algorithm itself (TURBO) to its reference; this is
  * the textbook elimination that produces the same kind of result. */
 int fm_pluq(fm_matrix A, int64_t m, int64_t n, uint32_t p, int32_t* row_perm, int32_t* col_perm,
