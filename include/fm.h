@@ -276,8 +276,9 @@ int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, f
  * outer block; the trailing updates are limb products on sub-matrices of A
  * (C <- C - L21 * U12). The bulk of each outer block's update runs on a second
  * stream the call creates (ordered against `stream` by events) while the next
- * block's panels factor on `stream`; the call also holds a 4-byte pinned host
- * buffer for the panels' flags. p must be prime; n <= 51200. Synchronous:
+ * block's panels factor on `stream`, and a panel's U12 product on a third one
+ * beside its L21 product; the call also holds a 4-byte pinned host buffer for
+ * the panels' flags. p must be prime; n <= 51200. Synchronous:
  * returns after the factorisation, with both streams idle.
  * The paper defers the TU algorithm itself (TURBO) to its reference; this is
  * the textbook elimination that produces the same kind of result. */

@@ -18,12 +18,12 @@
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kSlots = 6;
+constexpr int kSlots = 7;
 
 struct DeviceState {
     int* status = nullptr;
-    void* ws[kSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t ws_bytes[kSlots] = {0, 0, 0, 0, 0, 0};
+    void* ws[kSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t ws_bytes[kSlots] = {0, 0, 0, 0, 0, 0, 0};
     int sm_count = 0;
 };
 

@@ -994,6 +994,8 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
     int fast_panels = 0, searched_panels = 0, zero_panels = 0;
     struct LookAhead {
         cudaStream_t u = nullptr;
+        cudaStream_t v = nullptr;  // side stream: a panel row's product beside its L21 product
+        cudaEvent_t ev_v0 = nullptr, ev_v1 = nullptr;
         cudaEvent_t ev_s = nullptr, ev_u = nullptr, ev_flag = nullptr;
         int* h_flag = nullptr;  // pinned: the fast path's flag arrives without blocking the host
         bool pending = false;  // work enqueued on u since s last waited for it
@@ -1005,6 +1007,12 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 cudaStreamSynchronize(u);
                 cudaStreamDestroy(u);
             }
+            if (v) {
+                cudaStreamSynchronize(v);
+                cudaStreamDestroy(v);
+            }
+            if (ev_v0) cudaEventDestroy(ev_v0);
+            if (ev_v1) cudaEventDestroy(ev_v1);
             if (ev_s) cudaEventDestroy(ev_s);
             if (ev_u) cudaEventDestroy(ev_u);
             if (ev_flag) cudaEventDestroy(ev_flag);
@@ -1012,6 +1020,9 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         }
     } la;
     FM_CUDA_TRY(cudaStreamCreateWithFlags(&la.u, cudaStreamNonBlocking));
+    FM_CUDA_TRY(cudaStreamCreateWithFlags(&la.v, cudaStreamNonBlocking));
+    FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_v0, cudaEventDisableTiming));
+    FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_v1, cudaEventDisableTiming));
     FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_s, cudaEventDisableTiming));
     FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_u, cudaEventDisableTiming));
     FM_CUDA_TRY(cudaEventCreateWithFlags(&la.ev_flag, cudaEventDisableTiming));
@@ -1048,10 +1059,20 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             if (fm_limb_plan(m, n, (int64_t)kOuter * kNb, p, &o, &lq) == FM_OK)
                 most = std::max(most, fm_limb_workspace_bytes(lq));
         }
-        if (most && (!fm_workspace(0, most) || !fm_workspace(5, most))) return FM_ENOMEM;
+        if (most && (!fm_workspace(0, most) || !fm_workspace(5, most) || !fm_workspace(6, most)))
+            return FM_ENOMEM;
     }
     // C op A * B with every operand a sub-matrix of A (the limb product writes
     // C over the B operand when they are the same part: it splits B first)
+    // the panel row's product on the side stream v, in a workspace of its own
+    auto product_v = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
+        if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
+        FmLimbPlan lq;
+        FM_TRY(fm_limb_plan_shaped(C.rows, C.cols, Aop.cols, p, nullptr, &lq));
+        void* lws = fm_workspace(6, fm_limb_workspace_bytes(lq));
+        if (!lws) return FM_ENOMEM;
+        return fm_limb_run(lq, C, Aop, Bop, p, op, lws, status, la.v);
+    };
     // the same on the look-ahead stream, in its own workspace, on capped CTAs
     auto product_u = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
         if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
@@ -1207,6 +1228,19 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                 ++fast_panels;
                 for (int t = 0; t < kNb; ++t) pivot_pos.push_back((int)(c0 + t));
                 const fm_matrix Xm{xs, 0, 7}, Ym{ys, 0, 7};
+                // A panel that does not end its block updates the block's columns
+                // behind it: U12 <- L11^-1 A12, then A22 <- A22 - L21 U12. U12
+                // does not depend on L21, so it runs on the side stream v (once
+                // the inverses are done) beside the L21 product, and s waits for
+                // it before the update.
+                const bool inner = nbk + 1 < kOuter && c0 + w < n && r + kNb < m && c0 + w < c_lim;
+                const fm_sub A12{Am, r, c0 + w, kNb, c_lim - (c0 + w)};
+                if (inner) {
+                    FM_CUDA_TRY(cudaEventRecord(la.ev_v0, s));
+                    FM_CUDA_TRY(cudaStreamWaitEvent(la.v, la.ev_v0, 0));
+                    FM_TRY(product_v(A12, fm_sub{Xm, 0, 0, kNb, kNb}, A12, FM_OP_SET));
+                    FM_CUDA_TRY(cudaEventRecord(la.ev_v1, la.v));
+                }
                 if (r + kNb < m) {
                     // L21 <- A21 U11^-1, over A21 itself (its planes are split before it is written)
                     const fm_sub A21{Am, r + kNb, c0, m - r - kNb, kNb};
@@ -1216,7 +1250,14 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
                     if (!lws) return FM_ENOMEM;
                     FM_TRY(fm_limb_run(lq, A21, A21, fm_sub{Ym, 0, 0, kNb, kNb}, p, FM_OP_SET, lws, status, s));
                 }
-                FM_TRY(after_panel(kNb, Xm));
+                if (inner) {
+                    FM_CUDA_TRY(cudaStreamWaitEvent(s, la.ev_v1, 0));
+                    bk[nbk++] = kNb;
+                    FM_TRY(product(fm_sub{Am, r + kNb, c0 + w, m - r - kNb, A12.cols},
+                                   fm_sub{Am, r + kNb, c0, m - r - kNb, kNb}, A12, FM_OP_SUB));
+                } else {
+                    FM_TRY(after_panel(kNb, Xm));
+                }
                 r += kNb;
                 continue;
             }
