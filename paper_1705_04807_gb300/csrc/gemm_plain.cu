@@ -99,21 +99,26 @@ __host__ __device__ constexpr int plain_stages()
     return LT == 5 ? 4 : 2;
 }
 
-// Output rows per warp: a CTA has T' / kRowsPerWarp warps (16 at T' = 64,
-// 8 at 32). Each multiply-add's 64-bit accumulation waits on the previous one
-// into the same accumulator; four rows a warp (instead of eight) doubles the
-// warps per SM sub-partition that hide that latency, for more shared-memory
-// loads per multiply-add.
-constexpr int kRowsPerWarp = 4;
-
-template <int LT>
-__host__ __device__ constexpr int plain_threads()
+// Output rows per warp: a CTA has T' / rows_per_warp warps. Each integer
+// multiply-add's 64-bit accumulation waits on the previous one into the same
+// accumulator; four rows a warp (instead of eight) doubles the warps per SM
+// sub-partition that hide that latency, for more shared-memory loads per
+// multiply-add. The FP64 form is bound by its pipe and keeps eight (four
+// measured 9 % slower there).
+template <int ARITH>
+__host__ __device__ constexpr int rows_per_warp()
 {
-    return (1 << LT) / kRowsPerWarp * 32;
+    return ARITH == kArithDfma ? 8 : 4;
 }
 
 template <int LT, int ARITH>
-__global__ void __launch_bounds__(plain_threads<LT>())
+__host__ __device__ constexpr int plain_threads()
+{
+    return (1 << LT) / rows_per_warp<ARITH>() * 32;
+}
+
+template <int LT, int ARITH>
+__global__ void __launch_bounds__(plain_threads<LT, ARITH>())
     plain_kernel(const FmCallDesc* __restrict__ calls, const FmWorkItem* __restrict__ items,
                  const FmLPiece* __restrict__ lps, int64_t n_items, uint32_t p, int* queue,
                  int* status)
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(plain_threads<LT>())
     using Val = typename Traits<ARITH>::Val;
     constexpr int T = 1 << LT;
     constexpr int TE = T * T;             // elements per tile
-    constexpr int RPW = kRowsPerWarp;     // output rows per warp
+    constexpr int RPW = rows_per_warp<ARITH>();  // output rows per warp
     constexpr int CPL = T / 32;           // output columns per lane
     constexpr uint32_t kTileBytes = TE * 4;
     constexpr int S = plain_stages<LT>();
@@ -297,7 +302,7 @@ int launch_t(const FmCallDesc* calls, const FmWorkItem* items, const FmLPiece* l
     const size_t smem = (size_t)plain_stages<LT>() * 4 * T * T * 4;
     auto k = plain_kernel<LT, ARITH>;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<grid, plain_threads<LT>(), smem, s>>>(calls, items, lps, n_items, p, queue, status);
+    k<<<grid, plain_threads<LT, ARITH>(), smem, s>>>(calls, items, lps, n_items, p, queue, status);
     FM_CUDA_TRY(cudaGetLastError());
     return FM_OK;
 }
@@ -330,7 +335,7 @@ int fm_plain_occupancy(int lt, int arith)
     if (lt == L && arith == A) {                                                                 \
         cudaFuncSetAttribute(plain_kernel<L, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                              (int)smem);                                                         \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, plain_kernel<L, A>, plain_threads<L>(), smem); \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, plain_kernel<L, A>, plain_threads<L, A>(), smem); \
     }
     FM_OCC(5, kArithNarrow)
     FM_OCC(5, kArithWide)
