@@ -1063,8 +1063,10 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             return FM_ENOMEM;
     }
     // C op A * B with every operand a sub-matrix of A (the limb product writes
-    // C over the B operand when they are the same part: it splits B first)
-    // the panel row's product on the side stream v, in a workspace of its own
+    // C over the B operand when they are the same part: it splits B first):
+    // product on s (fm_gemm_modp's own choice of form), product_v on the side
+    // stream v in a workspace of its own, product_u on the look-ahead stream u
+    // in another, on capped CTAs
     auto product_v = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
         if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
         FmLimbPlan lq;
@@ -1073,7 +1075,6 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         if (!lws) return FM_ENOMEM;
         return fm_limb_run(lq, C, Aop, Bop, p, op, lws, status, la.v);
     };
-    // the same on the look-ahead stream, in its own workspace, on capped CTAs
     auto product_u = [&](const fm_sub& C, const fm_sub& Aop, const fm_sub& Bop, int op) -> int {
         if (C.rows == 0 || C.cols == 0 || Aop.cols == 0) return FM_OK;
         FmLimbPlan lq;
