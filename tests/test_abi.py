@@ -166,3 +166,35 @@ def test_validate_residues_rejects_bad_arguments_on_the_host(fm):
             fm.fm_validate_residues(fm.sub(M, 0, 0, 8, 8), p)
     with pytest.raises(fm.FmError):
         fm.fm_validate_residues(fm.sub(M, 60, 0, 8, 8), 65521)   # outside the matrix
+
+
+def test_default_tile_width_follows_the_shape(fm):
+    # fm_gemm_modp's limb form sizes its workspace for the planes of the output
+    # tile width it will run (host only: without a GPU the SM count takes its
+    # default). Fold form: 128-wide tiles for K <= 1024 and for thin products,
+    # 256-wide ones for long products with many tiles; an explicit width is
+    # kept; the residue form always takes 128.
+    lt, lg = 7, 7  # 16384 x 16384 grids at T' = 128; fake bases 4 GiB apart
+    C, A, B = (fm.matrix(q << 32, lg, lt) for q in (1, 2, 3))
+
+    def ws(p, M, N, K, o=None):
+        return fm.fm_gemm_modp_workspace_size(fm.sub(C, 0, 0, M, N), fm.sub(A, 0, 0, M, K),
+                                              fm.sub(B, 0, 0, K, N), p, fm.FM_ALGO_LIMB_TC, o)
+
+    def planes(p, M, N, K, bn):
+        o = fm.opts(0, bn)
+        return fm.fm_limb_planes_size(M, K, fm.FM_LIMB_A, p, o) + fm.fm_limb_planes_size(K, N, fm.FM_LIMB_B, p, o)
+
+    p16, p31 = 65521, 2147483647
+    # shapes whose planes differ between the widths (row blocks padded to an even
+    # count at 256, columns to 128 or 256)
+    cases = [((8000, 8000, 512), 128),     # short K
+             ((8000, 8000, 8192), 256),    # long, many tiles
+             ((16000, 100, 2048), 128),    # one column of tiles
+             ((100, 11000, 2048), 128)]    # one row block
+    for (M, N, K), bn in cases:
+        assert planes(p16, M, N, K, 128) != planes(p16, M, N, K, 256)
+        assert ws(p16, M, N, K) == planes(p16, M, N, K, bn), (M, N, K)
+    assert ws(p16, 8000, 8000, 8192, fm.opts(0, 128)) == planes(p16, 8000, 8000, 8192, 128)
+    assert ws(p16, 8000, 8000, 512, fm.opts(0, 256)) == planes(p16, 8000, 8000, 512, 256)
+    assert ws(p31, 4000, 4000, 4096) == planes(p31, 4000, 4000, 4096, 128)
