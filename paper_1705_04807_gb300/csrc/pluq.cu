@@ -1044,10 +1044,12 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
         la.set = cur_set;
         return FM_OK;
     };
-    // u's GEMM CTAs: 4/5 of the SM count (config 5: 120 of 152 took 30.5 ms,
-    // 202 -- spread over every SM, so that the one-CTA panel kernels, which take
-    // a whole SM's registers, wait for it -- 31.9 ms, 76 or fewer starve u)
-    const int u_ctas = std::max(2, sms * 4 / 5);
+    // u's GEMM CTAs: all but one SM in twelve (140 of 152). With the side stream
+    // v also running, a 16384 x 12288 rank-10000 factorization took 29.7 / 27.8 /
+    // 27.5 / 31.5 / 30.1 ms at 100 / 121 / 140 / 152 / 170 CTAs: at 152 or more u
+    // reaches every SM and the one-CTA panel kernels, which take a whole SM's
+    // registers, wait for it; at 121 or fewer u is starved
+    const int u_ctas = std::max(2, sms - sms / 12);
     // plane workspaces sized once for the largest product (K = a block's pivots),
     // so that neither stream's workspace is reallocated while the other runs
     {
