@@ -648,10 +648,14 @@ __device__ __forceinline__ void unit_lower_inv_cols(const uint32_t* const (&lrow
 // of a lower triangle are the inverses of its diagonal blocks: when dg is not
 // null (k = 128) they are taken from there (block b's inverse column-major at
 // dg + b * 2048 + (UPPER ? 1024 : 0), as diag_lu_kernel leaves them).
+// A column block of the lower inverse depends on no other column block, so
+// with cb >= 0 (k = 128) only block column cb is computed and stored: the
+// columns [32 cb, 32 cb + 32) of X, or for UPPER the rows [32 cb, 32 cb + 32)
+// of U^-1, which come from those columns of the inverse of V^T.
 template <bool UPPER, bool SMALL>
 __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t r0, int64_t c0, int k, uint32_t* X,
                                              int xlt, uint32_t p, uint64_t mu, const uint32_t* dinv,
-                                             const uint32_t* dg)
+                                             const uint32_t* dg, int cb = -1)
 {
     const uint32_t mu32 = (uint32_t)(0xFFFFFFFFu / p);
     extern __shared__ uint32_t smx[];
@@ -701,14 +705,16 @@ __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t 
     // 2. block rows below the first: thread (r, c) = (warp, lane) of each 32 x 32 block
     for (int bi = 1; bi < nb; ++bi) {
         const int i = 32 * bi + warp;
-        for (int bj = 0; bj < bi; ++bj) {
+        const int bj0 = cb < 0 ? 0 : cb, bj1 = cb < 0 ? bi : min(bi, cb + 1);
+        if (bj0 >= bj1) continue;  // the same for every thread
+        for (int bj = bj0; bj < bj1; ++bj) {
             uint64_t acc = 0;
 #pragma unroll 8
             for (int t = 32 * bj; t < 32 * bi; ++t) acc = mac<SMALL>(acc, L[i * S + t], Xs[t * S + 32 * bj + lane], p, mu);
             T[(bj * 32 + warp) * 32 + lane] = red64(acc, p, mu);
         }
         __syncthreads();
-        for (int bj = 0; bj < bi; ++bj) {
+        for (int bj = bj0; bj < bj1; ++bj) {
             uint64_t acc = 0;
 #pragma unroll 8
             for (int s2 = 0; s2 < 32; ++s2)
@@ -716,6 +722,14 @@ __device__ __forceinline__ void tri_inv_body(const uint32_t* A, int lt, int64_t 
             Xs[i * S + 32 * bj + lane] = neg_mod(acc, p, mu);
         }
         __syncthreads();
+    }
+    if (cb >= 0) {
+        for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
+            const int i = UPPER ? 32 * cb + e / k : e / 32, j = UPPER ? e % k : 32 * cb + e % 32;
+            X[fm_encode((uint64_t)i, (uint64_t)j, xlt)] =
+                UPPER ? mulmod(Xs[j * S + i], dinv[j], p, mu) : Xs[i * S + j];
+        }
+        return;
     }
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int i = e / k, j = e % k;
@@ -732,10 +746,11 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const uint32_t* A,
     tri_inv_body<false, SMALL>(A, lt, r0, c0, k, X, xlt, p, mu, nullptr, nullptr);
 }
 
-// Both inverses of a diagonal block factored by diag_lu_kernel: CTA 0 writes
-// X = L11^-1, CTA 1 writes Y = U11^-1. Launched right behind diag_lu_kernel,
-// before the host has read its flag: when the fast path failed (*flag != 0)
-// it returns at once.
+// Both inverses of a diagonal block factored by diag_lu_kernel, one 32-wide
+// block column each of eight CTAs: CTAs 0-3 write the block columns of
+// X = L11^-1, CTAs 4-7 the block rows of Y = U11^-1. Launched right behind
+// diag_lu_kernel, before the host has read its flag: when the fast path failed
+// (*flag != 0) it returns at once.
 template <bool SMALL>
 __global__ void __launch_bounds__(kInvThreads) tri_inv2_kernel(const uint32_t* A, int lt, int64_t r0, int64_t c0,
                                                                uint32_t* X, uint32_t* Y, int xlt, uint32_t p,
@@ -743,10 +758,11 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv2_kernel(const uint32_t* A
                                                                const uint32_t* dg)
 {
     if (*flag != 0) return;
-    if (blockIdx.x == 0)
-        tri_inv_body<false, SMALL>(A, lt, r0, c0, kNb, X, xlt, p, mu, nullptr, dg);
+    const int cb = (int)(blockIdx.x & 3);
+    if (blockIdx.x < 4)
+        tri_inv_body<false, SMALL>(A, lt, r0, c0, kNb, X, xlt, p, mu, nullptr, dg, cb);
     else
-        tri_inv_body<true, SMALL>(A, lt, r0, c0, kNb, Y, xlt, p, mu, dinv, dg);
+        tri_inv_body<true, SMALL>(A, lt, r0, c0, kNb, Y, xlt, p, mu, dinv, dg, cb);
 }
 
 // ---- diagonal-block fast path -------------------------------------------------
@@ -1223,7 +1239,7 @@ extern "C" int fm_pluq(fm_matrix Am, int64_t m, int64_t n, uint32_t p, int32_t* 
             FM_CUDA_TRY(cudaEventRecord(la.ev_flag, s));
             auto ik = p < (1u << 16) ? tri_inv2_kernel<true> : tri_inv2_kernel<false>;
             FM_CUDA_TRY(cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
-            ik<<<2, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv, d_flag, dgs);
+            ik<<<8, kInvThreads, ismem, s>>>(Am.base, Am.log2_T, r, c0, xs, ys, 7, p, mu, dinv, d_flag, dgs);
             FM_CUDA_TRY(cudaGetLastError());
             FM_CUDA_TRY(cudaEventSynchronize(la.ev_flag));
             const int flag = *la.h_flag;
