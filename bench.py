@@ -73,15 +73,22 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU under torchrun (RANK, LOCAL_RANK, WORLD_SIZE and
+    MASTER_* from the environment): NCCL on the GPUs, or `backend` (gloo on
+    host cores) when given. The ranks are independent replicas; the group only
+    carries the barriers and the max over ranks of the timed region."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend in (None, "nccl"):
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -96,9 +103,16 @@ def allreduce_max(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ops_per_step, steps, max_ms, world):
+    """Whole-job throughput in Gop/s: every rank runs `steps` steps of
+    `ops_per_step` operations; the job takes the slowest rank's time."""
+    return world * ops_per_step * steps / (max_ms / 1e3) / 1e9
 
 
 class Clocks:
@@ -909,7 +923,7 @@ def run_fm(args, world, rank, local):
     local_ms = t_start.elapsed_time(t_end)
     total_ms = allreduce_max(local_ms, world)
     ops = 2.0 * n * n * n
-    value = world * ops * args.steps / (total_ms / 1e3) / 1e9
+    value = job_value(ops, args.steps, total_ms, world)
     st = fm.fm_get_last_device_status(s)
     assert st == 0, f"device status {st}"
 
@@ -971,7 +985,7 @@ def run_fm(args, world, rank, local):
         same = bool(torch.equal(last.to(torch.int32) & 0xFFFF, want) if u16 else torch.equal(last, want))
         assert same
         esz = 2 if u16 else 4
-        return {"value": world * ops * args.steps / (ms / 1e3) / 1e9, "unit": "Gop/s",
+        return {"value": job_value(ops, args.steps, ms, world), "unit": "Gop/s",
                 "h2d_bytes_per_step": 3 * n * n * esz, "d2h_bytes_per_step": n * n * esz,
                 "host_dtype": "u16" if u16 else "u32", "ms_per_step": ms / args.steps}
 
