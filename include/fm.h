@@ -258,7 +258,9 @@ int fm_limb_gemm(fm_sub C, const void* a_planes, const void* b_planes, int64_t K
  * any stream capture. All calls share the one array, so calls that can overlap
  * on the GPU (different streams without ordering) race and must be serialised
  * by the caller; the array keeps the last call's contents, and every call
- * rewrites all of it that it reads. A device-side wait that expires raises
+ * rewrites all of it that its stored results depend on (what it leaves, the
+ * planes' rows past M or N, reaches only outputs that are never stored). A
+ * device-side wait that expires raises
  * FM_ETIMEOUT in the array's own status word; fm_get_last_device_status reads
  * (and clears) that word together with the library's, without allocating. */
 int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, int32_t op, fm_stream stream);

@@ -96,8 +96,10 @@ extern "C" int fm_gemm_modp_noalloc(fm_sub C, fm_sub A, fm_sub B, uint32_t p, in
     if (!scratch) return FM_ECUDA;
     // The status word is not cleared here: like the library's own status word
     // it keeps the first error raised since fm_get_last_device_status last read
-    // it. The split overwrites every byte of the planes it uses (padding
-    // included), so nothing left by an earlier call needs clearing either.
+    // it. Nothing left in the planes by an earlier call needs clearing either:
+    // the split writes every plane byte a stored output depends on, the zero
+    // K padding included; plane rows past M (A) or N (B) keep older contents,
+    // which reach only output rows and columns that are never stored.
     int* status = reinterpret_cast<int*>(scratch + kNoallocPlaneBytes);
     return fm_limb_run(plan, C, A, B, p, op, scratch, status, s);
 }
