@@ -91,6 +91,14 @@ def test_pluq_special_cases(orc):
     u[0] = 1
     v[0] = 1
     assert _check_pluq(orc, (np.outer(u, v) % p).astype(np.uint32), p) == 1
+    # cases that need a permutation whatever the pivot rule: with an all-zero
+    # first row, U's nonzero first row can only come from row 1 (P is not the
+    # identity); with an all-zero first column, U(0, 0) != 0 needs another
+    # column first (Q is not the identity)
+    A = np.array([[0, 0], [5, 7]], np.uint32)
+    assert _check_pluq(orc, A, p) == 1 and orc.pluq(A, p)[0][0] == 1
+    A = np.array([[0, 2, 4], [0, 1, 9]], np.uint32)
+    assert _check_pluq(orc, A, p) == 2 and orc.pluq(A, p)[1][0] != 0
 
 
 @pytest.mark.parametrize("p", [2, 3, 65521])
