@@ -519,3 +519,38 @@ def test_default_calls_stand_in_without_mistake_passes(orc, monkeypatch):
     monkeypatch.setattr(recursion, "default_calls", _default_calls_with(None))
     failed, _ = _run_pins((test_table1_calls, test_oracle_recursion), orc)
     assert failed == []
+
+
+# ---------------------------------------------------------------------------
+# sampled entries and the matrix-vector product behind Freivalds' check
+# ---------------------------------------------------------------------------
+def _entries_with_swapped_index(real):
+    def gemm_modp_entries(C, A, B, p, op, ij):
+        ij = np.asarray(ij, dtype=np.int64).reshape(-1, 2)
+        full = real(C, A, B, p, op)
+        i, j = ij[:, 0], ij[:, 1]
+        ok = (j < full.shape[0]) & (i < full.shape[1])
+        out = full[i, j].copy()
+        out[ok] = full[j[ok], i[ok]]
+        return out
+    return gemm_modp_entries
+
+
+def _matvec_dropping_last_term(A, x, p):
+    A = np.asarray(A, dtype=np.uint64)
+    x = np.asarray(x, dtype=np.uint64)
+    if A.shape[1] < 2:
+        return (A.astype(object) @ x.astype(object) % p).astype(np.uint32)
+    return (A[:, :-1].astype(object) @ x[:-1].astype(object) % p).astype(np.uint32)
+
+
+def test_entries_pin_catches_a_swapped_index(orc):
+    stand_in = _Oracle(orc, gemm_modp_entries=_entries_with_swapped_index(orc.gemm_modp))
+    failed, _ = _run_pins((test_oracle_gemm,), stand_in)
+    assert failed
+
+
+def test_freivalds_pin_catches_a_matvec_that_drops_a_term(orc, monkeypatch):
+    monkeypatch.setattr(oracle, "matvec_modp", _matvec_dropping_last_term)
+    failed, _ = _run_pins((test_oracle_gemm,), orc)
+    assert failed
