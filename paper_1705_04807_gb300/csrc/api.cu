@@ -477,7 +477,7 @@ extern "C" int fm_gemm_modp_batched(fm_plan* plan, fm_stream stream)
 
 extern "C" int64_t fm_plan_work_items(const fm_plan* plan)
 {
-    return plan ? plan->n_items : FM_EINVAL;
+    return plan ? plan->n_items : (int64_t)FM_EINVAL;
 }
 
 extern "C" int64_t fm_plan_launches(const fm_plan* plan)
