@@ -205,7 +205,8 @@ int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uint32_t p, in
  * + 256 (A0+A1)*(B0+B1) + (2^16-256) A1*B1) instead of four.
  *   role FM_LIMB_A (an M x K operand): plane t holds MB x ceil(K/64) tiles in
  *     row-block-major order, each 128 rows x 64 k (16 KB); MB = ceil(M/128),
- *     rounded up to even when BN = 256 (a CTA pair takes two row blocks).
+ *     rounded up to even when BN = 256 or in the residue form (p >= 2^16 or
+ *     p even), where a CTA pair may take two row blocks.
  *   role FM_LIMB_B (a K x N operand, stored transposed): plane t holds
  *     ceil(N/BN) x ceil(K/64) tiles, each BN rows (n) x 64 k (BN * 128 bytes),
  *     BN = the product's output tile width (fm_opts.block_n; default 256 when
@@ -213,7 +214,9 @@ int64_t fm_gemm_modp_workspace_size(fm_sub C, fm_sub A, fm_sub B, uint32_t p, in
  *   Inside a tile, row r is 128 bytes; its 16-byte chunk c (8 consecutive k)
  *   is stored at r*128 + ((c ^ (r % 8)) * 16) (the 128-byte swizzle of the
  *   tensor core's shared-memory operand layout). Entries past the operand's
- *   extent are zero. Planes follow each other without gaps. */
+ *   K extent are zero; rows past its M (A) or N (B) extent, a padding row
+ *   block included, are not written, since they reach only output rows or
+ *   columns that are never stored. Planes follow each other without gaps. */
 enum { FM_LIMB_A = 0, FM_LIMB_B = 1 };
 
 /* Bytes of the limb planes of an operand (rows x cols as the operand is

@@ -198,3 +198,29 @@ def test_default_tile_width_follows_the_shape(fm):
     assert ws(p16, 8000, 8000, 8192, fm.opts(0, 128)) == planes(p16, 8000, 8000, 8192, 128)
     assert ws(p16, 8000, 8000, 512, fm.opts(0, 256)) == planes(p16, 8000, 8000, 512, 256)
     assert ws(p31, 4000, 4000, 4096) == planes(p31, 4000, 4000, 4096, 128)
+
+
+def test_limb_planes_size_follows_the_documented_layout(fm):
+    # host-only: the plane bytes fm_limb_planes_size reports are the layout the
+    # header documents -- per plane, A in ceil(M/128) x ceil(K/64) tiles of
+    # 16 KB (row blocks rounded up to even for 256-wide tiles and in the
+    # residue form), B in ceil(N/BN) x ceil(K/64) tiles of BN * 128 bytes;
+    # planes: 2 limbs + Karatsuba sum (odd p < 2^16), w + w(w-1)/2 (residue
+    # form, w limbs and every pair sum), w without Karatsuba
+    def cdiv(a, b):
+        return -(-a // b)
+
+    cases = [(65521, 3, 256, True), (257, 3, 256, True), (65534, 3, 128, True),
+             (65537, 6, 128, True), (2147483647, 10, 128, True)]
+    for p, planes, bn, even in cases:
+        for M, K, N in ((100, 64, 100), (129, 65, 300), (300, 1000, 129), (1, 1, 1), (4096, 4096, 4096)):
+            mb = cdiv(M, 128)
+            mb += mb % 2 if even else 0
+            kb = cdiv(K, 64)
+            assert fm.fm_limb_planes_size(M, K, fm.FM_LIMB_A, p, None) == planes * mb * kb * 16384, (p, M, K)
+            assert fm.fm_limb_planes_size(K, N, fm.FM_LIMB_B, p, None) == planes * cdiv(N, bn) * kb * bn * 128, (p, K, N)
+    # without Karatsuba the two-limb fold form keeps just its two digit planes
+    assert fm.fm_limb_planes_size(100, 64, fm.FM_LIMB_A, 65521, fm.opts(no_karatsuba=1)) == 2 * 2 * 1 * 16384
+    for bad in ((-1, 64, fm.FM_LIMB_A, 65521), (64, 64, 7, 65521), (64, 64, fm.FM_LIMB_A, 1)):
+        with pytest.raises(fm.FmError):
+            fm.fm_limb_planes_size(*bad)
